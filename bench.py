@@ -1,0 +1,377 @@
+"""Benchmark of the PF-MP hot path on GB300.
+
+Workload (one "step"): solve K x = b to a true relative residual of 1e-10 on a
+16^3 x 32 lattice -- SU(3) links U = exp(i 0.5 H) with Gaussian H (seed 1),
+Wilson-clover c_sw = 1.0, kappa = 0.130, even-odd preconditioned, Gaussian complex
+right-hand side (seed 100) -- with the mixed-precision CG (FP32 iterations, FP64
+reliable updates, FP64 true residual).  Inputs are resident in HBM when the timed
+region starts; L2 is flushed (a 512 MiB write) before every timed step.
+
+Also reported on the same line:
+  fp64_cg    the same solve with CG in FP64 throughout (the baseline the mixed solver
+             is compared against), and the speedup;
+  e2e        the same solve through the host-memory entry point pfmp_solve_host
+             (H2D of b and D2H of x inside the timed region), wall clock;
+  roofline   the stencil kernels (Wilson hop with fused clover epilogues, FP32) timed
+             by CUDA events inside the library over R applications of K on a
+             32^3 x 64 lattice (1.7 GB of FP32 operator data, far above the 129 MB L2),
+             algorithmic bytes / time against the measured HBM copy bandwidth;
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the same solve.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank solves its own copy (replicas, weak scaling).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (16, 16, 16, 32)
+EPS, KAPPA, CSW, TOL = 0.5, 0.130, 1.0, 1e-10
+GAUGE_SEED, RHS_SEED = 1, 100
+ROOF_DIMS = (32, 32, 32, 64)
+METRIC = "PF-MP traj & solve time: mixed+learned vs FP64 CG at 1e-10; dslash HBM GB/s"
+UNIT = "ms per solve (16^3x32 K x = b to 1e-10 true residual)"
+WORKLOAD = "Dslash + solver at 16^3x32: eps=0.5 random SU(3), c_sw=1.0, kappa=0.130, Gaussian RHS, 1e-10"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_setup(n):
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if os.environ.get("PFMP_BENCH_GLOO") is None else "gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allmax(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle (CPU) timing
+def oracle_sample(iters):
+    """The FP64 CPU oracle's CG on the same system, stopped after `iters` iterations.
+
+    Returns (seconds per iteration, estimated iterations to 1e-10 from the oracle's own
+    residual decay, threads)."""
+    import torch
+
+    import pfmp_inputs as pin
+    from oracle.dirac import WilsonClover
+    from oracle.lattice import Lattice, algebra_to_matrix, expi_hermitian
+
+    lat = Lattice(DIMS, bc_t=-1)
+    U = expi_hermitian(algebra_to_matrix(torch.tensor(pin.gauge_algebra(DIMS, GAUGE_SEED)).reshape(*lat.shape, 4, 8)), EPS)
+    W = WilsonClover(lat, U, KAPPA, CSW)
+    _ = W.Ainv
+    b = torch.tensor(pin.spinor(DIMS, RHS_SEED)).reshape(*lat.shape, 4, 3) * lat.even
+    x = torch.zeros_like(b)
+    r = b.clone()
+    p = r.clone()
+    rr = (r.conj() * r).sum().real
+    bb = rr
+    t0 = time.perf_counter()
+    res = []
+    for _ in range(iters):
+        Ap = W.K(p)
+        a = rr / (p.conj() * Ap).sum().real
+        x = x + a * p
+        r = r - a * Ap
+        rn = (r.conj() * r).sum().real
+        p = r + (rn / rr) * p
+        rr = rn
+        res.append(math.sqrt(rr / bb))
+    dt = (time.perf_counter() - t0) / iters
+    rate = math.log(res[-1]) / iters
+    est = int(math.ceil(math.log(TOL) / rate)) if rate < 0 else None
+    return dt, est, torch.get_num_threads()
+
+
+def oracle_iterations():
+    """Iterations the oracle's FP64 CG needs on this system (stored by
+    tests/golden/make_cg_iterations.py, which runs only the oracle)."""
+    p = os.path.join(ROOT, "tests", "golden", "cg_iterations_16x16x16x32.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return int(json.load(f)["iterations"]), "the oracle's full FP64 CG run (stored)"
+    return None, None
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    per_step = []
+    est = None
+    thr = None
+    for _ in range(args.warmup + args.steps):
+        dt, est, thr = oracle_sample(2)
+        per_step.append(dt)
+    per_it = statistics.mean(per_step[args.warmup:])
+    n_it, how = oracle_iterations()
+    if n_it is None:
+        n_it, how = est, "extrapolated from the sample's residual decay"
+    value = per_it * n_it * 1e3
+    sample = (f"{2 * args.steps} FP64 oracle CG iterations (2 per step) on the full 16^3x32 system; ms/solve = "
+              f"s/iteration x {n_it} iterations ({how})")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "implementation": "FP64 CPU oracle (PyTorch CPU ops)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world):
+    import torch
+
+    import pfmp_inputs as pin
+    from paper_1609_02652_gb300 import capi
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def l2_flush():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+
+    ctx = capi.pfmp_ctx_create(DIMS, -1, stream.cuda_stream)
+    h = torch.tensor(np.ascontiguousarray(pin.gauge_algebra(DIMS, GAUGE_SEED)).reshape(-1), device="cuda")
+    bcan = torch.tensor(np.ascontiguousarray(pin.spinor(DIMS, RHS_SEED)).view(np.float64).reshape(-1), device="cuda")
+    torch.cuda.synchronize()
+    capi.pfmp_gauge_from_algebra(ctx, h, EPS, capi.PFMP_DEVICE)
+    op = capi.pfmp_op_create(ctx, KAPPA, CSW)
+    nb64 = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F64) // 8
+    b = torch.zeros(nb64, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    capi.pfmp_spinor_pack(ctx, b, capi.PFMP_F64, bcan, capi.PFMP_DEVICE, 0)
+    mixed = capi.SolverParams(method=capi.PFMP_SOLVER_CG_MIXED, tol=TOL, max_iter=20000, delta=0.1, check_every=32)
+    plain = capi.SolverParams(method=capi.PFMP_SOLVER_CG64, tol=TOL, max_iter=20000, delta=0.1, check_every=32)
+
+    def timed(params, steps, profile=False):
+        times, infos = [], []
+        for _ in range(steps):
+            l2_flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(capi.pfmp_solve(op, params, x, b))
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times, infos
+
+    for _ in range(args.warmup):
+        capi.pfmp_solve(op, mixed, x, b)
+    torch.cuda.synchronize()
+    barrier(world)
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if "CUDA_VISIBLE_DEVICES" in os.environ else local
+    clk = Clocks(gpu_index)
+    launches0 = capi.pfmp_launch_count()
+    capi.pfmp_profile_begin(ctx)
+    t_mixed, info_mixed = timed(mixed, args.steps)
+    n_hop, hop_ms, hop_bytes = capi.pfmp_profile_end(ctx, capi.PFMP_KERNEL_HOP_F32)
+    launches = capi.pfmp_launch_count() - launches0
+    clocks = clk.stop()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_step = allmax(sum(t_mixed), world) / args.steps
+    value = ms_step / world  # whole-job ms per solve (replicas)
+
+    # FP64 CG baseline (same system, same flush)
+    for _ in range(1):
+        capi.pfmp_solve(op, plain, x, b)
+    t_plain, info_plain = timed(plain, max(2, min(args.steps, 3)))
+    fp64_ms = statistics.mean(t_plain)
+
+    # end to end through host memory (pinned), wall clock
+    bh = torch.empty(DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] * 24, dtype=torch.float64, pin_memory=True)
+    bh.copy_(bcan.cpu())
+    xh = torch.empty_like(bh).pin_memory()
+    capi.pfmp_solve_host(op, mixed, xh.data_ptr(), bh.data_ptr())
+    e2e = []
+    for _ in range(args.steps):
+        l2_flush()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        capi.pfmp_solve_host(op, mixed, xh.data_ptr(), bh.data_ptr())
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = allmax(statistics.mean(e2e), world) / world
+    capi.pfmp_op_destroy(op)
+    capi.pfmp_ctx_destroy(ctx)
+
+    # roofline of the stencil kernels on a lattice far larger than L2
+    roof = roofline(capi, stream, l2_flush)
+
+    hbm, src = peaks()
+    hop_gbs_l2 = hop_bytes / (hop_ms * 1e-3) / 1e9 if hop_ms > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "16x16x16x32", "solver": "mixed CG, FP32 + FP64 reliable updates",
+                   "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
+        "iterations": info_mixed[-1].iters, "reliable_updates": info_mixed[-1].reliable_updates,
+        "true_rel_res": info_mixed[-1].true_rel_res,
+        "fp64_cg": {"ms": fp64_ms, "iterations": info_plain[-1].iters, "true_rel_res": info_plain[-1].true_rel_res,
+                    "speedup_mixed_vs_fp64": fp64_ms / ms_step},
+        "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 8),
+                "d2h_bytes_per_step": int(xh.numel() * 8)},
+        "roofline": roof,
+        "hop_in_solve": {"launches": n_hop, "avg_us": hop_ms * 1e3 / max(n_hop, 1), "algorithmic_gbs": hop_gbs_l2,
+                         "note": "16^3x32 FP32 working set (~75 MB) is L2-resident inside a solve"},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_it, est, thr = oracle_sample(args.cpu_iters)
+        n_it, how = oracle_iterations()
+        if n_it is None:
+            n_it, how = info_plain[-1].iters, "the FP64 CG iteration count of the GPU run"
+        line["cpu_baseline"] = {
+            "value": per_it * n_it * 1e3, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"{args.cpu_iters} FP64 oracle CG iterations on the full 16^3x32 system; ms/solve = "
+                      f"s/iteration x {n_it} iterations ({how})"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def roofline(capi, stream, l2_flush, reps=12):
+    import torch
+
+    import pfmp_inputs as pin
+
+    ctx = capi.pfmp_ctx_create(ROOF_DIMS, -1, stream.cuda_stream)
+    V = ROOF_DIMS[0] * ROOF_DIMS[1] * ROOF_DIMS[2] * ROOF_DIMS[3]
+    h = torch.tensor(np.ascontiguousarray(pin.gauge_algebra(ROOF_DIMS, GAUGE_SEED)).reshape(-1), device="cuda")
+    torch.cuda.synchronize()
+    capi.pfmp_gauge_from_algebra(ctx, h, EPS, capi.PFMP_DEVICE)
+    del h
+    op = capi.pfmp_op_create(ctx, KAPPA, CSW)
+    n32 = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F32) // 4
+    a = torch.randn(n32, dtype=torch.float32, device="cuda")
+    o = torch.zeros_like(a)
+    for _ in range(3):
+        capi.pfmp_kop(op, capi.PFMP_F32, o, a)
+    capi.pfmp_profile_begin(ctx)
+    for _ in range(reps):
+        l2_flush()
+        capi.pfmp_kop(op, capi.PFMP_F32, o, a)
+    n, ms, by = capi.pfmp_profile_end(ctx, capi.PFMP_KERNEL_HOP_F32)
+    capi.pfmp_op_destroy(op)
+    capi.pfmp_ctx_destroy(ctx)
+    hbm, src = peaks()
+    achieved = by / (ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "hop_f32_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get("bytes_per_launch_32x32x32x64")
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "peak_source": src,
+            "kernel": "k_hop FP32 (Wilson hop + fused clover epilogues), 4 launches per K",
+            "workload": "K applications on 32^3x64, FP32, L2 flushed before each K",
+            "launches": n, "avg_us": ms * 1e3 / n, "bytes_per_launch": by / n}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-iters", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

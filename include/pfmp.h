@@ -1,0 +1,187 @@
+/*
+ * pfmp.h -- C-ABI of the GB300 (sm_103a) library for the data-parallel hot path of
+ * polynomial-filtered mass-preconditioned HMC (PF-MP HMC; Haar, Kamleh, Zanotti,
+ * Nakamura, "Applying polynomial filtering to mass preconditioned Hybrid Monte Carlo").
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status: PFMP_OK (0) or one of the PFMP_E_* codes;
+ *    pfmp_last_error() gives a text for the most recent failure on this host thread.
+ *    No C++ exception crosses this boundary.
+ *  - All device work is enqueued on the context's CUDA stream.  Functions that return a
+ *    host scalar (norms, actions, solver info) synchronise that stream and say so.
+ *  - Handles (pfmp_ctx, pfmp_op, pfmp_poly, pfmp_action) are opaque and owned by the
+ *    library; each is released by its matching *_destroy.
+ *  - Spinor arguments ("void* field") are caller-owned DEVICE buffers of one parity in
+ *    the library's device layout: pfmp_spinor_bytes() gives their size; they are
+ *    filled with pfmp_spinor_pack() from the canonical layout.  The library never
+ *    frees caller buffers.
+ *  - Canonical host layout (used for gauge fields, spinors and momenta that cross the
+ *    boundary): lexicographic site index s = x + Lx*(y + Ly*(z + Lz*t)); gauge links
+ *    [s][mu][row][col] complex double (mu = 0..3 is x, y, z, t); spinors
+ *    [s][spin][colour] complex double in the chiral (DeGrand-Rossi) gamma basis;
+ *    momenta/forces [s][mu][a] real double, coefficients of P = sum_a p_a T_a with
+ *    T_a = lambda_a / 2.  Complex numbers are interleaved (re, im).
+ *  - Lattice extents must all be even (even-odd preconditioning) and Lx*Ly*Lz*Lt/2
+ *    must fit in an int.
+ *
+ * Operator (Sec. 2.1 and Table 3.1 of the paper, plus a clover term):
+ *    M = A - kappa H,  (H psi)(x) = sum_mu (1 - g_mu) U_mu(x) psi(x+mu)
+ *                                        + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu),
+ *    A(x) = 1 - kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x),
+ *    F_{mu nu} = traceless part of (Q_{mu nu} - Q_{mu nu}^dag)/(8i), Q = clover leaves,
+ *    M-hat = A_ee - kappa^2 H_eo A_oo^{-1} H_oe (even-odd Schur complement),
+ *    K = M-hat^dag M-hat (Sec. 2.1 eq. for S_F), J = the same at kappa' (eq. hasenbusch).
+ * Fermion fields in time direction carry the factor bc_t (-1: antiperiodic) across the
+ * boundary; gauge links are periodic.
+ */
+#ifndef PFMP_H
+#define PFMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define PFMP_OK 0
+#define PFMP_E_INVALID 1         /* bad argument (null pointer, odd extent, bad enum)   */
+#define PFMP_E_NOMEM 2           /* device or host allocation failed                     */
+#define PFMP_E_CUDA 3            /* a CUDA call failed; see pfmp_last_error()            */
+#define PFMP_E_NOT_CONVERGED 4   /* solver hit max_iter before the requested residual    */
+#define PFMP_E_TIMEOUT 5         /* a bounded device wait gave up                        */
+#define PFMP_E_NAN 6             /* a NaN/Inf appeared in a solver scalar or in dH       */
+#define PFMP_E_UNSUPPORTED 7     /* valid but not implemented (e.g. odd polynomial order)*/
+
+/* ---- precisions and locations ---------------------------------------------------- */
+#define PFMP_F64 0
+#define PFMP_F32 1
+#define PFMP_HOST 0
+#define PFMP_DEVICE 1
+
+typedef struct pfmp_ctx pfmp_ctx;
+typedef struct pfmp_op pfmp_op;
+
+/* Text of a status code (static storage). */
+const char* pfmp_strerror(int status);
+/* Text of the most recent error on this host thread ("" if none). */
+const char* pfmp_last_error(void);
+/* Library version, as major*10000 + minor*100 + patch. */
+int pfmp_version(void);
+/* Number of CUDA kernels this library has launched in this process (all contexts).  */
+int64_t pfmp_launch_count(void);
+
+/* ---- context: lattice geometry, stream, gauge field ---------------------------------
+ * pfmp_ctx_create: dims = {Lx, Ly, Lz, Lt} (all even, >= 2); bc_t = +1 or -1 is the
+ * fermion time boundary factor; stream is a cudaStream_t (NULL: the legacy default
+ * stream) borrowed, not owned.  Allocates the gauge field (FP64 master copy plus FP64
+ * and FP32 12-real compressed copies) and reduction scratch on the current device.
+ * Errors: PFMP_E_INVALID (odd or non-positive extent, |bc_t| != 1), PFMP_E_NOMEM.   */
+int pfmp_ctx_create(pfmp_ctx** ctx, const int dims[4], int bc_t, void* stream);
+int pfmp_ctx_destroy(pfmp_ctx* ctx);
+int pfmp_ctx_set_stream(pfmp_ctx* ctx, void* stream);
+/* Sites per parity (V/2). */
+int64_t pfmp_half_volume(const pfmp_ctx* ctx);
+/* Bytes of one single-parity spinor field of precision prec in the device layout. */
+int64_t pfmp_spinor_bytes(const pfmp_ctx* ctx, int prec);
+
+/* Gauge field in the canonical layout ([V][4][3][3] complex double), from host or
+ * device memory (where = PFMP_HOST / PFMP_DEVICE).  Links must be SU(3): the
+ * compressed copies keep two rows and rebuild the third as conj(row0 x row1).
+ * Setting the gauge field invalidates every operator's clover term until
+ * pfmp_op_update().                                                                  */
+int pfmp_gauge_set(pfmp_ctx* ctx, const double* U, int where);
+int pfmp_gauge_get(pfmp_ctx* ctx, double* U, int where);
+/* Field initialisation: U_mu(x) = exp(i eps H_mu(x)), H = sum_a h_a T_a with the
+ * coefficients h[V][4][8] (canonical order, host or device).  exp by scaling and
+ * squaring of the Taylor series, then reunitarised (rows Gram-Schmidt, row2 = cross).*/
+int pfmp_gauge_from_algebra(pfmp_ctx* ctx, const double* h, double eps, int where);
+/* Mean plaquette <Re tr U_{mu nu}>/3 over all sites and planes (synchronises).       */
+int pfmp_plaquette(pfmp_ctx* ctx, double* plaq);
+
+/* ---- spinor layout conversion --------------------------------------------------------
+ * pack: take the sites of parity `parity` (0 even, 1 odd) out of a canonical full-lattice
+ * spinor ([V][4][3] complex double, host or device) into the device field dst of
+ * precision prec.  unpack: write a parity field back into the canonical array; in
+ * device memory the other parity's sites are left untouched, in host memory they are
+ * written as zero (the whole array is copied back).                                  */
+int pfmp_spinor_pack(pfmp_ctx* ctx, void* dst, int prec, const double* src, int where, int parity);
+int pfmp_spinor_unpack(pfmp_ctx* ctx, double* dst, int where, const void* src, int prec, int parity);
+
+/* ---- the fermion operator ------------------------------------------------------------
+ * pfmp_op_create: an operator at (kappa, c_sw) on the context's gauge field.  Builds the
+ * clover blocks A (even sites) and A^{-1} (odd sites) in FP64 and FP32, and
+ * sum_{x odd} log det A(x).  A must be positive definite (Cholesky); otherwise
+ * PFMP_E_NAN.  pfmp_op_update rebuilds them after the gauge field changed.          */
+int pfmp_op_create(pfmp_ctx* ctx, double kappa, double csw, pfmp_op** op);
+int pfmp_op_update(pfmp_op* op);
+int pfmp_op_destroy(pfmp_op* op);
+/* sum over odd sites of log det A(x) (host scalar; synchronises).                    */
+int pfmp_op_logdet(pfmp_op* op, double* logdet_oo);
+
+/* Wilson hop restricted to one parity: out (parity out_parity) = H_{out,in} in; with
+ * dagger = 1 the adjoint hop H^dag (projectors (1 + g_mu) forward, (1 - g_mu) back).  */
+int pfmp_dslash(pfmp_op* op, int prec, void* out, const void* in, int out_parity, int dagger);
+/* out = A in (inverse = 0, even parity only) or A^{-1} in (inverse = 1, odd parity only):
+ * the blocks the even-odd operator needs.                                            */
+int pfmp_clover_apply(pfmp_op* op, int prec, void* out, const void* in, int parity, int inverse);
+/* out = M-hat in (dagger = 0) or M-hat^dag in (dagger = 1); even parity fields.      */
+int pfmp_mhat(pfmp_op* op, int prec, void* out, const void* in, int dagger);
+/* out = K in = M-hat^dag M-hat in; if in_K_in is not NULL it receives <in, K in> =
+ * ||M-hat in||^2 in FP64 (synchronises).                                             */
+int pfmp_kop(pfmp_op* op, int prec, void* out, const void* in, double* in_K_in);
+
+/* ---- BLAS-1 on single-parity fields (FP64 global sums) ----------------------------- */
+int pfmp_norm2(pfmp_ctx* ctx, int prec, const void* x, double* result);  /* synchronises */
+int pfmp_cdot(pfmp_ctx* ctx, int prec, const void* x, const void* y, double result[2]);
+int pfmp_axpy(pfmp_ctx* ctx, int prec, double a_re, double a_im, const void* x, void* y); /* y += a x */
+int pfmp_convert(pfmp_ctx* ctx, void* dst, int dst_prec, const void* src, int src_prec);
+
+/* ---- solvers on K (Sec. 2.1: CG; Sec. 3.1 and App. C: multi-shift CG) ---------------- */
+#define PFMP_SOLVER_CG64 0      /* CG in FP64 throughout                                 */
+#define PFMP_SOLVER_CG_MIXED 1  /* FP32 CG with FP64 reliable updates (true residual in  */
+                                /* FP64, solution accumulated in FP64)                    */
+typedef struct {
+  int method;        /* PFMP_SOLVER_*                                                     */
+  double tol;        /* stop when ||b - K x|| / ||b|| < tol, residual recomputed in FP64  */
+  int max_iter;      /* iteration cap -> PFMP_E_NOT_CONVERGED                              */
+  double delta;      /* mixed: reliable update when the sloppy residual fell by delta      */
+  int check_every;   /* iterations between host convergence checks (0: default 16)        */
+} pfmp_solver_params;
+
+typedef struct {
+  int iters;             /* CG iterations                                                 */
+  int reliable_updates;  /* FP64 residual recomputations (mixed)                         */
+  double true_rel_res;   /* ||b - K x|| / ||b|| recomputed in FP64 at exit                */
+  int64_t k_apply;       /* applications of K (either precision)                         */
+  int status;            /* PFMP_OK or PFMP_E_NOT_CONVERGED / PFMP_E_NAN                  */
+} pfmp_solve_info;
+
+/* x = K^{-1} b with zero initial guess; x, b FP64 even-parity device fields (x may not
+ * alias b).  Synchronises; info may be NULL.                                          */
+int pfmp_solve(pfmp_op* op, const pfmp_solver_params* params, void* x, const void* b,
+               pfmp_solve_info* info);
+/* The same call through host memory: b and x are canonical full-lattice spinors in
+ * host memory ([V][4][3] complex double; even sites of b are read, x receives the
+ * solution on even sites and zero on odd sites).  Copies in, packs, solves, unpacks
+ * and copies out inside the call.                                                     */
+int pfmp_solve_host(pfmp_op* op, const pfmp_solver_params* params, double* x_host,
+                    const double* b_host, pfmp_solve_info* info);
+
+/* ---- kernel timing (tracing) ------------------------------------------------------
+ * pfmp_profile_begin: from now on every stencil launch of this context is bracketed by
+ * CUDA events on the context's stream.  pfmp_profile_end (synchronises) stops recording
+ * and reports, for one kernel class, the number of launches, their summed device time
+ * in milliseconds, and their summed algorithmic DRAM bytes (per output site: 8 links of
+ * 12 reals, one input and one output spinor of 24 reals, plus 72 clover reals and 24
+ * local-input reals for the fused even-odd epilogues).                              */
+#define PFMP_KERNEL_HOP_F32 0
+#define PFMP_KERNEL_HOP_F64 1
+int pfmp_profile_begin(pfmp_ctx* ctx);
+int pfmp_profile_end(pfmp_ctx* ctx, int kernel_class, int64_t* launches, double* total_ms, double* total_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFMP_H */

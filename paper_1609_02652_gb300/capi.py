@@ -1,0 +1,268 @@
+"""Thin ctypes binding of the C-ABI in include/pfmp.h.
+
+Functions keep the C names and argument order; device buffers are passed as integer
+addresses (e.g. ``tensor.data_ptr()``), host arrays as numpy arrays.  A non-zero status
+raises ``PfmpError`` with the library's message.  Nothing here computes: every step of
+the method runs in the CUDA library.  Importing this module without the built library
+raises ``ImportError`` -- there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpfmp.so")
+
+PFMP_OK = 0
+PFMP_E_INVALID = 1
+PFMP_E_NOMEM = 2
+PFMP_E_CUDA = 3
+PFMP_E_NOT_CONVERGED = 4
+PFMP_E_TIMEOUT = 5
+PFMP_E_NAN = 6
+PFMP_E_UNSUPPORTED = 7
+PFMP_F64 = 0
+PFMP_F32 = 1
+PFMP_HOST = 0
+PFMP_DEVICE = 1
+PFMP_KERNEL_HOP_F32 = 0
+PFMP_KERNEL_HOP_F64 = 1
+PFMP_SOLVER_CG64 = 0
+PFMP_SOLVER_CG_MIXED = 1
+
+
+class PfmpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"pfmp status {status}: {msg}")
+        self.status = status
+
+
+class SolverParams(C.Structure):
+    _fields_ = [("method", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("delta", C.c_double),
+                ("check_every", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("reliable_updates", C.c_int), ("true_rel_res", C.c_double),
+                ("k_apply", C.c_int64), ("status", C.c_int)]
+
+
+P = C.c_void_p
+I = C.c_int
+D = C.c_double
+DP = C.POINTER(C.c_double)
+
+# name: (restype, argtypes)
+SIGNATURES = {
+    "pfmp_strerror": (C.c_char_p, [I]),
+    "pfmp_last_error": (C.c_char_p, []),
+    "pfmp_version": (I, []),
+    "pfmp_launch_count": (C.c_int64, []),
+    "pfmp_ctx_create": (I, [C.POINTER(P), C.POINTER(I), I, P]),
+    "pfmp_ctx_destroy": (I, [P]),
+    "pfmp_ctx_set_stream": (I, [P, P]),
+    "pfmp_half_volume": (C.c_int64, [P]),
+    "pfmp_spinor_bytes": (C.c_int64, [P, I]),
+    "pfmp_gauge_set": (I, [P, P, I]),
+    "pfmp_gauge_get": (I, [P, P, I]),
+    "pfmp_gauge_from_algebra": (I, [P, P, D, I]),
+    "pfmp_plaquette": (I, [P, DP]),
+    "pfmp_spinor_pack": (I, [P, P, I, P, I, I]),
+    "pfmp_spinor_unpack": (I, [P, P, I, P, I, I]),
+    "pfmp_op_create": (I, [P, D, D, C.POINTER(P)]),
+    "pfmp_op_update": (I, [P]),
+    "pfmp_op_destroy": (I, [P]),
+    "pfmp_op_logdet": (I, [P, DP]),
+    "pfmp_dslash": (I, [P, I, P, P, I, I]),
+    "pfmp_clover_apply": (I, [P, I, P, P, I, I]),
+    "pfmp_mhat": (I, [P, I, P, P, I]),
+    "pfmp_kop": (I, [P, I, P, P, DP]),
+    "pfmp_norm2": (I, [P, I, P, DP]),
+    "pfmp_cdot": (I, [P, I, P, P, DP]),
+    "pfmp_axpy": (I, [P, I, D, D, P, P]),
+    "pfmp_convert": (I, [P, P, I, P, I]),
+    "pfmp_solve": (I, [P, C.POINTER(SolverParams), P, P, C.POINTER(SolveInfo)]),
+    "pfmp_solve_host": (I, [P, C.POINTER(SolverParams), P, P, C.POINTER(SolveInfo)]),
+    "pfmp_profile_begin": (I, [P]),
+    "pfmp_profile_end": (I, [P, I, C.POINTER(C.c_int64), DP, DP]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libpfmp.so (built in-tree by paper_1609_02652_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1609_02652_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != PFMP_OK:
+        L = lib()
+        msg = L.pfmp_last_error().decode() or L.pfmp_strerror(status).decode()
+        raise PfmpError(status, msg)
+    return status
+
+
+def _ptr(x):
+    """Address of a torch tensor, numpy array or integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+# ---------------------------------------------------------------- same-name wrappers
+def pfmp_ctx_create(dims, bc_t=-1, stream=None):
+    h = P()
+    d = (I * 4)(*dims)
+    check(lib().pfmp_ctx_create(C.byref(h), d, int(bc_t), stream))
+    return h
+
+
+def pfmp_ctx_destroy(ctx):
+    check(lib().pfmp_ctx_destroy(ctx))
+
+
+def pfmp_ctx_set_stream(ctx, stream):
+    check(lib().pfmp_ctx_set_stream(ctx, stream))
+
+
+def pfmp_half_volume(ctx):
+    return int(lib().pfmp_half_volume(ctx))
+
+
+def pfmp_spinor_bytes(ctx, prec):
+    return int(lib().pfmp_spinor_bytes(ctx, prec))
+
+
+def pfmp_gauge_set(ctx, U, where):
+    check(lib().pfmp_gauge_set(ctx, _ptr(U), where))
+
+
+def pfmp_gauge_get(ctx, U, where):
+    check(lib().pfmp_gauge_get(ctx, _ptr(U), where))
+
+
+def pfmp_gauge_from_algebra(ctx, h, eps, where):
+    check(lib().pfmp_gauge_from_algebra(ctx, _ptr(h), float(eps), where))
+
+
+def pfmp_plaquette(ctx):
+    v = C.c_double()
+    check(lib().pfmp_plaquette(ctx, C.byref(v)))
+    return v.value
+
+
+def pfmp_spinor_pack(ctx, dst, prec, src, where, parity):
+    check(lib().pfmp_spinor_pack(ctx, _ptr(dst), prec, _ptr(src), where, parity))
+
+
+def pfmp_spinor_unpack(ctx, dst, where, src, prec, parity):
+    check(lib().pfmp_spinor_unpack(ctx, _ptr(dst), where, _ptr(src), prec, parity))
+
+
+def pfmp_op_create(ctx, kappa, csw):
+    h = P()
+    check(lib().pfmp_op_create(ctx, float(kappa), float(csw), C.byref(h)))
+    return h
+
+
+def pfmp_op_update(op):
+    check(lib().pfmp_op_update(op))
+
+
+def pfmp_op_destroy(op):
+    check(lib().pfmp_op_destroy(op))
+
+
+def pfmp_op_logdet(op):
+    v = C.c_double()
+    check(lib().pfmp_op_logdet(op, C.byref(v)))
+    return v.value
+
+
+def pfmp_dslash(op, prec, out, inp, out_parity, dagger=0):
+    check(lib().pfmp_dslash(op, prec, _ptr(out), _ptr(inp), out_parity, dagger))
+
+
+def pfmp_clover_apply(op, prec, out, inp, parity, inverse):
+    check(lib().pfmp_clover_apply(op, prec, _ptr(out), _ptr(inp), parity, inverse))
+
+
+def pfmp_mhat(op, prec, out, inp, dagger=0):
+    check(lib().pfmp_mhat(op, prec, _ptr(out), _ptr(inp), dagger))
+
+
+def pfmp_kop(op, prec, out, inp, want_norm=False):
+    v = C.c_double()
+    check(lib().pfmp_kop(op, prec, _ptr(out), _ptr(inp), C.byref(v) if want_norm else None))
+    return v.value if want_norm else None
+
+
+def pfmp_norm2(ctx, prec, x):
+    v = C.c_double()
+    check(lib().pfmp_norm2(ctx, prec, _ptr(x), C.byref(v)))
+    return v.value
+
+
+def pfmp_cdot(ctx, prec, x, y):
+    v = (C.c_double * 2)()
+    check(lib().pfmp_cdot(ctx, prec, _ptr(x), _ptr(y), v))
+    return complex(v[0], v[1])
+
+
+def pfmp_axpy(ctx, prec, a, x, y):
+    a = complex(a)
+    check(lib().pfmp_axpy(ctx, prec, a.real, a.imag, _ptr(x), _ptr(y)))
+
+
+def pfmp_convert(ctx, dst, dst_prec, src, src_prec):
+    check(lib().pfmp_convert(ctx, _ptr(dst), dst_prec, _ptr(src), src_prec))
+
+
+def pfmp_solve(op, params, x, b, raise_on_error=True):
+    info = SolveInfo()
+    st = lib().pfmp_solve(op, C.byref(params), _ptr(x), _ptr(b), C.byref(info))
+    if raise_on_error:
+        check(st)
+    return info
+
+
+def pfmp_solve_host(op, params, x_host, b_host, raise_on_error=True):
+    info = SolveInfo()
+    st = lib().pfmp_solve_host(op, C.byref(params), _ptr(x_host), _ptr(b_host), C.byref(info))
+    if raise_on_error:
+        check(st)
+    return info
+
+
+def pfmp_profile_begin(ctx):
+    check(lib().pfmp_profile_begin(ctx))
+
+
+def pfmp_profile_end(ctx, kernel_class):
+    n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+    check(lib().pfmp_profile_end(ctx, kernel_class, C.byref(n), C.byref(ms), C.byref(by)))
+    return n.value, ms.value, by.value
+
+
+def pfmp_launch_count():
+    return int(lib().pfmp_launch_count())

@@ -1,0 +1,346 @@
+// extern "C" entry points: argument checks, exception-to-status translation, and the
+// small amount of orchestration each call needs.  See include/pfmp.h for the contract.
+#include <cstring>
+#include <new>
+
+#include "context.h"
+
+namespace pfmp {
+const char* last_error();
+pfmp_ctx* ctx_create(const int dims[4], int bc_t, void* stream);
+void ctx_destroy(pfmp_ctx* c);
+void gauge_set(pfmp_ctx* c, const double* U, int where);
+void gauge_get(pfmp_ctx* c, double* U, int where);
+void gauge_from_algebra(pfmp_ctx* c, const double* h, double eps, int where);
+double plaquette(pfmp_ctx* c);
+void spinor_pack_any(pfmp_ctx* c, void* dst, int prec, const double* src, int where, int parity);
+void spinor_unpack_any(pfmp_ctx* c, double* dst, int where, const void* src, int prec, int parity);
+void profile_begin(pfmp_ctx* c);
+long long launch_count();
+void profile_end(pfmp_ctx* c, int cls, long* launches, double* ms, double* bytes);
+}  // namespace pfmp
+
+using namespace pfmp;
+
+#define API_BEGIN \
+  try {           \
+    set_last_error("");
+#define API_END                                         \
+  }                                                     \
+  catch (const Err& e) {                                \
+    return e.code;                                      \
+  }                                                     \
+  catch (const std::bad_alloc&) {                       \
+    set_last_error("host allocation failed");           \
+    return PFMP_E_NOMEM;                                \
+  }                                                     \
+  catch (...) {                                         \
+    set_last_error("unexpected C++ exception");         \
+    return PFMP_E_INVALID;                              \
+  }                                                     \
+  return PFMP_OK;
+
+static void check_prec(int prec) { PFMP_REQUIRE(prec == PFMP_F64 || prec == PFMP_F32, PFMP_E_INVALID, "bad precision"); }
+static void check_where(int w) { PFMP_REQUIRE(w == PFMP_HOST || w == PFMP_DEVICE, PFMP_E_INVALID, "bad location"); }
+
+static void op_free(pfmp_op* op) {
+  if (!op) return;
+  for (int p = 0; p < 2; ++p) {
+    dev_free(op->clov64[p]);
+    dev_free(op->clov32[p]);
+  }
+  dev_free(op->t64);
+  dev_free(op->t32);
+  dev_free(op->e64);
+  dev_free(op->e32);
+  for (int k = 0; k < 6; ++k) dev_free(op->cg64[k]);
+  for (int k = 0; k < 4; ++k) dev_free(op->cg32[k]);
+  dev_free(op->scal);
+  if (op->h_scal) cudaFreeHost(op->h_scal);
+  delete op;
+}
+
+extern "C" {
+
+const char* pfmp_strerror(int s) {
+  switch (s) {
+    case PFMP_OK: return "ok";
+    case PFMP_E_INVALID: return "invalid argument";
+    case PFMP_E_NOMEM: return "out of memory";
+    case PFMP_E_CUDA: return "CUDA error";
+    case PFMP_E_NOT_CONVERGED: return "solver did not converge";
+    case PFMP_E_TIMEOUT: return "bounded device wait timed out";
+    case PFMP_E_NAN: return "NaN or Inf encountered";
+    case PFMP_E_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* pfmp_last_error(void) { return last_error(); }
+int pfmp_version(void) { return 100; }
+int64_t pfmp_launch_count(void) { return (int64_t)launch_count(); }
+
+int pfmp_ctx_create(pfmp_ctx** ctx, const int dims[4], int bc_t, void* stream) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && dims, PFMP_E_INVALID, "null argument");
+  *ctx = ctx_create(dims, bc_t, stream);
+  API_END
+}
+
+int pfmp_ctx_destroy(pfmp_ctx* ctx) {
+  API_BEGIN
+  ctx_destroy(ctx);
+  API_END
+}
+
+int pfmp_ctx_set_stream(pfmp_ctx* ctx, void* stream) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx, PFMP_E_INVALID, "null context");
+  ctx->stream = (cudaStream_t)stream;
+  API_END
+}
+
+int64_t pfmp_half_volume(const pfmp_ctx* ctx) { return ctx ? ctx->g.Vh : -1; }
+int64_t pfmp_spinor_bytes(const pfmp_ctx* ctx, int prec) {
+  if (!ctx || (prec != PFMP_F64 && prec != PFMP_F32)) return -1;
+  return (int64_t)spinor_bytes(ctx->g, prec);
+}
+
+int pfmp_gauge_set(pfmp_ctx* ctx, const double* U, int where) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && U, PFMP_E_INVALID, "null argument");
+  check_where(where);
+  gauge_set(ctx, U, where);
+  API_END
+}
+
+int pfmp_gauge_get(pfmp_ctx* ctx, double* U, int where) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && U, PFMP_E_INVALID, "null argument");
+  check_where(where);
+  gauge_get(ctx, U, where);
+  API_END
+}
+
+int pfmp_gauge_from_algebra(pfmp_ctx* ctx, const double* h, double eps, int where) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && h, PFMP_E_INVALID, "null argument");
+  check_where(where);
+  gauge_from_algebra(ctx, h, eps, where);
+  API_END
+}
+
+int pfmp_plaquette(pfmp_ctx* ctx, double* plaq) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && plaq, PFMP_E_INVALID, "null argument");
+  *plaq = plaquette(ctx);
+  API_END
+}
+
+int pfmp_spinor_pack(pfmp_ctx* ctx, void* dst, int prec, const double* src, int where, int parity) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && dst && src && (parity == 0 || parity == 1), PFMP_E_INVALID, "bad argument");
+  check_prec(prec);
+  check_where(where);
+  spinor_pack_any(ctx, dst, prec, src, where, parity);
+  API_END
+}
+
+int pfmp_spinor_unpack(pfmp_ctx* ctx, double* dst, int where, const void* src, int prec, int parity) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && dst && src && (parity == 0 || parity == 1), PFMP_E_INVALID, "bad argument");
+  check_prec(prec);
+  check_where(where);
+  spinor_unpack_any(ctx, dst, where, src, prec, parity);
+  API_END
+}
+
+int pfmp_op_create(pfmp_ctx* ctx, double kappa, double csw, pfmp_op** out) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && out, PFMP_E_INVALID, "null argument");
+  PFMP_REQUIRE(kappa > 0 && csw >= 0, PFMP_E_INVALID, "kappa must be > 0 and c_sw >= 0");
+  pfmp_op* op = new pfmp_op();
+  op->ctx = ctx;
+  op->kappa = kappa;
+  op->csw = csw;
+  try {
+    const Geom& g = ctx->g;
+    for (int p = 0; p < 2; ++p) {
+      op->clov64[p] = (double2*)dev_alloc((size_t)g.Vh * 36 * sizeof(double2));
+      op->clov32[p] = (float4*)dev_alloc((size_t)g.Vh * 18 * sizeof(float4));
+    }
+    op->t64 = (double2*)dev_alloc(spinor_bytes(g, PFMP_F64));
+    op->e64 = (double2*)dev_alloc(spinor_bytes(g, PFMP_F64));
+    op->t32 = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
+    op->e32 = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
+    for (int k = 0; k < 6; ++k) op->cg64[k] = (double2*)dev_alloc(spinor_bytes(g, PFMP_F64));
+    for (int k = 0; k < 4; ++k) op->cg32[k] = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
+    op->scal = (CGScalars*)dev_alloc(sizeof(CGScalars));
+    PFMP_CUDA(cudaMallocHost(&op->h_scal, sizeof(CGScalars)));
+    clover_build(op);
+  } catch (...) {
+    op_free(op);
+    throw;
+  }
+  *out = op;
+  API_END
+}
+
+int pfmp_op_update(pfmp_op* op) {
+  API_BEGIN
+  PFMP_REQUIRE(op, PFMP_E_INVALID, "null operator");
+  clover_build(op);
+  API_END
+}
+
+int pfmp_op_destroy(pfmp_op* op) {
+  API_BEGIN
+  if (op) cudaStreamSynchronize(op->ctx->stream);
+  op_free(op);
+  API_END
+}
+
+int pfmp_op_logdet(pfmp_op* op, double* ld) {
+  API_BEGIN
+  PFMP_REQUIRE(op && ld, PFMP_E_INVALID, "null argument");
+  *ld = op->logdet_oo;
+  API_END
+}
+
+int pfmp_dslash(pfmp_op* op, int prec, void* out, const void* in, int out_parity, int dagger) {
+  API_BEGIN
+  PFMP_REQUIRE(op && out && in && out != in && (out_parity == 0 || out_parity == 1), PFMP_E_INVALID, "bad argument");
+  check_prec(prec);
+  hop(op, prec, out, in, out_parity, dagger != 0);
+  API_END
+}
+
+int pfmp_clover_apply(pfmp_op* op, int prec, void* out, const void* in, int parity, int inverse) {
+  API_BEGIN
+  PFMP_REQUIRE(op && out && in, PFMP_E_INVALID, "null argument");
+  PFMP_REQUIRE((parity == 0 && !inverse) || (parity == 1 && inverse), PFMP_E_UNSUPPORTED,
+               "the library keeps A on even sites and A^{-1} on odd sites only");
+  check_prec(prec);
+  clover_mul(op, prec, out, in, parity);
+  API_END
+}
+
+int pfmp_mhat(pfmp_op* op, int prec, void* out, const void* in, int dagger) {
+  API_BEGIN
+  PFMP_REQUIRE(op && out && in && out != in, PFMP_E_INVALID, "bad argument");
+  check_prec(prec);
+  mhat(op, prec, out, in, dagger != 0, nullptr, nullptr);
+  API_END
+}
+
+int pfmp_kop(pfmp_op* op, int prec, void* out, const void* in, double* in_K_in) {
+  API_BEGIN
+  PFMP_REQUIRE(op && out && in && out != in, PFMP_E_INVALID, "bad argument");
+  check_prec(prec);
+  pfmp_ctx* c = op->ctx;
+  kop(op, prec, out, in, in_K_in ? c->d_sums : nullptr, nullptr);
+  if (in_K_in) {
+    PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    PFMP_CUDA(cudaStreamSynchronize(c->stream));
+    *in_K_in = c->h_sums[0];
+  }
+  API_END
+}
+
+int pfmp_norm2(pfmp_ctx* ctx, int prec, const void* x, double* result) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && x && result, PFMP_E_INVALID, "null argument");
+  check_prec(prec);
+  blas_norm2(ctx, prec, x, ctx->d_sums);
+  PFMP_CUDA(cudaMemcpyAsync(ctx->h_sums, ctx->d_sums, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  PFMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  *result = ctx->h_sums[0];
+  API_END
+}
+
+int pfmp_cdot(pfmp_ctx* ctx, int prec, const void* x, const void* y, double result[2]) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && x && y && result, PFMP_E_INVALID, "null argument");
+  check_prec(prec);
+  blas_cdot(ctx, prec, x, y, ctx->d_sums);
+  PFMP_CUDA(cudaMemcpyAsync(ctx->h_sums, ctx->d_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  PFMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  result[0] = ctx->h_sums[0];
+  result[1] = ctx->h_sums[1];
+  API_END
+}
+
+int pfmp_axpy(pfmp_ctx* ctx, int prec, double a_re, double a_im, const void* x, void* y) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && x && y, PFMP_E_INVALID, "null argument");
+  check_prec(prec);
+  blas_axpy(ctx, prec, a_re, a_im, x, y);
+  API_END
+}
+
+int pfmp_convert(pfmp_ctx* ctx, void* dst, int dst_prec, const void* src, int src_prec) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && dst && src, PFMP_E_INVALID, "null argument");
+  check_prec(dst_prec);
+  check_prec(src_prec);
+  blas_copy(ctx, dst, dst_prec, src, src_prec);
+  API_END
+}
+
+static int solve_impl(pfmp_op* op, const pfmp_solver_params* prm, void* x, const void* b, pfmp_solve_info* info) {
+  int iters = 0, rel = 0;
+  double res = 0;
+  long kap = 0;
+  int st = solve(op, prm->method, prm->tol, prm->max_iter, prm->delta, prm->check_every, x, b, &iters, &rel, &res, &kap);
+  if (info) {
+    info->iters = iters;
+    info->reliable_updates = rel;
+    info->true_rel_res = res;
+    info->k_apply = kap;
+    info->status = st;
+  }
+  if (st != PFMP_OK) set_last_error(pfmp_strerror(st));
+  return st;
+}
+
+int pfmp_solve(pfmp_op* op, const pfmp_solver_params* prm, void* x, const void* b, pfmp_solve_info* info) {
+  API_BEGIN
+  PFMP_REQUIRE(op && prm && x && b, PFMP_E_INVALID, "null argument");
+  int st = solve_impl(op, prm, x, b, info);
+  if (st != PFMP_OK) return st;
+  API_END
+}
+
+int pfmp_solve_host(pfmp_op* op, const pfmp_solver_params* prm, double* x_host, const double* b_host,
+                    pfmp_solve_info* info) {
+  API_BEGIN
+  PFMP_REQUIRE(op && prm && x_host && b_host, PFMP_E_INVALID, "null argument");
+  pfmp_ctx* c = op->ctx;
+  // solver workspace slots 3 and 4 hold b and x of a host-memory solve
+  void* b = op->cg64[3];
+  void* x = op->cg64[4];
+  spinor_pack_any(c, b, PFMP_F64, b_host, PFMP_HOST, 0);
+  int st = solve_impl(op, prm, x, b, info);
+  spinor_unpack_any(c, x_host, PFMP_HOST, x, PFMP_F64, 0);
+  if (st != PFMP_OK) return st;
+  API_END
+}
+
+int pfmp_profile_begin(pfmp_ctx* ctx) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx, PFMP_E_INVALID, "null context");
+  profile_begin(ctx);
+  API_END
+}
+
+int pfmp_profile_end(pfmp_ctx* ctx, int cls, int64_t* launches, double* total_ms, double* total_bytes) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && launches && total_ms && total_bytes, PFMP_E_INVALID, "null argument");
+  PFMP_REQUIRE(cls == PFMP_KERNEL_HOP_F32 || cls == PFMP_KERNEL_HOP_F64, PFMP_E_INVALID, "bad kernel class");
+  long n = 0;
+  profile_end(ctx, cls, &n, total_ms, total_bytes);
+  *launches = n;
+  API_END
+}
+
+}  // extern "C"

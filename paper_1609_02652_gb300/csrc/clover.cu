@@ -1,0 +1,214 @@
+// Clover term: field strength from the four plaquette leaves, the two chiral 6x6
+// blocks of A = 1 - kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}, and on odd sites
+// A^{-1} with log det A by Cholesky.  FP64 throughout; the FP32 copy is rounded last.
+//
+// In the chiral gamma basis sigma_{mu nu} = diag(s+, s-) with 2x2 Pauli blocks, so
+//   sum_{mu<nu} sigma F = sum_k s_k (x) X_k,
+//   upper (spins 0,1): X1 = F12 - F03, X2 = F02 + F13, X3 = F01 - F23,
+//   lower (spins 2,3): X1 = F12 + F03, X2 = F02 - F13, X3 = F01 + F23,
+// and each block is 1 - kappa c_sw [[X3, X1 - i X2], [X1 + i X2, -X3]].
+#include <cstring>
+
+#include "context.h"
+#include "fields.cuh"
+
+namespace pfmp {
+
+__device__ __forceinline__ Mat3<double> mlink(const double2* U, const Geom& g, const int x[4], int mu) {
+  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+  Mat3<double> M;
+  load_link18(M, U + (size_t)((p * 4 + mu) * 9) * g.Vh, cb_index(g, x), g.Vh);
+  return M;
+}
+__device__ __forceinline__ void shift(const Geom& g, const int x[4], int mu, int d, int y[4]) {
+  for (int k = 0; k < 4; ++k) y[k] = x[k];
+  y[mu] = (y[mu] + d + g.L[mu]) % g.L[mu];
+}
+
+// F_{mu nu}(x): traceless part of (Q - Q^dag)/(8i), Q = sum of the four leaves at x
+__device__ Mat3<double> field_strength(const double2* U, const Geom& g, const int x[4], int mu, int nu) {
+  int xpm[4], xpn[4], xmm[4], xmn[4], xmmpn[4], xmmmn[4], xpmmn[4];
+  shift(g, x, mu, 1, xpm);
+  shift(g, x, nu, 1, xpn);
+  shift(g, x, mu, -1, xmm);
+  shift(g, x, nu, -1, xmn);
+  shift(g, xmm, nu, 1, xmmpn);
+  shift(g, xmm, nu, -1, xmmmn);
+  shift(g, xpm, nu, -1, xpmmn);
+  const Mat3<double> Um = mlink(U, g, x, mu), Un = mlink(U, g, x, nu);
+  // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+  Mat3<double> Q = matmul_nd(matmul_nd(matmul(Um, mlink(U, g, xpm, nu)), mlink(U, g, xpn, mu)), Un);
+  // leaf 2: U_nu(x) U_mu(x-mu+nu)^dag U_nu(x-mu)^dag U_mu(x-mu)
+  const Mat3<double> Um_xmm = mlink(U, g, xmm, mu);
+  Mat3<double> L = matmul(matmul_nd(matmul_nd(Un, mlink(U, g, xmmpn, mu)), mlink(U, g, xmm, nu)), Um_xmm);
+  Q = mat_add(Q, L);
+  // leaf 3: U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu)
+  {
+    Mat3<double> A = dagger(Um_xmm);
+    A = matmul_nd(A, mlink(U, g, xmmmn, nu));
+    A = matmul(A, mlink(U, g, xmmmn, mu));
+    A = matmul(A, mlink(U, g, xmn, nu));
+    L = A;
+  }
+  Q = mat_add(Q, L);
+  // leaf 4: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x+mu-nu) U_mu(x)^dag
+  {
+    Mat3<double> A = dagger(mlink(U, g, xmn, nu));
+    A = matmul(A, mlink(U, g, xmn, mu));
+    A = matmul(A, mlink(U, g, xpmmn, nu));
+    A = matmul_nd(A, Um);
+    L = A;
+  }
+  Q = mat_add(Q, L);
+  Mat3<double> F;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      cplx<double> d = Q.m[i][j] - conj(Q.m[j][i]);
+      F.m[i][j] = 0.125 * times_mi(d);
+    }
+  const double tr = (F.m[0][0].re + F.m[1][1].re + F.m[2][2].re) / 3.0;
+  for (int i = 0; i < 3; ++i) {
+    F.m[i][i].re -= tr;
+    F.m[i][i].im = 0.0;
+  }
+  return F;
+}
+
+struct CloverOut {
+  double2* A64;   // even: A
+  double2* Ai64;  // odd: A^{-1}
+  float4* A32;
+  float4* Ai32;
+  int* bad;
+};
+
+__device__ void store_block32(float4* f, const HermBlock<double>& b, int blk, int cb, int Vh) {
+  float4* g = f + (size_t)(9 * blk) * Vh;
+  g[cb] = make_float4((float)b.d[0], (float)b.d[1], (float)b.d[2], (float)b.d[3]);
+  g[(size_t)Vh + cb] = make_float4((float)b.d[4], (float)b.d[5], (float)b.o[0].re, (float)b.o[0].im);
+  for (int k = 0; k < 7; ++k)
+    g[(size_t)(2 + k) * Vh + cb] =
+        make_float4((float)b.o[1 + 2 * k].re, (float)b.o[1 + 2 * k].im, (float)b.o[2 + 2 * k].re, (float)b.o[2 + 2 * k].im);
+}
+
+// Cholesky A = L L^dag (6x6 Hermitian positive definite); returns false if not PD.
+__device__ bool cholesky6(const cplx<double> A[6][6], cplx<double> L[6][6], double& logdet) {
+  logdet = 0.0;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) L[i][j] = mk(0.0, 0.0);
+  for (int j = 0; j < 6; ++j) {
+    double d = A[j][j].re;
+    for (int k = 0; k < j; ++k) d -= norm2(L[j][k]);
+    if (!(d > 0.0)) return false;
+    const double ljj = sqrt(d);
+    L[j][j] = mk(ljj, 0.0);
+    logdet += 2.0 * log(ljj);
+    for (int i = j + 1; i < 6; ++i) {
+      cplx<double> s = A[i][j];
+      for (int k = 0; k < j; ++k) s = s - mul_cj(L[i][k], L[j][k]);
+      L[i][j] = (1.0 / ljj) * s;
+    }
+  }
+  return true;
+}
+
+__global__ void k_clover_build(Geom g, const double2* __restrict__ U, double kc, CloverOut out, ReduceBuf rb,
+                               double* logdet_out) {
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  double ld[1] = {0.0};
+  if (cb < g.Vh) {
+    int x[4];
+    cb_coords(g, cb, p, x);
+    Mat3<double> F[6];
+    int k = 0;
+    for (int mu = 0; mu < 4; ++mu)
+      for (int nu = mu + 1; nu < 4; ++nu) F[k++] = field_strength(U, g, x, mu, nu);
+    // F index: 0:(0,1) 1:(0,2) 2:(0,3) 3:(1,2) 4:(1,3) 5:(2,3)
+    HermBlock<double> B[2];
+    for (int blk = 0; blk < 2; ++blk) {
+      const double s = blk == 0 ? -1.0 : 1.0;
+      cplx<double> A[6][6];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          cplx<double> X1 = F[3].m[i][j] + s * F[2].m[i][j];
+          cplx<double> X2 = F[1].m[i][j] - s * F[4].m[i][j];
+          cplx<double> X3 = F[0].m[i][j] + s * F[5].m[i][j];
+          const double one = (i == j) ? 1.0 : 0.0;
+          A[i][j] = mk(one, 0.0) - kc * X3;
+          A[i + 3][j + 3] = mk(one, 0.0) + kc * X3;
+          A[i][j + 3] = -kc * (X1 - times_i(X2));
+          A[i + 3][j] = -kc * (X1 + times_i(X2));
+        }
+      if (p == 0) {
+        for (int i = 0; i < 6; ++i) B[blk].d[i] = A[i][i].re;
+        for (int i = 1; i < 6; ++i)
+          for (int j = 0; j < i; ++j) B[blk].o[tri_index(i, j)] = A[i][j];
+      } else {
+        cplx<double> L[6][6];
+        double l;
+        if (!cholesky6(A, L, l)) {
+          atomicExch(out.bad, 1);
+          l = 0.0;
+          for (int i = 0; i < 6; ++i) L[i][i] = mk(1.0, 0.0);
+        }
+        ld[0] += l;
+        // Linv = L^{-1} (lower triangular), A^{-1} = Linv^dag Linv
+        cplx<double> Li[6][6];
+        for (int i = 0; i < 6; ++i)
+          for (int j = 0; j < 6; ++j) Li[i][j] = mk(0.0, 0.0);
+        for (int j = 0; j < 6; ++j) {
+          Li[j][j] = mk(1.0 / L[j][j].re, 0.0);
+          for (int i = j + 1; i < 6; ++i) {
+            cplx<double> s2 = mk(0.0, 0.0);
+            for (int kk = j; kk < i; ++kk) s2 = s2 + L[i][kk] * Li[kk][j];
+            Li[i][j] = (-1.0 / L[i][i].re) * s2;
+          }
+        }
+        for (int i = 0; i < 6; ++i)
+          for (int j = 0; j <= i; ++j) {
+            cplx<double> s2 = mk(0.0, 0.0);
+            for (int kk = i; kk < 6; ++kk) s2 = s2 + cj_mul(Li[kk][i], Li[kk][j]);
+            if (i == j)
+              B[blk].d[i] = s2.re;
+            else
+              B[blk].o[tri_index(i, j)] = s2;
+          }
+      }
+    }
+    if (p == 0) {
+      store_clover(out.A64, B, cb, g.Vh);
+      store_block32(out.A32, B[0], 0, cb, g.Vh);
+      store_block32(out.A32, B[1], 1, cb, g.Vh);
+    } else {
+      store_clover(out.Ai64, B, cb, g.Vh);
+      store_block32(out.Ai32, B[0], 0, cb, g.Vh);
+      store_block32(out.Ai32, B[1], 1, cb, g.Vh);
+    }
+  }
+  double tot[1];
+  if (grid_sum<1>(ld, rb, tot)) *logdet_out = tot[0];
+}
+
+void clover_build(pfmp_op* op) {
+  pfmp_ctx* c = op->ctx;
+  CloverOut o;
+  o.A64 = op->clov64[0];
+  o.Ai64 = op->clov64[1];
+  o.A32 = op->clov32[0];
+  o.Ai32 = op->clov32[1];
+  o.bad = (int*)(c->d_sums + 8);
+  PFMP_CUDA(cudaMemsetAsync(o.bad, 0, sizeof(int), c->stream));
+  dim3 grid(nblocks(c->g.Vh, 128), 2);
+  k_clover_build<<<grid, 128, 0, c->stream>>>(c->g, c->U64, op->kappa * op->csw, o, c->rb, c->d_sums);
+  PFMP_CHECK_LAUNCH();
+  PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, 9 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PFMP_CUDA(cudaStreamSynchronize(c->stream));
+  int bad;
+  memcpy(&bad, c->h_sums + 8, sizeof(int));
+  PFMP_REQUIRE(bad == 0, PFMP_E_NAN, "clover block not positive definite (A has a non-positive eigenvalue)");
+  op->logdet_oo = c->h_sums[0];
+  op->built_version = c->gauge_version;
+}
+
+}  // namespace pfmp

@@ -1,0 +1,121 @@
+// Host-side definitions of the library's opaque handles and of the internal entry
+// points the C-ABI wrappers (capi.cu) call.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "pfmp_internal.cuh"
+#include "reduce.cuh"
+
+namespace pfmp {
+
+// device scalars of one solver instance (written by reduction finishers)
+struct CGScalars {
+  double rr;        // current |r|^2
+  double rr_new;
+  double pAp;
+  double alpha;
+  double beta;
+  double stop_rr;   // stop the device loop once rr < stop_rr
+  int done;        // every CG kernel returns at once when set
+  int done_next;   // raised by the x/r update, copied to done after the p update
+  int iter;
+};
+
+}  // namespace pfmp
+
+namespace pfmp {
+// CUDA-event timing of the stencil kernels (off unless pfmp_profile_begin was called)
+struct KernelProfile {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;   // reusable events
+  size_t used = 0;
+  struct Rec {
+    int cls;
+    double bytes;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+};
+}  // namespace pfmp
+
+struct pfmp_ctx {
+  pfmp::Geom g;
+  pfmp::KernelProfile prof;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  double2* U64 = nullptr;    // master [2][4][9][Vh]
+  double2* U64c = nullptr;   // compressed [2][4][6][Vh]
+  float4* U32 = nullptr;     // compressed [2][4][3][Vh]
+  pfmp::ReduceBuf rb{};
+  double* d_sums = nullptr;  // [8] results of generic reductions
+  double* h_sums = nullptr;  // pinned mirror
+  double* canon = nullptr;   // canonical full-lattice scratch (V*24 doubles)
+  long gauge_version = 0;
+};
+
+struct pfmp_op {
+  pfmp_ctx* ctx = nullptr;
+  double kappa = 0, csw = 0;
+  double2* clov64[2] = {nullptr, nullptr};  // [0]: A on even sites, [1]: A^{-1} on odd sites
+  float4* clov32[2] = {nullptr, nullptr};
+  double logdet_oo = 0;
+  long built_version = -1;
+  // workspace (odd temporaries and even scratch)
+  double2* t64 = nullptr;
+  float4* t32 = nullptr;
+  double2* e64 = nullptr;
+  float4* e32 = nullptr;
+  double2* cg64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // r p Ap | b x (host solve) | spare
+  float4* cg32[4] = {nullptr, nullptr, nullptr, nullptr};
+  pfmp::CGScalars* scal = nullptr;
+  pfmp::CGScalars* h_scal = nullptr;
+};
+
+namespace pfmp {
+
+inline size_t spinor_bytes(const Geom& g, int prec) { return (size_t)g.Vh * 24 * (prec == PFMP_F64 ? 8 : 4); }
+void* dev_alloc(size_t bytes);
+void dev_free(void* p);
+
+// core.cu
+void gauge_refresh_compressed(pfmp_ctx* c);
+void spinor_pack(pfmp_ctx* c, void* dst, int prec, const double* src_dev, int parity);
+void spinor_unpack(pfmp_ctx* c, double* dst_dev, const void* src, int prec, int parity);
+
+// clover.cu
+void clover_build(pfmp_op* op);
+
+// profiling (core.cu): bracket one launch with events when profiling is on
+void prof_start(pfmp_ctx* c, cudaEvent_t* a);
+void prof_stop(pfmp_ctx* c, int cls, double bytes, cudaEvent_t a);
+
+// dslash.cu
+void hop(pfmp_op* op, int prec, void* out, const void* in, int out_parity, bool dagger);
+void clover_mul(pfmp_op* op, int prec, void* out, const void* in, int parity);
+// out = M-hat in (or dagger); if pAp != nullptr the finisher of the second kernel
+// stores ||out||^2 into *pAp (device scalar) and, when scal != nullptr, alpha = rr/pAp
+void mhat(pfmp_op* op, int prec, void* out, const void* in, bool dagger, double* norm_out,
+          CGScalars* scal);
+void kop(pfmp_op* op, int prec, void* out, const void* in, double* pKp_dev, CGScalars* scal);
+
+// blas.cu
+void blas_zero(pfmp_ctx* c, int prec, void* x);
+void blas_copy(pfmp_ctx* c, void* dst, int dprec, const void* src, int sprec);
+void blas_axpy(pfmp_ctx* c, int prec, double are, double aim, const void* x, void* y);
+void blas_norm2(pfmp_ctx* c, int prec, const void* x, double* out_dev);
+void blas_cdot(pfmp_ctx* c, int prec, const void* x, const void* y, double* out_dev);
+// r = b - Ax (F64), returns |r|^2 into out_dev
+void blas_xmy_norm(pfmp_ctx* c, const void* b, const void* Ax, void* r, double* out_dev);
+// CG steps (device scalars)
+void cg_step_xr(pfmp_ctx* c, int prec, void* x, void* r, const void* p, const void* Ap, CGScalars* s);
+void cg_step_p(pfmp_ctx* c, int prec, void* p, const void* r, CGScalars* s);
+// x64 += x32 (accumulate the sloppy solution)
+void blas_add_lo(pfmp_ctx* c, void* x64, const void* x32);
+
+// solver.cu
+int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int check_every, void* x,
+          const void* b, int* iters, int* rel_updates, double* true_res, long* kapply);
+
+}  // namespace pfmp

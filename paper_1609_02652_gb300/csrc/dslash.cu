@@ -1,0 +1,343 @@
+// Wilson hop (the dslash), clover multiply, and the fused even-odd operator
+// M-hat = A_ee - kappa^2 H_eo A_oo^{-1} H_oe and K = M-hat^dag M-hat.
+//
+// One thread per output site.  Each thread spin-projects its 8 neighbours to
+// two-component half spinors (the projectors (1 -+ g_mu) have rank 2), multiplies by
+// the link (FP32: 12-real links, third row rebuilt in registers), and rebuilds the
+// four-component result.  Two fused epilogues make M-hat a two-kernel operation:
+//   EPI_CLOV  out = C (H in)            (odd sites: C = A_oo^{-1})
+//   EPI_XPAY  out = C x + coef (H in)   (even sites: C = A_ee, x the local input), with
+//             an optional grid reduction of ||out||^2 feeding the CG scalars.
+// M-hat^dag uses the adjoint hop (projector signs swapped): A is Hermitian, so
+// M-hat^dag = A_ee - kappa^2 H^dag_eo A_oo^{-1} H^dag_oe.
+#include "context.h"
+#include "fields.cuh"
+
+namespace pfmp {
+
+enum { EPI_PLAIN = 0, EPI_CLOV = 1, EPI_XPAY = 2 };
+
+template <int PREC>
+struct HopParams {
+  using vec = typename Prec<PREC>::vec;
+  Geom g;
+  int p;  // output parity
+  vec* out;
+  const vec* in;     // parity 1 - p
+  const vec* gauge;  // [2][4][link_vecs][Vh]
+  const vec* clov;   // clover blocks of parity p (EPI_CLOV, EPI_XPAY)
+  const vec* x;      // local input of parity p (EPI_XPAY)
+  double coef;
+  ReduceBuf rb;
+  double* norm_out;  // ||out||^2 (device) when reducing
+  CGScalars* scal;   // optional: alpha = rr / ||out||^2; skip all work once done
+};
+
+// ---------------------------------------------------------------- spin projection
+// half spinor of (1 + S g_MU) psi, and the rebuild of the full result from it
+template <int MU, int S, typename T>
+__device__ __forceinline__ Half<T> project(const Spinor<T>& p) {
+  Half<T> h;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (MU == 0) {
+      h.h[0][c] = S > 0 ? p.s[0][c] + times_i(p.s[3][c]) : p.s[0][c] - times_i(p.s[3][c]);
+      h.h[1][c] = S > 0 ? p.s[1][c] + times_i(p.s[2][c]) : p.s[1][c] - times_i(p.s[2][c]);
+    } else if (MU == 1) {
+      h.h[0][c] = S > 0 ? p.s[0][c] - p.s[3][c] : p.s[0][c] + p.s[3][c];
+      h.h[1][c] = S > 0 ? p.s[1][c] + p.s[2][c] : p.s[1][c] - p.s[2][c];
+    } else if (MU == 2) {
+      h.h[0][c] = S > 0 ? p.s[0][c] + times_i(p.s[2][c]) : p.s[0][c] - times_i(p.s[2][c]);
+      h.h[1][c] = S > 0 ? p.s[1][c] - times_i(p.s[3][c]) : p.s[1][c] + times_i(p.s[3][c]);
+    } else {
+      h.h[0][c] = S > 0 ? p.s[0][c] + p.s[2][c] : p.s[0][c] - p.s[2][c];
+      h.h[1][c] = S > 0 ? p.s[1][c] + p.s[3][c] : p.s[1][c] - p.s[3][c];
+    }
+  }
+  return h;
+}
+
+template <int MU, int S, typename T>
+__device__ __forceinline__ void accumulate(Spinor<T>& a, const Half<T>& h) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    a.s[0][c] = a.s[0][c] + h.h[0][c];
+    a.s[1][c] = a.s[1][c] + h.h[1][c];
+    if (MU == 0) {  // r2 = -S i h1, r3 = -S i h0
+      a.s[2][c] = S > 0 ? a.s[2][c] + times_mi(h.h[1][c]) : a.s[2][c] + times_i(h.h[1][c]);
+      a.s[3][c] = S > 0 ? a.s[3][c] + times_mi(h.h[0][c]) : a.s[3][c] + times_i(h.h[0][c]);
+    } else if (MU == 1) {  // r2 = S h1, r3 = -S h0
+      a.s[2][c] = S > 0 ? a.s[2][c] + h.h[1][c] : a.s[2][c] - h.h[1][c];
+      a.s[3][c] = S > 0 ? a.s[3][c] - h.h[0][c] : a.s[3][c] + h.h[0][c];
+    } else if (MU == 2) {  // r2 = -S i h0, r3 = S i h1
+      a.s[2][c] = S > 0 ? a.s[2][c] + times_mi(h.h[0][c]) : a.s[2][c] + times_i(h.h[0][c]);
+      a.s[3][c] = S > 0 ? a.s[3][c] + times_i(h.h[1][c]) : a.s[3][c] + times_mi(h.h[1][c]);
+    } else {  // r2 = S h0, r3 = S h1
+      a.s[2][c] = S > 0 ? a.s[2][c] + h.h[0][c] : a.s[2][c] - h.h[0][c];
+      a.s[3][c] = S > 0 ? a.s[3][c] + h.h[1][c] : a.s[3][c] - h.h[1][c];
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ Half<T> mul_half(const Mat3<T>& U, const Half<T>& h) {
+  Half<T> r;
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) r.h[k][i] = U.m[i][0] * h.h[k][0] + U.m[i][1] * h.h[k][1] + U.m[i][2] * h.h[k][2];
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ Half<T> mul_half_dag(const Mat3<T>& U, const Half<T>& h) {
+  Half<T> r;
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      r.h[k][i] = cj_mul(U.m[0][i], h.h[k][0]) + cj_mul(U.m[1][i], h.h[k][1]) + cj_mul(U.m[2][i], h.h[k][2]);
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ void scale_half(Half<T>& h, T s) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) h.h[k][i] = s * h.h[k][i];
+}
+
+// forward (x+mu, projector 1 + SF g) and backward (x-mu, projector 1 - SF g) terms
+template <int PREC, int MU, int SF>
+__device__ __forceinline__ void hop_dir(Spinor<typename Prec<PREC>::real>& acc, const HopParams<PREC>& a,
+                                        const int x[4], int cb) {
+  using T = typename Prec<PREC>::real;
+  constexpr int LV = Prec<PREC>::link_vecs;
+  const Geom& g = a.g;
+  const int Vh = g.Vh;
+  {
+    const int n = nbr_cb(g, x, MU, +1);
+    Spinor<T> psi;
+    load_spinor(psi, a.in, n, Vh);
+    Half<T> h = project<MU, SF>(psi);
+    Mat3<T> U;
+    load_link(U, a.gauge + (size_t)((a.p * 4 + MU) * LV) * Vh, cb, Vh);
+    Half<T> r = mul_half(U, h);
+    if (MU == 3 && x[3] == g.L[3] - 1) scale_half(r, (T)g.bc_t);
+    accumulate<MU, SF>(acc, r);
+  }
+  {
+    const int n = nbr_cb(g, x, MU, -1);
+    Spinor<T> psi;
+    load_spinor(psi, a.in, n, Vh);
+    Half<T> h = project<MU, -SF>(psi);
+    Mat3<T> U;
+    load_link(U, a.gauge + (size_t)(((1 - a.p) * 4 + MU) * LV) * Vh, n, Vh);
+    Half<T> r = mul_half_dag(U, h);
+    if (MU == 3 && x[3] == 0) scale_half(r, (T)g.bc_t);
+    accumulate<MU, -SF>(acc, r);
+  }
+}
+
+template <int PREC, bool DAG, int EPI, bool REDUCE>
+__global__ void __launch_bounds__(128) k_hop(HopParams<PREC> a) {
+  using T = typename Prec<PREC>::real;
+  if (a.scal && a.scal->done) return;
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  double nrm[1] = {0.0};
+  if (cb < a.g.Vh) {
+    int x[4];
+    cb_coords(a.g, cb, a.p, x);
+    Spinor<T> acc;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc.s[s][c] = mk<T>(0, 0);
+    constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF g_mu
+    hop_dir<PREC, 0, SF>(acc, a, x, cb);
+    hop_dir<PREC, 1, SF>(acc, a, x, cb);
+    hop_dir<PREC, 2, SF>(acc, a, x, cb);
+    hop_dir<PREC, 3, SF>(acc, a, x, cb);
+    Spinor<T> out;
+    if (EPI == EPI_PLAIN) {
+      const T cf = (T)a.coef;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out.s[s][c] = cf * acc.s[s][c];
+    } else if (EPI == EPI_CLOV) {
+      HermBlock<T> B[2];
+      load_clover(B, a.clov, cb, a.g.Vh);
+      out = clover_apply(B, acc);
+      const T cf = (T)a.coef;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out.s[s][c] = cf * out.s[s][c];
+    } else {
+      HermBlock<T> B[2];
+      load_clover(B, a.clov, cb, a.g.Vh);
+      Spinor<T> xl;
+      load_spinor(xl, a.x, cb, a.g.Vh);
+      out = clover_apply(B, xl);
+      const T cf = (T)a.coef;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out.s[s][c] = out.s[s][c] + cf * acc.s[s][c];
+    }
+    store_spinor(a.out, out, cb, a.g.Vh);
+    if (REDUCE) {
+      double t = 0;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) t += (double)norm2(out.s[s][c]);
+      nrm[0] = t;
+    }
+  }
+  if (REDUCE) {
+    double tot[1];
+    if (grid_sum<1>(nrm, a.rb, tot)) {
+      *a.norm_out = tot[0];
+      if (a.scal) a.scal->alpha = a.scal->rr / tot[0];
+    }
+  }
+}
+
+template <int PREC>
+__global__ void k_clover_mul(Geom g, typename Prec<PREC>::vec* out, const typename Prec<PREC>::vec* in,
+                             const typename Prec<PREC>::vec* clov) {
+  using T = typename Prec<PREC>::real;
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  HermBlock<T> B[2];
+  load_clover(B, clov, cb, g.Vh);
+  Spinor<T> x;
+  load_spinor(x, in, cb, g.Vh);
+  store_spinor(out, clover_apply(B, x), cb, g.Vh);
+}
+
+// ---------------------------------------------------------------- host drivers
+constexpr int kHopBlock = 128;
+
+template <int PREC>
+static HopParams<PREC> params(pfmp_op* op, int p, void* out, const void* in) {
+  using vec = typename Prec<PREC>::vec;
+  HopParams<PREC> a;
+  a.g = op->ctx->g;
+  a.p = p;
+  a.out = (vec*)out;
+  a.in = (const vec*)in;
+  a.gauge = PREC == PFMP_F64 ? (const vec*)(const void*)op->ctx->U64c : (const vec*)(const void*)op->ctx->U32;
+  a.clov = nullptr;
+  a.x = nullptr;
+  a.coef = 1.0;
+  a.rb = op->ctx->rb;
+  a.norm_out = nullptr;
+  a.scal = nullptr;
+  return a;
+}
+
+// algorithmic bytes of one launch: per output site 8 links (12 reals), one input spinor
+// (each neighbour read once with ideal reuse), the output spinor, plus the clover
+// blocks (72 reals) and for EPI_XPAY the local input spinor
+template <int PREC>
+static double hop_bytes(int epi, int Vh) {
+  const double reals = 8 * 12 + 24 + 24 + (epi >= EPI_CLOV ? 72 : 0) + (epi == EPI_XPAY ? 24 : 0);
+  return reals * (PREC == PFMP_F64 ? 8 : 4) * (double)Vh;
+}
+
+template <int PREC, bool DAG, int EPI, bool RED>
+static void launch(const HopParams<PREC>& a, pfmp_ctx* c) {
+  cudaEvent_t ev;
+  prof_start(c, &ev);
+  k_hop<PREC, DAG, EPI, RED><<<nblocks(a.g.Vh, kHopBlock), kHopBlock, 0, c->stream>>>(a);
+  PFMP_CHECK_LAUNCH();
+  prof_stop(c, PREC == PFMP_F64 ? PFMP_KERNEL_HOP_F64 : PFMP_KERNEL_HOP_F32, hop_bytes<PREC>(EPI, a.g.Vh), ev);
+}
+
+template <int PREC>
+static const typename Prec<PREC>::vec* clov_ptr(pfmp_op* op, int parity) {
+  if (PREC == PFMP_F64) return (const typename Prec<PREC>::vec*)(const void*)op->clov64[parity];
+  return (const typename Prec<PREC>::vec*)(const void*)op->clov32[parity];
+}
+
+static void require_clover(pfmp_op* op) {
+  PFMP_REQUIRE(op->built_version == op->ctx->gauge_version, PFMP_E_INVALID,
+               "gauge field changed since the clover term was built: call pfmp_op_update");
+}
+
+template <int PREC>
+static void hop_t(pfmp_op* op, void* out, const void* in, int p, bool dagger) {
+  auto a = params<PREC>(op, p, out, in);
+  if (dagger)
+    launch<PREC, true, EPI_PLAIN, false>(a, op->ctx);
+  else
+    launch<PREC, false, EPI_PLAIN, false>(a, op->ctx);
+}
+
+void hop(pfmp_op* op, int prec, void* out, const void* in, int out_parity, bool dagger) {
+  if (prec == PFMP_F64)
+    hop_t<PFMP_F64>(op, out, in, out_parity, dagger);
+  else
+    hop_t<PFMP_F32>(op, out, in, out_parity, dagger);
+}
+
+void clover_mul(pfmp_op* op, int prec, void* out, const void* in, int parity) {
+  require_clover(op);
+  const Geom& g = op->ctx->g;
+  if (prec == PFMP_F64)
+    k_clover_mul<PFMP_F64><<<nblocks(g.Vh), kBlock, 0, op->ctx->stream>>>(g, (double2*)out, (const double2*)in,
+                                                                            clov_ptr<PFMP_F64>(op, parity));
+  else
+    k_clover_mul<PFMP_F32><<<nblocks(g.Vh), kBlock, 0, op->ctx->stream>>>(g, (float4*)out, (const float4*)in,
+                                                                            clov_ptr<PFMP_F32>(op, parity));
+  PFMP_CHECK_LAUNCH();
+}
+
+template <int PREC>
+static void mhat_t(pfmp_op* op, void* out, const void* in, bool dagger, double* norm_out, CGScalars* scal) {
+  void* t = PREC == PFMP_F64 ? (void*)op->t64 : (void*)op->t32;
+  pfmp_ctx* s = op->ctx;
+  // t = A_oo^{-1} H_oe in
+  auto a1 = params<PREC>(op, 1, t, in);
+  a1.clov = clov_ptr<PREC>(op, 1);
+  a1.scal = scal;
+  // out = A_ee in - kappa^2 H_eo t
+  auto a2 = params<PREC>(op, 0, out, t);
+  a2.clov = clov_ptr<PREC>(op, 0);
+  a2.x = (const typename Prec<PREC>::vec*)in;
+  a2.coef = -op->kappa * op->kappa;
+  a2.norm_out = norm_out;
+  a2.scal = scal;
+  if (dagger) {
+    launch<PREC, true, EPI_CLOV, false>(a1, s);
+    if (norm_out)
+      launch<PREC, true, EPI_XPAY, true>(a2, s);
+    else
+      launch<PREC, true, EPI_XPAY, false>(a2, s);
+  } else {
+    launch<PREC, false, EPI_CLOV, false>(a1, s);
+    if (norm_out)
+      launch<PREC, false, EPI_XPAY, true>(a2, s);
+    else
+      launch<PREC, false, EPI_XPAY, false>(a2, s);
+  }
+}
+
+void mhat(pfmp_op* op, int prec, void* out, const void* in, bool dagger, double* norm_out, CGScalars* scal) {
+  require_clover(op);
+  if (prec == PFMP_F64)
+    mhat_t<PFMP_F64>(op, out, in, dagger, norm_out, scal);
+  else
+    mhat_t<PFMP_F32>(op, out, in, dagger, norm_out, scal);
+}
+
+// out = K in; <in, K in> = ||M-hat in||^2 is reduced in the second kernel of M-hat
+void kop(pfmp_op* op, int prec, void* out, const void* in, double* pKp_dev, CGScalars* scal) {
+  void* e = prec == PFMP_F64 ? (void*)op->e64 : (void*)op->e32;
+  mhat(op, prec, e, in, false, pKp_dev, scal);
+  mhat(op, prec, out, e, true, nullptr, scal);
+}
+
+}  // namespace pfmp

@@ -1,0 +1,175 @@
+// Load/store of spinors, links and clover blocks in the device layouts (see
+// pfmp_internal.cuh), templated on the storage precision.
+#pragma once
+#include "pfmp_internal.cuh"
+
+namespace pfmp {
+
+template <int PREC>
+struct Prec;
+template <>
+struct Prec<PFMP_F64> {
+  using real = double;
+  using vec = double2;
+  static constexpr int spinor_vecs = 12;
+  static constexpr int link_vecs = 6;  // 12 reals
+  static constexpr int clover_vecs = 36;
+};
+template <>
+struct Prec<PFMP_F32> {
+  using real = float;
+  using vec = float4;
+  static constexpr int spinor_vecs = 6;
+  static constexpr int link_vecs = 3;
+  static constexpr int clover_vecs = 18;
+};
+
+// ---------------------------------------------------------------- spinors
+__device__ __forceinline__ void load_spinor(Spinor<double>& s, const double2* __restrict__ f, int cb, int Vh) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    double2 v = __ldg(f + (size_t)k * Vh + cb);
+    s.s[k / 3][k % 3] = mk(v.x, v.y);
+  }
+}
+__device__ __forceinline__ void store_spinor(double2* __restrict__ f, const Spinor<double>& s, int cb, int Vh) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) f[(size_t)k * Vh + cb] = make_double2(s.s[k / 3][k % 3].re, s.s[k / 3][k % 3].im);
+}
+__device__ __forceinline__ void load_spinor(Spinor<float>& s, const float4* __restrict__ f, int cb, int Vh) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    float4 v = __ldg(f + (size_t)k * Vh + cb);
+    s.s[(2 * k) / 3][(2 * k) % 3] = mk(v.x, v.y);
+    s.s[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(v.z, v.w);
+  }
+}
+__device__ __forceinline__ void store_spinor(float4* __restrict__ f, const Spinor<float>& s, int cb, int Vh) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    cplx<float> a = s.s[(2 * k) / 3][(2 * k) % 3], b = s.s[(2 * k + 1) / 3][(2 * k + 1) % 3];
+    f[(size_t)k * Vh + cb] = make_float4(a.re, a.im, b.re, b.im);
+  }
+}
+
+// ---------------------------------------------------------------- links (12-real)
+// link field of one (parity, mu): base pointer at [parity][mu], vectors strided by Vh
+__device__ __forceinline__ void load_link(Mat3<double>& U, const double2* __restrict__ f, int cb, int Vh) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double2 v = __ldg(f + (size_t)k * Vh + cb);
+    U.m[k / 3][k % 3] = mk(v.x, v.y);
+  }
+  reconstruct_row2(U);
+}
+__device__ __forceinline__ void load_link(Mat3<float>& U, const float4* __restrict__ f, int cb, int Vh) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float4 v = __ldg(f + (size_t)k * Vh + cb);
+    U.m[(2 * k) / 3][(2 * k) % 3] = mk(v.x, v.y);
+    U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(v.z, v.w);
+  }
+  reconstruct_row2(U);
+}
+
+// master gauge field: double2 [2][4][9][Vh], full 3x3
+__device__ __forceinline__ void load_link18(Mat3<double>& U, const double2* __restrict__ f, int cb, int Vh) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    double2 v = f[(size_t)k * Vh + cb];
+    U.m[k / 3][k % 3] = mk(v.x, v.y);
+  }
+}
+__device__ __forceinline__ void store_link18(double2* __restrict__ f, const Mat3<double>& U, int cb, int Vh) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) f[(size_t)k * Vh + cb] = make_double2(U.m[k / 3][k % 3].re, U.m[k / 3][k % 3].im);
+}
+
+// ---------------------------------------------------------------- clover blocks
+// one chiral block: 6 diagonal reals, 15 lower-triangle complex entries
+template <typename T>
+struct HermBlock {
+  T d[6];
+  cplx<T> o[15];  // (1,0),(2,0),(2,1),(3,0),(3,1),(3,2),(4,0),...,(5,4)
+};
+__host__ __device__ __forceinline__ int tri_index(int i, int j) { return i * (i - 1) / 2 + j; }  // i > j
+
+__device__ __forceinline__ void load_clover(HermBlock<double> b[2], const double2* __restrict__ f, int cb, int Vh) {
+#pragma unroll
+  for (int blk = 0; blk < 2; ++blk) {
+    const double2* g = f + (size_t)(18 * blk) * Vh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double2 v = __ldg(g + (size_t)k * Vh + cb);
+      b[blk].d[2 * k] = v.x;
+      b[blk].d[2 * k + 1] = v.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      double2 v = __ldg(g + (size_t)(3 + k) * Vh + cb);
+      b[blk].o[k] = mk(v.x, v.y);
+    }
+  }
+}
+__device__ __forceinline__ void store_clover(double2* __restrict__ f, const HermBlock<double> b[2], int cb, int Vh) {
+#pragma unroll
+  for (int blk = 0; blk < 2; ++blk) {
+    double2* g = f + (size_t)(18 * blk) * Vh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[(size_t)k * Vh + cb] = make_double2(b[blk].d[2 * k], b[blk].d[2 * k + 1]);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) g[(size_t)(3 + k) * Vh + cb] = make_double2(b[blk].o[k].re, b[blk].o[k].im);
+  }
+}
+__device__ __forceinline__ void load_clover(HermBlock<float> b[2], const float4* __restrict__ f, int cb, int Vh) {
+#pragma unroll
+  for (int blk = 0; blk < 2; ++blk) {
+    const float4* g = f + (size_t)(9 * blk) * Vh;
+    float4 v0 = __ldg(g + cb), v1 = __ldg(g + (size_t)Vh + cb);
+    b[blk].d[0] = v0.x;
+    b[blk].d[1] = v0.y;
+    b[blk].d[2] = v0.z;
+    b[blk].d[3] = v0.w;
+    b[blk].d[4] = v1.x;
+    b[blk].d[5] = v1.y;
+    b[blk].o[0] = mk(v1.z, v1.w);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      float4 v = __ldg(g + (size_t)(2 + k) * Vh + cb);
+      b[blk].o[1 + 2 * k] = mk(v.x, v.y);
+      b[blk].o[2 + 2 * k] = mk(v.z, v.w);
+    }
+  }
+}
+
+// y = B x for one Hermitian 6x6 block (x, y indexed 3*(spin - 2*blk) + colour)
+template <typename T>
+__device__ __forceinline__ void herm_apply(const HermBlock<T>& B, const cplx<T> x[6], cplx<T> y[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) y[i] = B.d[i] * x[i];
+#pragma unroll
+  for (int i = 1; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      cplx<T> a = B.o[tri_index(i, j)];
+      y[i] = y[i] + a * x[j];
+      y[j] = y[j] + cj_mul(a, x[i]);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ Spinor<T> clover_apply(const HermBlock<T> B[2], const Spinor<T>& in) {
+  Spinor<T> out;
+#pragma unroll
+  for (int blk = 0; blk < 2; ++blk) {
+    cplx<T> x[6], y[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) x[k] = in.s[2 * blk + k / 3][k % 3];
+    herm_apply(B[blk], x, y);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) out.s[2 * blk + k / 3][k % 3] = y[k];
+  }
+  return out;
+}
+
+}  // namespace pfmp

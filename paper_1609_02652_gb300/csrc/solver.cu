@@ -1,0 +1,150 @@
+// Conjugate gradient on K = M-hat^dag M-hat (the paper's solver, Sec. 2.1, Sec. 3.1):
+//  * CG64: FP64 throughout.
+//  * mixed: FP32 CG ("sloppy") with FP64 reliable updates: every time the sloppy residual
+//    has fallen by `delta` (or reached the target) the accumulated FP32 solution is
+//    added to the FP64 solution and the true residual b - K x is recomputed in FP64;
+//    the sloppy residual restarts from it while the search direction is kept.
+// The iteration runs on the device with no host round trip: alpha and beta come from
+// device scalars written by the reduction finishers, and a `done` flag makes every
+// queued kernel return at once after convergence.  The host looks at the scalars
+// every `check_every` iterations.  Zero initial guess (history-free, reversible MD).
+#include <cmath>
+
+#include "context.h"
+
+namespace pfmp {
+
+static void put_scalars(pfmp_op* op, double rr, double stop_rr) {
+  CGScalars* h = op->h_scal;
+  h->rr = rr;
+  h->rr_new = rr;
+  h->pAp = 0;
+  h->alpha = 0;
+  h->beta = 0;
+  h->stop_rr = stop_rr;
+  h->done = 0;
+  h->done_next = 0;
+  h->iter = 0;
+  PFMP_CUDA(cudaMemcpyAsync(op->scal, h, sizeof(CGScalars), cudaMemcpyHostToDevice, op->ctx->stream));
+}
+static void get_scalars(pfmp_op* op) {
+  PFMP_CUDA(cudaMemcpyAsync(op->h_scal, op->scal, sizeof(CGScalars), cudaMemcpyDeviceToHost, op->ctx->stream));
+  PFMP_CUDA(cudaStreamSynchronize(op->ctx->stream));
+}
+static double host_norm2(pfmp_op* op, int prec, const void* x) {
+  pfmp_ctx* c = op->ctx;
+  blas_norm2(c, prec, x, c->d_sums);
+  PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PFMP_CUDA(cudaStreamSynchronize(c->stream));
+  return c->h_sums[0];
+}
+
+// r = b - K x in FP64; returns |r|^2
+static double true_residual(pfmp_op* op, const void* x, const void* b, void* r, void* Ax) {
+  pfmp_ctx* c = op->ctx;
+  kop(op, PFMP_F64, Ax, x, nullptr, nullptr);
+  blas_xmy_norm(c, b, Ax, r, c->d_sums);
+  PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PFMP_CUDA(cudaStreamSynchronize(c->stream));
+  return c->h_sums[0];
+}
+
+// run the device CG loop (prec) until `done` or the iteration cap; returns iterations
+static int run_cg(pfmp_op* op, int prec, void* x, void* r, void* p, void* Ap, int max_iter, int check_every) {
+  pfmp_ctx* c = op->ctx;
+  int done_iters = 0;
+  for (;;) {
+    const int chunk = check_every < max_iter - done_iters ? check_every : max_iter - done_iters;
+    if (chunk <= 0) break;
+    for (int k = 0; k < chunk; ++k) {
+      kop(op, prec, Ap, p, &op->scal->pAp, op->scal);
+      cg_step_xr(c, prec, x, r, p, Ap, op->scal);
+      cg_step_p(c, prec, p, r, op->scal);
+    }
+    get_scalars(op);
+    done_iters = op->h_scal->iter;
+    if (op->h_scal->done) break;
+  }
+  return done_iters;
+}
+
+int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int check_every, void* x, const void* b,
+          int* iters, int* rel_updates, double* true_res, long* kapply) {
+  pfmp_ctx* c = op->ctx;
+  PFMP_REQUIRE(x != b, PFMP_E_INVALID, "x and b must not alias");
+  PFMP_REQUIRE(tol > 0 && max_iter > 0, PFMP_E_INVALID, "tol and max_iter must be positive");
+  if (check_every <= 0) check_every = 16;
+  if (!(delta > 0 && delta < 1)) delta = 0.1;
+  *iters = 0;
+  *rel_updates = 0;
+  *kapply = 0;
+  const double bb = host_norm2(op, PFMP_F64, b);
+  blas_zero(c, PFMP_F64, x);
+  if (bb == 0.0) {
+    *true_res = 0.0;
+    return PFMP_OK;
+  }
+  PFMP_REQUIRE(std::isfinite(bb), PFMP_E_NAN, "right-hand side is not finite");
+  void* r = op->cg64[0];
+  void* p = op->cg64[1];
+  void* Ap = op->cg64[2];
+  double rr_true = bb;
+  int total = 0;
+  if (method == PFMP_SOLVER_CG64) {
+    // restart from the true residual if the recursive one drifted below it
+    PFMP_CUDA(cudaMemcpyAsync(r, b, spinor_bytes(c->g, PFMP_F64), cudaMemcpyDeviceToDevice, c->stream));
+    for (int restart = 0; restart < 8 && total < max_iter; ++restart) {
+      PFMP_CUDA(cudaMemcpyAsync(p, r, spinor_bytes(c->g, PFMP_F64), cudaMemcpyDeviceToDevice, c->stream));
+      put_scalars(op, rr_true, 0.25 * tol * tol * bb);
+      // x accumulates in place: run_cg adds to x
+      const int it = run_cg(op, PFMP_F64, x, r, p, Ap, max_iter - total, check_every);
+      total += it;
+      *kapply += it;
+      PFMP_REQUIRE(std::isfinite(op->h_scal->rr), PFMP_E_NAN, "CG residual became NaN/Inf");
+      rr_true = true_residual(op, x, b, r, Ap);
+      *kapply += 1;
+      if (std::sqrt(rr_true / bb) < tol) break;
+    }
+  } else if (method == PFMP_SOLVER_CG_MIXED) {
+    float4* r32 = op->cg32[0];
+    float4* p32 = op->cg32[1];
+    float4* Ap32 = op->cg32[2];
+    float4* xs32 = op->cg32[3];
+    PFMP_CUDA(cudaMemcpyAsync(r, b, spinor_bytes(c->g, PFMP_F64), cudaMemcpyDeviceToDevice, c->stream));
+    blas_copy(c, r32, PFMP_F32, r, PFMP_F64);
+    blas_copy(c, p32, PFMP_F32, r32, PFMP_F32);
+    blas_zero(c, PFMP_F32, xs32);
+    double rr_s = host_norm2(op, PFMP_F32, r32);
+    while (total < max_iter) {
+      // sloppy target: a factor delta below the last true residual, not below tol
+      double stop = delta * delta * rr_true;
+      const double floor_rr = 0.25 * tol * tol * bb;
+      if (stop < floor_rr) stop = floor_rr;
+      put_scalars(op, rr_s, stop);
+      const int it = run_cg(op, PFMP_F32, xs32, r32, p32, Ap32, max_iter - total, check_every);
+      total += it;
+      *kapply += it;
+      PFMP_REQUIRE(std::isfinite(op->h_scal->rr), PFMP_E_NAN, "sloppy CG residual became NaN/Inf");
+      // reliable update
+      blas_add_lo(c, x, xs32);
+      rr_true = true_residual(op, x, b, r, Ap);
+      *kapply += 1;
+      *rel_updates += 1;
+      if (std::sqrt(rr_true / bb) < tol) break;
+      blas_copy(c, r32, PFMP_F32, r, PFMP_F64);
+      blas_zero(c, PFMP_F32, xs32);
+      rr_s = host_norm2(op, PFMP_F32, r32);
+      if (it == 0) {  // stalled: restart the direction as well
+        blas_copy(c, p32, PFMP_F32, r32, PFMP_F32);
+      }
+    }
+  } else {
+    PFMP_REQUIRE(false, PFMP_E_INVALID, "unknown solver method");
+  }
+  *iters = total;
+  *true_res = std::sqrt(rr_true / bb);
+  PFMP_REQUIRE(std::isfinite(*true_res), PFMP_E_NAN, "true residual is not finite");
+  return *true_res < tol ? PFMP_OK : PFMP_E_NOT_CONVERGED;
+}
+
+}  // namespace pfmp
