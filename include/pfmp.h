@@ -128,6 +128,20 @@ int pfmp_dslash(pfmp_op* op, int prec, void* out, const void* in, int out_parity
 int pfmp_clover_apply(pfmp_op* op, int prec, void* out, const void* in, int parity, int inverse);
 /* out = M-hat in (dagger = 0) or M-hat^dag in (dagger = 1); even parity fields.      */
 int pfmp_mhat(pfmp_op* op, int prec, void* out, const void* in, int dagger);
+/* Allocation-free M-hat (no counterpart in the paper: a library convenience).  The same
+ * result as pfmp_mhat (same kernels, bit-identical output), for callers that must not
+ * allocate device memory during the call -- inside a CUDA stream capture, a host
+ * callback, a latency-bound loop, or under a framework that owns the device memory
+ * pool.  Its odd-site temporary is a fixed array of PFMP_NOALLOC_SCRATCH_BYTES (64 MiB)
+ * inside the library image, held by every GPU that loads the library until exit; a
+ * lattice whose temporary (pfmp_spinor_bytes(ctx, prec)) is larger is rejected with
+ * PFMP_E_INVALID (FP64: up to 349,525 sites per parity, e.g. 24^3 x 48; FP32: twice
+ * that).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and must come before any stream capture on that device.
+ * Nothing is allocated or freed.  All calls share the array: calls that overlap on the
+ * GPU (different streams or threads at once) race on it.                            */
+#define PFMP_NOALLOC_SCRATCH_BYTES (64ll * 1024 * 1024)
+int pfmp_mhat_noalloc(pfmp_op* op, int prec, void* out, const void* in, int dagger);
 /* out = K in = M-hat^dag M-hat in; if in_K_in is not NULL it receives <in, K in> =
  * ||M-hat in||^2 in FP64 (synchronises).                                             */
 int pfmp_kop(pfmp_op* op, int prec, void* out, const void* in, double* in_K_in);

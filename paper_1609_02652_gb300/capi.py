@@ -77,6 +77,7 @@ SIGNATURES = {
     "pfmp_dslash": (I, [P, I, P, P, I, I]),
     "pfmp_clover_apply": (I, [P, I, P, P, I, I]),
     "pfmp_mhat": (I, [P, I, P, P, I]),
+    "pfmp_mhat_noalloc": (I, [P, I, P, P, I]),
     "pfmp_kop": (I, [P, I, P, P, DP]),
     "pfmp_norm2": (I, [P, I, P, DP]),
     "pfmp_cdot": (I, [P, I, P, P, DP]),
@@ -209,6 +210,10 @@ def pfmp_clover_apply(op, prec, out, inp, parity, inverse):
 
 def pfmp_mhat(op, prec, out, inp, dagger=0):
     check(lib().pfmp_mhat(op, prec, _ptr(out), _ptr(inp), dagger))
+
+
+def pfmp_mhat_noalloc(op, prec, out, inp, dagger=0):
+    check(lib().pfmp_mhat_noalloc(op, prec, _ptr(out), _ptr(inp), dagger))
 
 
 def pfmp_kop(op, prec, out, inp, want_norm=False):

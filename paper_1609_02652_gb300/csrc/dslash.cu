@@ -325,6 +325,33 @@ static void mhat_t(pfmp_op* op, void* out, const void* in, bool dagger, double* 
   }
 }
 
+// M-hat with a caller-supplied odd-site temporary (used by the allocation-free entry
+// point); the same two launches as mhat() below
+void mhat_with_temp(pfmp_op* op, int prec, void* out, const void* in, bool dagger, void* temp) {
+  require_clover(op);
+  if (prec == PFMP_F64) {
+    double2* keep = op->t64;
+    op->t64 = (double2*)temp;
+    try {
+      mhat_t<PFMP_F64>(op, out, in, dagger, nullptr, nullptr);
+    } catch (...) {
+      op->t64 = keep;
+      throw;
+    }
+    op->t64 = keep;
+  } else {
+    float4* keep = op->t32;
+    op->t32 = (float4*)temp;
+    try {
+      mhat_t<PFMP_F32>(op, out, in, dagger, nullptr, nullptr);
+    } catch (...) {
+      op->t32 = keep;
+      throw;
+    }
+    op->t32 = keep;
+  }
+}
+
 void mhat(pfmp_op* op, int prec, void* out, const void* in, bool dagger, double* norm_out, CGScalars* scal) {
   require_clover(op);
   if (prec == PFMP_F64)
