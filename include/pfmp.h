@@ -161,7 +161,7 @@ typedef struct {
   double tol;        /* stop when ||b - K x|| / ||b|| < tol, residual recomputed in FP64  */
   int max_iter;      /* iteration cap -> PFMP_E_NOT_CONVERGED                              */
   double delta;      /* mixed: reliable update when the sloppy residual fell by delta      */
-  int check_every;   /* iterations between host convergence checks (0: default 16)        */
+  int check_every;   /* iterations per CUDA-graph chunk between host checks (0: default 8) */
 } pfmp_solver_params;
 
 typedef struct {

@@ -16,7 +16,6 @@ double plaquette(pfmp_ctx* c);
 void spinor_pack_any(pfmp_ctx* c, void* dst, int prec, const double* src, int where, int parity);
 void spinor_unpack_any(pfmp_ctx* c, double* dst, int where, const void* src, int prec, int parity);
 void profile_begin(pfmp_ctx* c);
-long long launch_count();
 void profile_end(pfmp_ctx* c, int cls, long* launches, double* ms, double* bytes);
 }  // namespace pfmp
 
@@ -57,6 +56,9 @@ static void op_free(pfmp_op* op) {
   for (int k = 0; k < 4; ++k) dev_free(op->cg32[k]);
   dev_free(op->scal);
   if (op->h_scal) cudaFreeHost(op->h_scal);
+  for (auto& G : op->graph)
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (op->cap) cudaStreamDestroy(op->cap);
   delete op;
 }
 

@@ -71,6 +71,15 @@ struct pfmp_op {
   float4* cg32[4] = {nullptr, nullptr, nullptr, nullptr};
   pfmp::CGScalars* scal = nullptr;
   pfmp::CGScalars* h_scal = nullptr;
+  // CUDA graph of one chunk of CG iterations per precision (captured on `cap`, replayed
+  // on the context's stream); keyed by the buffers and the chunk length
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
+    int chunk = 0;
+    long long kernels = 0;  // kernel nodes in the graph (for the launch counter)
+  } graph[2];
+  cudaStream_t cap = nullptr;
 };
 
 namespace pfmp {

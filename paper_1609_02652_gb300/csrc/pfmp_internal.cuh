@@ -51,6 +51,8 @@ struct Err {
 
 void set_last_error(const std::string& s);
 void count_launch();
+void count_launches(long long n);
+long long launch_count();
 
 // ------------------------------------------------------------------ complex
 template <typename T>

@@ -49,18 +49,68 @@ static double true_residual(pfmp_op* op, const void* x, const void* b, void* r, 
   return c->h_sums[0];
 }
 
+static void launch_chunk(pfmp_op* op, int prec, void* x, void* r, void* p, void* Ap, int chunk) {
+  pfmp_ctx* c = op->ctx;
+  for (int k = 0; k < chunk; ++k) {
+    kop(op, prec, Ap, p, &op->scal->pAp, op->scal);
+    cg_step_xr(c, prec, x, r, p, Ap, op->scal);
+    cg_step_p(c, prec, p, r, op->scal);
+  }
+}
+
+// One chunk of CG iterations.  Without kernel profiling the chunk is captured once into
+// a CUDA graph (6 kernels per iteration, all parameters fixed: the scalars live on the
+// device) and replayed on the context's stream, which removes the per-launch host cost.
+static void run_chunk(pfmp_op* op, int prec, void* x, void* r, void* p, void* Ap, int chunk) {
+  pfmp_ctx* c = op->ctx;
+  if (c->prof.on) {
+    launch_chunk(op, prec, x, r, p, Ap, chunk);
+    return;
+  }
+  pfmp_op::Graph& G = op->graph[prec];
+  const void* key[4] = {x, r, p, Ap};
+  bool hit = G.exec && G.chunk == chunk;
+  for (int k = 0; k < 4 && hit; ++k) hit = G.key[k] == key[k];
+  if (!hit) {
+    if (G.exec) {
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+    }
+    if (!op->cap) PFMP_CUDA(cudaStreamCreateWithFlags(&op->cap, cudaStreamNonBlocking));
+    cudaStream_t keep = c->stream;
+    cudaGraph_t graph = nullptr;
+    PFMP_CUDA(cudaStreamBeginCapture(op->cap, cudaStreamCaptureModeThreadLocal));
+    c->stream = op->cap;
+    const long long n0 = launch_count();
+    try {
+      launch_chunk(op, prec, x, r, p, Ap, chunk);
+    } catch (...) {
+      c->stream = keep;
+      cudaStreamEndCapture(op->cap, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    c->stream = keep;
+    G.kernels = launch_count() - n0;
+    count_launches(-G.kernels);  // captured, not launched
+    PFMP_CUDA(cudaStreamEndCapture(op->cap, &graph));
+    cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    PFMP_CUDA(e);
+    G.chunk = chunk;
+    for (int k = 0; k < 4; ++k) G.key[k] = key[k];
+  }
+  PFMP_CUDA(cudaGraphLaunch(G.exec, c->stream));
+  count_launches(G.kernels);
+}
+
 // run the device CG loop (prec) until `done` or the iteration cap; returns iterations
 static int run_cg(pfmp_op* op, int prec, void* x, void* r, void* p, void* Ap, int max_iter, int check_every) {
-  pfmp_ctx* c = op->ctx;
   int done_iters = 0;
   for (;;) {
     const int chunk = check_every < max_iter - done_iters ? check_every : max_iter - done_iters;
     if (chunk <= 0) break;
-    for (int k = 0; k < chunk; ++k) {
-      kop(op, prec, Ap, p, &op->scal->pAp, op->scal);
-      cg_step_xr(c, prec, x, r, p, Ap, op->scal);
-      cg_step_p(c, prec, p, r, op->scal);
-    }
+    run_chunk(op, prec, x, r, p, Ap, chunk);
     get_scalars(op);
     done_iters = op->h_scal->iter;
     if (op->h_scal->done) break;
@@ -73,7 +123,7 @@ int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int c
   pfmp_ctx* c = op->ctx;
   PFMP_REQUIRE(x != b, PFMP_E_INVALID, "x and b must not alias");
   PFMP_REQUIRE(tol > 0 && max_iter > 0, PFMP_E_INVALID, "tol and max_iter must be positive");
-  if (check_every <= 0) check_every = 16;
+  if (check_every <= 0) check_every = 8;
   if (!(delta > 0 && delta < 1)) delta = 0.1;
   *iters = 0;
   *rel_updates = 0;
@@ -91,20 +141,24 @@ int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int c
   double rr_true = bb;
   int total = 0;
   if (method == PFMP_SOLVER_CG64) {
-    // restart from the true residual if the recursive one drifted below it
+    // the solution accumulates in an operator-owned buffer (a stable CUDA-graph key) and
+    // is copied to x at the end; restart from the true residual if the recursive one
+    // drifted below it
+    void* xa = op->cg64[5];
+    blas_zero(c, PFMP_F64, xa);
     PFMP_CUDA(cudaMemcpyAsync(r, b, spinor_bytes(c->g, PFMP_F64), cudaMemcpyDeviceToDevice, c->stream));
     for (int restart = 0; restart < 8 && total < max_iter; ++restart) {
       PFMP_CUDA(cudaMemcpyAsync(p, r, spinor_bytes(c->g, PFMP_F64), cudaMemcpyDeviceToDevice, c->stream));
       put_scalars(op, rr_true, 0.25 * tol * tol * bb);
-      // x accumulates in place: run_cg adds to x
-      const int it = run_cg(op, PFMP_F64, x, r, p, Ap, max_iter - total, check_every);
+      const int it = run_cg(op, PFMP_F64, xa, r, p, Ap, max_iter - total, check_every);
       total += it;
       *kapply += it;
       PFMP_REQUIRE(std::isfinite(op->h_scal->rr), PFMP_E_NAN, "CG residual became NaN/Inf");
-      rr_true = true_residual(op, x, b, r, Ap);
+      rr_true = true_residual(op, xa, b, r, Ap);
       *kapply += 1;
       if (std::sqrt(rr_true / bb) < tol) break;
     }
+    PFMP_CUDA(cudaMemcpyAsync(x, xa, spinor_bytes(c->g, PFMP_F64), cudaMemcpyDeviceToDevice, c->stream));
   } else if (method == PFMP_SOLVER_CG_MIXED) {
     float4* r32 = op->cg32[0];
     float4* p32 = op->cg32[1];

@@ -71,3 +71,33 @@ def test_solve_host_path_and_errors():
             capi.pfmp_ctx_create((4, 4, 3, 4), -1)
     finally:
         g.close()
+
+
+def test_fp64_cg_full_size_matches_oracle_iterations():
+    """At the benchmark size (16^3 x 32) the FP64 CG on the GPU takes the oracle's number of
+    iterations (stored by tests/golden/make_cg_iterations.py) to reach 1e-10, +-2 for the
+    different summation order, and its true residual agrees with the oracle's."""
+    import json
+    import os
+
+    from paper_1609_02652_gb300 import capi
+
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cg_iterations_16x16x16x32.json")))
+    dims = tuple(gold["dims"])
+    ctx = capi.pfmp_ctx_create(dims, -1, None)
+    try:
+        h = np.ascontiguousarray(pin.gauge_algebra(dims, 1)).reshape(-1)
+        capi.pfmp_gauge_from_algebra(ctx, h, gold["eps"], capi.PFMP_HOST)
+        op = capi.pfmp_op_create(ctx, gold["kappa"], gold["csw"])
+        b = np.ascontiguousarray(pin.spinor(dims, 100)).view(np.float64).reshape(-1)
+        x = np.zeros_like(b)
+        for method in (0, 1):
+            prm = capi.SolverParams(method=method, tol=gold["tol"], max_iter=2000, delta=0.1, check_every=8)
+            info = capi.pfmp_solve_host(op, prm, x, b)
+            assert info.true_rel_res < 1e-10
+            if method == 0:
+                assert abs(info.iters - gold["iterations"]) <= 2
+                assert abs(info.true_rel_res - gold["true_rel_res"]) < 0.05 * gold["true_rel_res"]
+        capi.pfmp_op_destroy(op)
+    finally:
+        capi.pfmp_ctx_destroy(ctx)
