@@ -183,6 +183,82 @@ int pfmp_solve(pfmp_op* op, const pfmp_solver_params* params, void* x, const voi
 int pfmp_solve_host(pfmp_op* op, const pfmp_solver_params* params, double* x_host,
                     const double* b_host, pfmp_solve_info* info);
 
+/* ---- multi-shift CG (Sec. 3.1; App. C eq. force_polycorr) ---------------------------
+ * x[k] = (K + sigma_k)^{-1} b for nshift complex shifts sigma_k = (sigma_re[k],
+ * sigma_im[k]) from one Krylov space of K (the seed system), FP64.  x[k] are FP64 even
+ * device fields owned by the caller (nshift <= 1024).  Stops when the seed residual and
+ * every shifted residual |zeta_k| ||r|| are below tol ||b||.  If info is not NULL,
+ * info->true_rel_res receives max_k ||b - (K + sigma_k) x_k|| / ||b|| recomputed in
+ * FP64 (one extra K per shift).  Synchronises.                                        */
+int pfmp_solve_multishift(pfmp_op* op, int nshift, const double* sigma_re, const double* sigma_im, void* const* x,
+                          const void* b, double tol, int max_iter, pfmp_solve_info* info);
+
+/* ---- Chebyshev polynomial filter (App. A) --------------------------------------------
+ * P_n(z) = a_n prod_{k=1}^n (z - z_k), z_k = mu (1 - cos t_k) - i sqrt(mu^2 - nu^2) sin t_k,
+ * t_k = 2 pi k / (n+1), a_n = 1 / (mu prod_k (mu - z_k)).  pfmp_poly_roots writes the n
+ * roots and a_n.  pfmp_poly_apply: out = P_n(K) in (which = 0), R(K) in (which = 1) or
+ * R(K)^dag in (which = 2), R = sqrt(a_n) prod_{Im z_k < 0} (K - z_k) so that P = R^dag R;
+ * factors applied in the order k = 1..n; FP64 even fields.  Even n only
+ * (PFMP_E_UNSUPPORTED otherwise), mu >= nu > 0.                                        */
+int pfmp_poly_roots(int n, double mu, double nu, double* z_re, double* z_im, double* a_n);
+int pfmp_poly_apply(pfmp_op* op, int n, double mu, double nu, int which, void* out, const void* in);
+
+/* ---- PF-MP action, forces, trajectory (Sec. 2.1, 2.5, App. B, App. C) --------------
+ * S = S_G + S_det + phi1^dag P(J) phi1 + phi2^dag [J P(J)]^{-1} phi2 + phi3^dag W K^{-1} W^dag phi3,
+ * S_G = beta sum_{x,mu<nu} (1 - Re tr U_{mu nu} / 3), S_det = -2 sum_{x odd} log det A(x),
+ * K at kappa, J = W^dag W with W = M-hat at kappa_h.  Pseudofermion heatbath from
+ * Gaussian noise xi (density exp(-xi^dag xi)): phi1 = R(J)^{-1} xi1,
+ * phi2 = R(J)^dag W^dag xi2, phi3 = W J^{-1} M-hat^dag xi3.  Forces are the algebra
+ * coefficients dS/d omega_a for U -> exp(i omega_a T_a) U (App. C forms; F1 costs 2n - 2
+ * J products, F2 one multi-shift solve with z_{n+1} = 0, F3 one CG on K).  All FP64.    */
+#define PFMP_TERM_GAUGE 0
+#define PFMP_TERM_DET 1
+#define PFMP_TERM_POLY 2
+#define PFMP_TERM_POLYCORR 3
+#define PFMP_TERM_HASEN 4
+typedef struct pfmp_action pfmp_action;
+typedef struct {
+  double beta, kappa, kappa_h, csw;  /* gauge coupling, target and Hasenbusch kappa, c_sw */
+  int n;                             /* polynomial order (even)                          */
+  double mu, nu;                     /* Chebyshev ellipse                                 */
+  double tol;                        /* relative residual of every solve in the action    */
+  int max_iter;
+} pfmp_action_params;
+typedef struct {
+  double H0, H1, dH;
+  int accepted;
+  double S0[5], S1[5];   /* per term at the start and end (0 for terms not in the schedule) */
+  double plaquette;      /* after the accept/reject decision                               */
+  int64_t k_apply;       /* K and J applications outside CUDA-graph replays                */
+  int force_evals;
+} pfmp_traj_info;
+int pfmp_action_create(pfmp_ctx* ctx, const pfmp_action_params* prm, pfmp_action** action);
+int pfmp_action_destroy(pfmp_action* action);
+/* rebuild the clover blocks after pfmp_gauge_set                                      */
+int pfmp_action_refresh(pfmp_action* action);
+/* xi: three canonical spinors ([3][V][4][3] complex double; even sites used)          */
+int pfmp_action_heatbath(pfmp_action* action, const double* xi, int where);
+int pfmp_action_get_phi(pfmp_action* action, int i, double* phi, int where);
+int pfmp_action_set_phi(pfmp_action* action, int i, const double* phi, int where);
+/* S[5] per term at the current gauge field (synchronises)                              */
+int pfmp_action_eval(pfmp_action* action, double S[5]);
+/* force of one term, canonical [V][4][8]                                               */
+int pfmp_action_force(pfmp_action* action, int term, double* F, int where);
+/* 2MN arrays of eq. 2MNSTS chained n times over tau: T and S of length 2n + 1          */
+int pfmp_schedule_2mn(int n, double tau, double lambda, double* T, double* S);
+/* generalised multi-scale merge (App. B): nschemes schemes, scheme i given by len[i]
+ * entries of T and S (concatenated); writes the merged T_out[cap] and
+ * S_out[nschemes][cap] and the merged length.                                          */
+int pfmp_schedule_merge(int nschemes, const int* len, const double* T, const double* S, int cap, double* T_out,
+                        double* S_out, int* len_out);
+/* One trajectory: heatbath from xi, H0, the merged schedule (T[len], S[nlevels][len]),
+ * each term t integrated on level term_level[t] (-1: term left out), H1, Metropolis
+ * accept iff u < exp(-dH); a rejected trajectory restores the gauge field.  mom: initial
+ * momenta, canonical [V][4][8].  Synchronises.                                          */
+int pfmp_trajectory(pfmp_action* action, int len, const double* T, int nlevels, const double* S,
+                    const int term_level[5], const double* mom, const double* xi, int where, double u,
+                    pfmp_traj_info* info);
+
 /* ---- kernel timing (tracing) ------------------------------------------------------
  * pfmp_profile_begin: from now on every stencil launch of this context is bracketed by
  * CUDA events on the context's stream.  pfmp_profile_end (synchronises) stops recording

@@ -48,6 +48,19 @@ class SolveInfo(C.Structure):
                 ("k_apply", C.c_int64), ("status", C.c_int)]
 
 
+class ActionParams(C.Structure):
+    _fields_ = [("beta", C.c_double), ("kappa", C.c_double), ("kappa_h", C.c_double), ("csw", C.c_double),
+                ("n", C.c_int), ("mu", C.c_double), ("nu", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int)]
+
+
+class TrajInfo(C.Structure):
+    _fields_ = [("H0", C.c_double), ("H1", C.c_double), ("dH", C.c_double), ("accepted", C.c_int),
+                ("S0", C.c_double * 5), ("S1", C.c_double * 5), ("plaquette", C.c_double),
+                ("k_apply", C.c_int64), ("force_evals", C.c_int)]
+
+
+PFMP_TERM_GAUGE, PFMP_TERM_DET, PFMP_TERM_POLY, PFMP_TERM_POLYCORR, PFMP_TERM_HASEN = range(5)
+
 P = C.c_void_p
 I = C.c_int
 D = C.c_double
@@ -85,6 +98,20 @@ SIGNATURES = {
     "pfmp_convert": (I, [P, P, I, P, I]),
     "pfmp_solve": (I, [P, C.POINTER(SolverParams), P, P, C.POINTER(SolveInfo)]),
     "pfmp_solve_host": (I, [P, C.POINTER(SolverParams), P, P, C.POINTER(SolveInfo)]),
+    "pfmp_solve_multishift": (I, [P, I, DP, DP, C.POINTER(P), P, D, I, C.POINTER(SolveInfo)]),
+    "pfmp_poly_roots": (I, [I, D, D, DP, DP, DP]),
+    "pfmp_poly_apply": (I, [P, I, D, D, I, P, P]),
+    "pfmp_action_create": (I, [P, C.POINTER(ActionParams), C.POINTER(P)]),
+    "pfmp_action_destroy": (I, [P]),
+    "pfmp_action_refresh": (I, [P]),
+    "pfmp_action_heatbath": (I, [P, P, I]),
+    "pfmp_action_get_phi": (I, [P, I, P, I]),
+    "pfmp_action_set_phi": (I, [P, I, P, I]),
+    "pfmp_action_eval": (I, [P, DP]),
+    "pfmp_action_force": (I, [P, I, P, I]),
+    "pfmp_schedule_2mn": (I, [I, D, D, DP, DP]),
+    "pfmp_schedule_merge": (I, [I, C.POINTER(I), DP, DP, I, DP, DP, C.POINTER(I)]),
+    "pfmp_trajectory": (I, [P, I, DP, I, DP, C.POINTER(I), P, P, I, D, C.POINTER(TrajInfo)]),
     "pfmp_profile_begin": (I, [P]),
     "pfmp_profile_end": (I, [P, I, C.POINTER(C.c_int64), DP, DP]),
 }
@@ -271,3 +298,96 @@ def pfmp_profile_end(ctx, kernel_class):
 
 def pfmp_launch_count():
     return int(lib().pfmp_launch_count())
+
+
+def _dp(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(DP)
+
+
+def pfmp_solve_multishift(op, sigmas, xs, b, tol, max_iter, want_info=True):
+    sig = np.asarray(sigmas, dtype=np.complex128)
+    re, pre = _dp(sig.real)
+    im, pim = _dp(sig.imag)
+    arr = (P * len(xs))(*[_ptr(x) for x in xs])
+    info = SolveInfo()
+    check(lib().pfmp_solve_multishift(op, len(xs), pre, pim, arr, _ptr(b), float(tol), int(max_iter),
+                                      C.byref(info) if want_info else None))
+    return info
+
+
+def pfmp_poly_roots(n, mu, nu):
+    zr = np.zeros(n)
+    zi = np.zeros(n)
+    an = C.c_double()
+    check(lib().pfmp_poly_roots(n, mu, nu, zr.ctypes.data_as(DP), zi.ctypes.data_as(DP), C.byref(an)))
+    return zr + 1j * zi, an.value
+
+
+def pfmp_poly_apply(op, n, mu, nu, which, out, inp):
+    check(lib().pfmp_poly_apply(op, n, mu, nu, which, _ptr(out), _ptr(inp)))
+
+
+def pfmp_action_create(ctx, params):
+    h = P()
+    check(lib().pfmp_action_create(ctx, C.byref(params), C.byref(h)))
+    return h
+
+
+def pfmp_action_destroy(a):
+    check(lib().pfmp_action_destroy(a))
+
+
+def pfmp_action_refresh(a):
+    check(lib().pfmp_action_refresh(a))
+
+
+def pfmp_action_heatbath(a, xi, where=PFMP_HOST):
+    check(lib().pfmp_action_heatbath(a, _ptr(xi), where))
+
+
+def pfmp_action_get_phi(a, i, out, where=PFMP_HOST):
+    check(lib().pfmp_action_get_phi(a, i, _ptr(out), where))
+
+
+def pfmp_action_set_phi(a, i, phi, where=PFMP_HOST):
+    check(lib().pfmp_action_set_phi(a, i, _ptr(phi), where))
+
+
+def pfmp_action_eval(a):
+    S = (C.c_double * 5)()
+    check(lib().pfmp_action_eval(a, S))
+    return np.array(S[:])
+
+
+def pfmp_action_force(a, term, out, where=PFMP_HOST):
+    check(lib().pfmp_action_force(a, term, _ptr(out), where))
+
+
+def pfmp_schedule_2mn(n, tau, lam):
+    T = np.zeros(2 * n + 1)
+    S = np.zeros(2 * n + 1)
+    check(lib().pfmp_schedule_2mn(n, tau, lam, T.ctypes.data_as(DP), S.ctypes.data_as(DP)))
+    return T, S
+
+
+def pfmp_schedule_merge(schemes, cap=4096):
+    lens = (I * len(schemes))(*[len(T) for T, _ in schemes])
+    T, pT = _dp(np.concatenate([np.asarray(T, float) for T, _ in schemes]))
+    S, pS = _dp(np.concatenate([np.asarray(S, float) for _, S in schemes]))
+    Tout = np.zeros(cap)
+    Sout = np.zeros((len(schemes), cap))
+    m = I()
+    check(lib().pfmp_schedule_merge(len(schemes), lens, pT, pS, cap, Tout.ctypes.data_as(DP),
+                                    Sout.ctypes.data_as(DP), C.byref(m)))
+    return Tout[:m.value].copy(), Sout[:, :m.value].copy()
+
+
+def pfmp_trajectory(a, T, S_levels, term_level, mom, xi, u, where=PFMP_HOST):
+    T, pT = _dp(T)
+    S, pS = _dp(np.asarray(S_levels).reshape(-1))
+    tl = (I * 5)(*term_level)
+    info = TrajInfo()
+    check(lib().pfmp_trajectory(a, len(T), pT, np.asarray(S_levels).shape[0], pS, tl, _ptr(mom), _ptr(xi), where,
+                                float(u), C.byref(info)))
+    return info

@@ -1,7 +1,10 @@
 // extern "C" entry points: argument checks, exception-to-status translation, and the
 // small amount of orchestration each call needs.  See include/pfmp.h for the contract.
+#include <cmath>
+#include <complex>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "context.h"
 
@@ -16,6 +19,19 @@ double plaquette(pfmp_ctx* c);
 void spinor_pack_any(pfmp_ctx* c, void* dst, int prec, const double* src, int where, int parity);
 void spinor_unpack_any(pfmp_ctx* c, double* dst, int where, const void* src, int prec, int parity);
 void profile_begin(pfmp_ctx* c);
+pfmp_action* action_create(pfmp_ctx* c, const pfmp_action_params* prm);
+void action_destroy(pfmp_action* A);
+void action_heatbath(pfmp_action* A, const void* xi1, const void* xi2, const void* xi3);
+void action_eval(pfmp_action* A, double S[5]);
+void action_force_out(pfmp_action* A, int term, double* out, int where);
+void action_get_phi(pfmp_action* A, int i, double* out, int where);
+void action_set_phi(pfmp_action* A, int i, const double* in, int where);
+void action_refresh(pfmp_action* A);
+void schedule_2mn(int n, double tau, double lam, double* T, double* S);
+int schedule_merge(int ns, const int* len, const double* T, const double* S, int cap, double* Tout, double* Sout);
+void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int term_level[5],
+                const double* mom, int where, const void* const xi[3], double u, pfmp_traj_info* info);
+pfmp_ctx* action_ctx(pfmp_action* A);
 void profile_end(pfmp_ctx* c, int cls, long* launches, double* ms, double* bytes);
 }  // namespace pfmp
 
@@ -42,7 +58,14 @@ using namespace pfmp;
 static void check_prec(int prec) { PFMP_REQUIRE(prec == PFMP_F64 || prec == PFMP_F32, PFMP_E_INVALID, "bad precision"); }
 static void check_where(int w) { PFMP_REQUIRE(w == PFMP_HOST || w == PFMP_DEVICE, PFMP_E_INVALID, "bad location"); }
 
-static void op_free(pfmp_op* op) {
+namespace pfmp {
+void op_delete(pfmp_op* op);
+pfmp_op* op_new(pfmp_ctx* ctx, double kappa, double csw);
+}
+
+static void op_free(pfmp_op* op) { op_delete(op); }
+
+void pfmp::op_delete(pfmp_op* op) {
   if (!op) return;
   for (int p = 0; p < 2; ++p) {
     dev_free(op->clov64[p]);
@@ -56,10 +79,39 @@ static void op_free(pfmp_op* op) {
   for (int k = 0; k < 4; ++k) dev_free(op->cg32[k]);
   dev_free(op->scal);
   if (op->h_scal) cudaFreeHost(op->h_scal);
+  ms_work_free(op);
   for (auto& G : op->graph)
     if (G.exec) cudaGraphExecDestroy(G.exec);
   if (op->cap) cudaStreamDestroy(op->cap);
   delete op;
+}
+
+pfmp_op* pfmp::op_new(pfmp_ctx* ctx, double kappa, double csw) {
+  PFMP_REQUIRE(kappa > 0 && csw >= 0, PFMP_E_INVALID, "kappa must be > 0 and c_sw >= 0");
+  pfmp_op* op = new pfmp_op();
+  op->ctx = ctx;
+  op->kappa = kappa;
+  op->csw = csw;
+  try {
+    const Geom& g = ctx->g;
+    for (int p = 0; p < 2; ++p) {
+      op->clov64[p] = (double2*)dev_alloc((size_t)g.Vh * 36 * sizeof(double2));
+      op->clov32[p] = (float4*)dev_alloc((size_t)g.Vh * 18 * sizeof(float4));
+    }
+    op->t64 = (double2*)dev_alloc(spinor_bytes(g, PFMP_F64));
+    op->e64 = (double2*)dev_alloc(spinor_bytes(g, PFMP_F64));
+    op->t32 = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
+    op->e32 = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
+    for (int k = 0; k < 6; ++k) op->cg64[k] = (double2*)dev_alloc(spinor_bytes(g, PFMP_F64));
+    for (int k = 0; k < 4; ++k) op->cg32[k] = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
+    op->scal = (CGScalars*)dev_alloc(sizeof(CGScalars));
+    PFMP_CUDA(cudaMallocHost(&op->h_scal, sizeof(CGScalars)));
+    clover_build(op);
+  } catch (...) {
+    op_delete(op);
+    throw;
+  }
+  return op;
 }
 
 extern "C" {
@@ -160,31 +212,7 @@ int pfmp_spinor_unpack(pfmp_ctx* ctx, double* dst, int where, const void* src, i
 int pfmp_op_create(pfmp_ctx* ctx, double kappa, double csw, pfmp_op** out) {
   API_BEGIN
   PFMP_REQUIRE(ctx && out, PFMP_E_INVALID, "null argument");
-  PFMP_REQUIRE(kappa > 0 && csw >= 0, PFMP_E_INVALID, "kappa must be > 0 and c_sw >= 0");
-  pfmp_op* op = new pfmp_op();
-  op->ctx = ctx;
-  op->kappa = kappa;
-  op->csw = csw;
-  try {
-    const Geom& g = ctx->g;
-    for (int p = 0; p < 2; ++p) {
-      op->clov64[p] = (double2*)dev_alloc((size_t)g.Vh * 36 * sizeof(double2));
-      op->clov32[p] = (float4*)dev_alloc((size_t)g.Vh * 18 * sizeof(float4));
-    }
-    op->t64 = (double2*)dev_alloc(spinor_bytes(g, PFMP_F64));
-    op->e64 = (double2*)dev_alloc(spinor_bytes(g, PFMP_F64));
-    op->t32 = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
-    op->e32 = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
-    for (int k = 0; k < 6; ++k) op->cg64[k] = (double2*)dev_alloc(spinor_bytes(g, PFMP_F64));
-    for (int k = 0; k < 4; ++k) op->cg32[k] = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
-    op->scal = (CGScalars*)dev_alloc(sizeof(CGScalars));
-    PFMP_CUDA(cudaMallocHost(&op->h_scal, sizeof(CGScalars)));
-    clover_build(op);
-  } catch (...) {
-    op_free(op);
-    throw;
-  }
-  *out = op;
+  *out = op_new(ctx, kappa, csw);
   API_END
 }
 
@@ -325,6 +353,174 @@ int pfmp_solve_host(pfmp_op* op, const pfmp_solver_params* prm, double* x_host, 
   int st = solve_impl(op, prm, x, b, info);
   spinor_unpack_any(c, x_host, PFMP_HOST, x, PFMP_F64, 0);
   if (st != PFMP_OK) return st;
+  API_END
+}
+
+int pfmp_solve_multishift(pfmp_op* op, int nshift, const double* sre, const double* sim, void* const* x, const void* b,
+                          double tol, int max_iter, pfmp_solve_info* info) {
+  API_BEGIN
+  PFMP_REQUIRE(op && sre && sim && x && b && nshift >= 1, PFMP_E_INVALID, "bad argument");
+  for (int k = 0; k < nshift; ++k) PFMP_REQUIRE(x[k] && x[k] != b, PFMP_E_INVALID, "bad solution pointer");
+  std::vector<std::complex<double>> sig(nshift);
+  for (int k = 0; k < nshift; ++k) sig[k] = std::complex<double>(sre[k], sim[k]);
+  int it = 0;
+  double res = 0;
+  long kap = 0;
+  int st = solve_multishift(op, nshift, sig.data(), x, b, tol, max_iter, 8, &it, &res, &kap, info != nullptr);
+  if (info) {
+    info->iters = it;
+    info->reliable_updates = 0;
+    info->true_rel_res = res;
+    info->k_apply = kap;
+    info->status = st;
+  }
+  if (st != PFMP_OK) {
+    set_last_error(pfmp_strerror(st));
+    return st;
+  }
+  API_END
+}
+
+int pfmp_poly_roots(int n, double mu, double nu, double* zre, double* zim, double* an) {
+  API_BEGIN
+  PFMP_REQUIRE(n >= 1 && mu >= nu && nu > 0, PFMP_E_INVALID, "need n >= 1 and mu >= nu > 0");
+  auto z = cheb_roots(n, mu, nu);
+  for (int k = 0; k < n; ++k) {
+    if (zre) zre[k] = z[k].real();
+    if (zim) zim[k] = z[k].imag();
+  }
+  if (an) *an = cheb_norm(n, mu, nu);
+  API_END
+}
+
+int pfmp_poly_apply(pfmp_op* op, int n, double mu, double nu, int which, void* out, const void* in) {
+  API_BEGIN
+  PFMP_REQUIRE(op && out && in && out != in, PFMP_E_INVALID, "bad argument");
+  PFMP_REQUIRE(mu >= nu && nu > 0 && n >= 1, PFMP_E_INVALID, "need n >= 1 and mu >= nu > 0");
+  PFMP_REQUIRE(n % 2 == 0, PFMP_E_UNSUPPORTED, "odd polynomial orders are not supported");
+  PFMP_REQUIRE(which >= 0 && which <= 2, PFMP_E_INVALID, "which must be 0 (P), 1 (R) or 2 (R^dag)");
+  auto z = cheb_roots(n, mu, nu);
+  const double an = cheb_norm(n, mu, nu);
+  if (which == 0) {
+    poly_product(op, z, an, out, in);
+  } else {
+    std::vector<std::complex<double>> h;
+    for (auto zk : z)
+      if (zk.imag() < 0) h.push_back(which == 1 ? zk : std::conj(zk));
+    poly_product(op, h, std::sqrt(an), out, in);
+  }
+  API_END
+}
+
+int pfmp_action_create(pfmp_ctx* ctx, const pfmp_action_params* prm, pfmp_action** out) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && prm && out, PFMP_E_INVALID, "null argument");
+  *out = action_create(ctx, prm);
+  API_END
+}
+
+int pfmp_action_destroy(pfmp_action* A) {
+  API_BEGIN
+  action_destroy(A);
+  API_END
+}
+
+int pfmp_action_refresh(pfmp_action* A) {
+  API_BEGIN
+  PFMP_REQUIRE(A, PFMP_E_INVALID, "null action");
+  action_refresh(A);
+  API_END
+}
+
+int pfmp_action_heatbath(pfmp_action* A, const double* xi, int where) {
+  API_BEGIN
+  PFMP_REQUIRE(A && xi, PFMP_E_INVALID, "null argument");
+  check_where(where);
+  pfmp_ctx* c = action_ctx(A);
+  const size_t n = (size_t)c->g.V * 24;
+  std::vector<double2*> d(3, nullptr);
+  try {
+    for (int i = 0; i < 3; ++i) {
+      d[i] = (double2*)dev_alloc(spinor_bytes(c->g, PFMP_F64));
+      spinor_pack_any(c, d[i], PFMP_F64, xi + i * n, where, 0);
+    }
+    action_heatbath(A, d[0], d[1], d[2]);
+    PFMP_CUDA(cudaStreamSynchronize(c->stream));
+  } catch (...) {
+    for (auto p : d) dev_free(p);
+    throw;
+  }
+  for (auto p : d) dev_free(p);
+  API_END
+}
+
+int pfmp_action_get_phi(pfmp_action* A, int i, double* phi, int where) {
+  API_BEGIN
+  PFMP_REQUIRE(A && phi, PFMP_E_INVALID, "null argument");
+  check_where(where);
+  action_get_phi(A, i, phi, where);
+  API_END
+}
+
+int pfmp_action_set_phi(pfmp_action* A, int i, const double* phi, int where) {
+  API_BEGIN
+  PFMP_REQUIRE(A && phi, PFMP_E_INVALID, "null argument");
+  check_where(where);
+  action_set_phi(A, i, phi, where);
+  API_END
+}
+
+int pfmp_action_eval(pfmp_action* A, double S[5]) {
+  API_BEGIN
+  PFMP_REQUIRE(A && S, PFMP_E_INVALID, "null argument");
+  action_eval(A, S);
+  API_END
+}
+
+int pfmp_action_force(pfmp_action* A, int term, double* F, int where) {
+  API_BEGIN
+  PFMP_REQUIRE(A && F && term >= 0 && term < 5, PFMP_E_INVALID, "bad argument");
+  check_where(where);
+  action_force_out(A, term, F, where);
+  API_END
+}
+
+int pfmp_schedule_2mn(int n, double tau, double lambda, double* T, double* S) {
+  API_BEGIN
+  PFMP_REQUIRE(n >= 1 && T && S && tau > 0, PFMP_E_INVALID, "bad argument");
+  schedule_2mn(n, tau, lambda, T, S);
+  API_END
+}
+
+int pfmp_schedule_merge(int ns, const int* len, const double* T, const double* S, int cap, double* Tout, double* Sout,
+                        int* len_out) {
+  API_BEGIN
+  PFMP_REQUIRE(ns >= 1 && len && T && S && Tout && Sout && len_out && cap >= 1, PFMP_E_INVALID, "bad argument");
+  for (int i = 0; i < ns; ++i) PFMP_REQUIRE(len[i] >= 1, PFMP_E_INVALID, "empty scheme");
+  *len_out = schedule_merge(ns, len, T, S, cap, Tout, Sout);
+  API_END
+}
+
+int pfmp_trajectory(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int term_level[5],
+                    const double* mom, const double* xi, int where, double u, pfmp_traj_info* info) {
+  API_BEGIN
+  PFMP_REQUIRE(A && T && S && term_level && mom && xi && info, PFMP_E_INVALID, "null argument");
+  check_where(where);
+  pfmp_ctx* c = action_ctx(A);
+  const size_t n = (size_t)c->g.V * 24;
+  std::vector<double2*> d(3, nullptr);
+  try {
+    for (int i = 0; i < 3; ++i) {
+      d[i] = (double2*)dev_alloc(spinor_bytes(c->g, PFMP_F64));
+      spinor_pack_any(c, d[i], PFMP_F64, xi + i * n, where, 0);
+    }
+    const void* xs[3] = {d[0], d[1], d[2]};
+    trajectory(A, len, T, nlev, S, term_level, mom, where, xs, u, info);
+  } catch (...) {
+    for (auto p : d) dev_free(p);
+    throw;
+  }
+  for (auto p : d) dev_free(p);
   API_END
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <complex>
 #include <vector>
 
 #include "pfmp_internal.cuh"
@@ -26,6 +27,7 @@ struct CGScalars {
 }  // namespace pfmp
 
 namespace pfmp {
+struct MSWork;
 // CUDA-event timing of the stencil kernels (off unless pfmp_profile_begin was called)
 struct KernelProfile {
   bool on = false;
@@ -80,6 +82,8 @@ struct pfmp_op {
     long long kernels = 0;  // kernel nodes in the graph (for the launch counter)
   } graph[2];
   cudaStream_t cap = nullptr;
+  pfmp::MSWork* ms = nullptr;  // multi-shift workspace (grown on demand)
+  long long kapply = 0;         // K applications issued (graph replays not included)
 };
 
 namespace pfmp {
@@ -109,6 +113,17 @@ void mhat(pfmp_op* op, int prec, void* out, const void* in, bool dagger, double*
           CGScalars* scal);
 void kop(pfmp_op* op, int prec, void* out, const void* in, double* pKp_dev, CGScalars* scal);
 
+void hop_clov_odd(pfmp_op* op, void* out, const void* in, bool dagger);
+
+// force.cu
+void force_hop(pfmp_ctx* c, double* F, int pz, const void* Lf, const void* Rf, const void* Lb, const void* Rb,
+               double coef);
+void clover_insert(pfmp_ctx* c, double* Hc, int p, const void* a, const void* b, double coef);
+void clover_insert_det(pfmp_op* op, double* Hc, double coef);
+void clover_force(pfmp_ctx* c, double* F, const double* Hc);
+void gauge_force(pfmp_ctx* c, double* F, double beta);
+void deriv_mhat(pfmp_op* op, double* F, double* Hc, const void* a, const void* b, double coef, void* y, void* w);
+
 // blas.cu
 void blas_zero(pfmp_ctx* c, int prec, void* x);
 void blas_copy(pfmp_ctx* c, void* dst, int dprec, const void* src, int sprec);
@@ -122,6 +137,15 @@ void cg_step_xr(pfmp_ctx* c, int prec, void* x, void* r, const void* p, const vo
 void cg_step_p(pfmp_ctx* c, int prec, void* p, const void* r, CGScalars* s);
 // x64 += x32 (accumulate the sloppy solution)
 void blas_add_lo(pfmp_ctx* c, void* x64, const void* x32);
+
+// multishift.cu
+void caxpby(pfmp_ctx* c, std::complex<double> a, const void* x, std::complex<double> b, void* y);
+int solve_multishift(pfmp_op* op, int ns, const std::complex<double>* sigma, void* const* x, const void* b, double tol,
+                     int max_iter, int check, int* iters, double* max_true_res, long* kapply, bool want_true_res);
+void ms_work_free(pfmp_op* op);
+std::vector<std::complex<double>> cheb_roots(int n, double mu, double nu);
+double cheb_norm(int n, double mu, double nu);
+void poly_product(pfmp_op* op, const std::vector<std::complex<double>>& z, double scale, void* out, const void* in);
 
 // solver.cu
 int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int check_every, void* x,

@@ -12,6 +12,7 @@
 // M-hat^dag = A_ee - kappa^2 H^dag_eo A_oo^{-1} H^dag_oe.
 #include "context.h"
 #include "fields.cuh"
+#include "spin.cuh"
 
 namespace pfmp {
 
@@ -32,79 +33,6 @@ struct HopParams {
   double* norm_out;  // ||out||^2 (device) when reducing
   CGScalars* scal;   // optional: alpha = rr / ||out||^2; skip all work once done
 };
-
-// ---------------------------------------------------------------- spin projection
-// half spinor of (1 + S g_MU) psi, and the rebuild of the full result from it
-template <int MU, int S, typename T>
-__device__ __forceinline__ Half<T> project(const Spinor<T>& p) {
-  Half<T> h;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (MU == 0) {
-      h.h[0][c] = S > 0 ? p.s[0][c] + times_i(p.s[3][c]) : p.s[0][c] - times_i(p.s[3][c]);
-      h.h[1][c] = S > 0 ? p.s[1][c] + times_i(p.s[2][c]) : p.s[1][c] - times_i(p.s[2][c]);
-    } else if (MU == 1) {
-      h.h[0][c] = S > 0 ? p.s[0][c] - p.s[3][c] : p.s[0][c] + p.s[3][c];
-      h.h[1][c] = S > 0 ? p.s[1][c] + p.s[2][c] : p.s[1][c] - p.s[2][c];
-    } else if (MU == 2) {
-      h.h[0][c] = S > 0 ? p.s[0][c] + times_i(p.s[2][c]) : p.s[0][c] - times_i(p.s[2][c]);
-      h.h[1][c] = S > 0 ? p.s[1][c] - times_i(p.s[3][c]) : p.s[1][c] + times_i(p.s[3][c]);
-    } else {
-      h.h[0][c] = S > 0 ? p.s[0][c] + p.s[2][c] : p.s[0][c] - p.s[2][c];
-      h.h[1][c] = S > 0 ? p.s[1][c] + p.s[3][c] : p.s[1][c] - p.s[3][c];
-    }
-  }
-  return h;
-}
-
-template <int MU, int S, typename T>
-__device__ __forceinline__ void accumulate(Spinor<T>& a, const Half<T>& h) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    a.s[0][c] = a.s[0][c] + h.h[0][c];
-    a.s[1][c] = a.s[1][c] + h.h[1][c];
-    if (MU == 0) {  // r2 = -S i h1, r3 = -S i h0
-      a.s[2][c] = S > 0 ? a.s[2][c] + times_mi(h.h[1][c]) : a.s[2][c] + times_i(h.h[1][c]);
-      a.s[3][c] = S > 0 ? a.s[3][c] + times_mi(h.h[0][c]) : a.s[3][c] + times_i(h.h[0][c]);
-    } else if (MU == 1) {  // r2 = S h1, r3 = -S h0
-      a.s[2][c] = S > 0 ? a.s[2][c] + h.h[1][c] : a.s[2][c] - h.h[1][c];
-      a.s[3][c] = S > 0 ? a.s[3][c] - h.h[0][c] : a.s[3][c] + h.h[0][c];
-    } else if (MU == 2) {  // r2 = -S i h0, r3 = S i h1
-      a.s[2][c] = S > 0 ? a.s[2][c] + times_mi(h.h[0][c]) : a.s[2][c] + times_i(h.h[0][c]);
-      a.s[3][c] = S > 0 ? a.s[3][c] + times_i(h.h[1][c]) : a.s[3][c] + times_mi(h.h[1][c]);
-    } else {  // r2 = S h0, r3 = S h1
-      a.s[2][c] = S > 0 ? a.s[2][c] + h.h[0][c] : a.s[2][c] - h.h[0][c];
-      a.s[3][c] = S > 0 ? a.s[3][c] + h.h[1][c] : a.s[3][c] - h.h[1][c];
-    }
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ Half<T> mul_half(const Mat3<T>& U, const Half<T>& h) {
-  Half<T> r;
-#pragma unroll
-  for (int k = 0; k < 2; ++k)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) r.h[k][i] = U.m[i][0] * h.h[k][0] + U.m[i][1] * h.h[k][1] + U.m[i][2] * h.h[k][2];
-  return r;
-}
-template <typename T>
-__device__ __forceinline__ Half<T> mul_half_dag(const Mat3<T>& U, const Half<T>& h) {
-  Half<T> r;
-#pragma unroll
-  for (int k = 0; k < 2; ++k)
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-      r.h[k][i] = cj_mul(U.m[0][i], h.h[k][0]) + cj_mul(U.m[1][i], h.h[k][1]) + cj_mul(U.m[2][i], h.h[k][2]);
-  return r;
-}
-template <typename T>
-__device__ __forceinline__ void scale_half(Half<T>& h, T s) {
-#pragma unroll
-  for (int k = 0; k < 2; ++k)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) h.h[k][i] = s * h.h[k][i];
-}
 
 // forward (x+mu, projector 1 + SF g) and backward (x-mu, projector 1 - SF g) terms
 template <int PREC, int MU, int SF>
@@ -360,8 +288,21 @@ void mhat(pfmp_op* op, int prec, void* out, const void* in, bool dagger, double*
     mhat_t<PFMP_F32>(op, out, in, dagger, norm_out, scal);
 }
 
+// out (odd) = A_oo^{-1} H_oe in (or the adjoint hop), FP64: the first half of M-hat,
+// used by the force terms
+void hop_clov_odd(pfmp_op* op, void* out, const void* in, bool dagger) {
+  require_clover(op);
+  auto a = params<PFMP_F64>(op, 1, out, in);
+  a.clov = clov_ptr<PFMP_F64>(op, 1);
+  if (dagger)
+    launch<PFMP_F64, true, EPI_CLOV, false>(a, op->ctx);
+  else
+    launch<PFMP_F64, false, EPI_CLOV, false>(a, op->ctx);
+}
+
 // out = K in; <in, K in> = ||M-hat in||^2 is reduced in the second kernel of M-hat
 void kop(pfmp_op* op, int prec, void* out, const void* in, double* pKp_dev, CGScalars* scal) {
+  op->kapply += 1;
   void* e = prec == PFMP_F64 ? (void*)op->e64 : (void*)op->e32;
   mhat(op, prec, e, in, false, pKp_dev, scal);
   mhat(op, prec, out, e, true, nullptr, scal);

@@ -1,0 +1,373 @@
+// Fermion, clover and gauge forces (App. C), accumulated in FP64 as algebra coefficients
+// f[p][mu][a][cb] = dS/d omega_a for U_mu(x) -> exp(i omega_a T_a) U_mu(x).
+//
+// The fermion forces of App. C are sums of contractions Re[eta^dag (dK/dU) chi].  With
+// K = M-hat^dag M-hat:
+//   Re eta^dag dK chi = Re (M-hat chi)^dag dM-hat eta + Re (M-hat eta)^dag dM-hat chi,
+// and with M-hat = A_ee - kappa^2 H_eo A_oo^{-1} H_oe,
+//   a^dag dM-hat b = a^dag dA_ee b - kappa^2 [a^dag dH_eo y + w^dag dH_oe b - w^dag dA_oo y],
+//   y = A_oo^{-1} H_oe b,  w = A_oo^{-1} H^dag_oe a.
+// Hop terms: for a link U_mu(z) the forward term a(z)^dag (1 - g_mu) dU b(z+mu) and the
+// backward term a(z+mu)^dag (1 + g_mu) dU^dag b(z) give, with dU = i w T U,
+//   d/dw_a = i tr(T_a Z),  Z = sum_s (U R_f)_s ((1 - g_mu) L_f)_s^dag - sum_s R_b,s (U (1 + g_mu) L_b)_s^dag.
+// Clover terms: a^dag (sigma (x) dF) b = tr_c(dF G), G = sum_{s s'} sigma_{s s'} b_s' a_s^dag;
+// with F = traceless part of (Q - Q^dag)/(8i),
+//   Re tr(dF G) = (1/8) Im tr(dQ H),  H = G~ + G~^dag (G~ traceless),
+// so each site keeps one Hermitian traceless H per plane (8 reals) summed over every
+// term, and one final kernel differentiates the clover leaves: for U_mu(z) in the plane
+// (mu, nu) with corners z, z+mu, z+mu+nu, z+nu (above) and z-nu, z-nu+mu (below),
+//   d/dw_a = (1/8) Re tr(T_a [U X_above - Y_below U^dag]),
+//   X_above = H(z+mu) V1 V2 V3 + V1 H(z+mu+nu) V2 V3 + V1 V2 H(z+nu) V3 + V1 V2 V3 H(z),
+//   Y_below = H(z) W1 W2 W3 + W1 H(z-nu) W2 W3 + W1 W2 H(z-nu+mu) W3 + W1 W2 W3 H(z+mu),
+//   V1 = U_nu(z+mu), V2 = U_mu(z+nu)^dag, V3 = U_nu(z)^dag,
+//   W1 = U_nu(z-nu)^dag, W2 = U_mu(z-nu), W3 = U_nu(z-nu+mu).
+// Gauge force (Wilson action, beta/3 normalisation): d/dw_a = (beta/3) Im tr(T_a U S),
+// S the sum of the six staples.
+#include <cmath>
+
+#include "context.h"
+#include "fields.cuh"
+#include "spin.cuh"
+
+namespace pfmp {
+
+constexpr double kInvSqrt3 = 0.57735026918962576451;
+
+// c_a = tr(lambda_a M), a = 1..8 (complex)
+__device__ __forceinline__ void tr_lambda(const Mat3<double>& M, cplx<double> t[8]) {
+  t[0] = M.m[1][0] + M.m[0][1];
+  t[1] = times_i(M.m[0][1] - M.m[1][0]);
+  t[2] = M.m[0][0] - M.m[1][1];
+  t[3] = M.m[2][0] + M.m[0][2];
+  t[4] = times_i(M.m[0][2] - M.m[2][0]);
+  t[5] = M.m[2][1] + M.m[1][2];
+  t[6] = times_i(M.m[1][2] - M.m[2][1]);
+  t[7] = kInvSqrt3 * (M.m[0][0] + M.m[1][1] - 2.0 * M.m[2][2]);
+}
+
+// H = sum_a h_a T_a (Hermitian traceless)
+__device__ __forceinline__ Mat3<double> from_algebra(const double h[8]) {
+  Mat3<double> H;
+  const double s = 0.5;
+  H.m[0][0] = mk(s * (h[2] + kInvSqrt3 * h[7]), 0.0);
+  H.m[1][1] = mk(s * (-h[2] + kInvSqrt3 * h[7]), 0.0);
+  H.m[2][2] = mk(s * (-2.0 * kInvSqrt3 * h[7]), 0.0);
+  H.m[0][1] = mk(s * h[0], -s * h[1]);
+  H.m[1][0] = mk(s * h[0], s * h[1]);
+  H.m[0][2] = mk(s * h[3], -s * h[4]);
+  H.m[2][0] = mk(s * h[3], s * h[4]);
+  H.m[1][2] = mk(s * h[5], -s * h[6]);
+  H.m[2][1] = mk(s * h[5], s * h[6]);
+  return H;
+}
+
+__device__ __forceinline__ Mat3<double> mlink(const double2* U, const Geom& g, const int x[4], int mu) {
+  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+  Mat3<double> M;
+  load_link18(M, U + (size_t)((p * 4 + mu) * 9) * g.Vh, cb_index(g, x), g.Vh);
+  return M;
+}
+__device__ __forceinline__ void shift(const Geom& g, const int x[4], int mu, int d, int y[4]) {
+  for (int k = 0; k < 4; ++k) y[k] = x[k];
+  y[mu] = (y[mu] + d + g.L[mu]) % g.L[mu];
+}
+
+__device__ __forceinline__ double* fptr(double* F, const Geom& g, int p, int mu, int a) {
+  return F + (size_t)((p * 4 + mu) * 8 + a) * g.Vh;
+}
+
+// outer product sum_s u_s v_s^dag over 4 spins
+__device__ __forceinline__ Mat3<double> outer(const Spinor<double>& u, const Spinor<double>& v) {
+  Mat3<double> M;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      cplx<double> s = mk(0.0, 0.0);
+      for (int k = 0; k < 4; ++k) s = s + mul_cj(u.s[k][i], v.s[k][j]);
+      M.m[i][j] = s;
+    }
+  return M;
+}
+
+// (1 + S g_MU) psi as a full spinor
+template <int MU, int S>
+__device__ __forceinline__ Spinor<double> proj_full(const Spinor<double>& p) {
+  Spinor<double> r;
+  for (int s = 0; s < 4; ++s)
+    for (int c = 0; c < 3; ++c) r.s[s][c] = mk(0.0, 0.0);
+  accumulate<MU, S>(r, project<MU, S>(p));
+  return r;
+}
+
+__device__ __forceinline__ Spinor<double> umul(const Mat3<double>& U, const Spinor<double>& v) {
+  Spinor<double> r;
+  for (int s = 0; s < 4; ++s)
+    for (int i = 0; i < 3; ++i) r.s[s][i] = U.m[i][0] * v.s[s][0] + U.m[i][1] * v.s[s][1] + U.m[i][2] * v.s[s][2];
+  return r;
+}
+
+template <int MU>
+__device__ void hop_force_dir(double* F, const double2* U64, const Geom& g, int pz, int cb, const int z[4],
+                              const double2* Lf, const double2* Rf, const double2* Lb, const double2* Rb, double coef) {
+  const Mat3<double> U = mlink(U64, g, z, MU);
+  const int n = nbr_cb(g, z, MU, +1);
+  Spinor<double> lf, rf, lb, rb;
+  load_spinor(lf, Lf, cb, g.Vh);
+  load_spinor(rf, Rf, n, g.Vh);
+  load_spinor(lb, Lb, n, g.Vh);
+  load_spinor(rb, Rb, cb, g.Vh);
+  // Y_f = sum_s (U R_f)_s ((1 - g) L_f)_s^dag,  Y_b = sum_s R_b,s (U (1 + g) L_b)_s^dag
+  Mat3<double> Yf = outer(umul(U, rf), proj_full<MU, -1>(lf));
+  Mat3<double> Yb = outer(rb, umul(U, proj_full<MU, +1>(lb)));
+  double c = coef;
+  if (MU == 3 && z[3] == g.L[3] - 1) c *= g.bc_t;
+  Mat3<double> Z;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Z.m[i][j] = Yf.m[i][j] - Yb.m[i][j];
+  cplx<double> t[8];
+  tr_lambda(Z, t);
+  // Re(i tr(T_a Z)) = -Im tr(T_a Z) = -(1/2) Im tr(lambda_a Z)
+  for (int a = 0; a < 8; ++a) fptr(F, g, pz, MU, a)[cb] += -0.5 * c * t[a].im;
+}
+
+__global__ void k_force_hop(double* F, const double2* U64, Geom g, int pz, const double2* Lf, const double2* Rf,
+                            const double2* Lb, const double2* Rb, double coef) {
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  int z[4];
+  cb_coords(g, cb, pz, z);
+  hop_force_dir<0>(F, U64, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
+  hop_force_dir<1>(F, U64, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
+  hop_force_dir<2>(F, U64, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
+  hop_force_dir<3>(F, U64, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
+}
+
+// G for the six planes from the chiral Pauli structure of sigma_{mu nu}:
+// P1 = O01 + O10, P2 = -i O01 + i O10, P3 = O00 - O11 per chiral block B, O_ij = b_{2B+j} a_{2B+i}^dag;
+// planes (01,02,03,12,13,23) = (P3+ + P3-, P2+ + P2-, -P1+ + P1-, P1+ + P1-, P2+ - P2-, -P3+ + P3-)
+__device__ void plane_G(const Spinor<double>& a, const Spinor<double>& b, Mat3<double> G[6]) {
+  Mat3<double> P[2][3];
+  for (int B = 0; B < 2; ++B) {
+    Mat3<double> O[2][2];
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j)
+        for (int c = 0; c < 3; ++c)
+          for (int d = 0; d < 3; ++d) O[i][j].m[c][d] = mul_cj(b.s[2 * B + j][c], a.s[2 * B + i][d]);
+    for (int c = 0; c < 3; ++c)
+      for (int d = 0; d < 3; ++d) {
+        P[B][0].m[c][d] = O[0][1].m[c][d] + O[1][0].m[c][d];
+        P[B][1].m[c][d] = times_i(O[1][0].m[c][d] - O[0][1].m[c][d]);
+        P[B][2].m[c][d] = O[0][0].m[c][d] - O[1][1].m[c][d];
+      }
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int d = 0; d < 3; ++d) {
+      G[0].m[c][d] = P[0][2].m[c][d] + P[1][2].m[c][d];
+      G[1].m[c][d] = P[0][1].m[c][d] + P[1][1].m[c][d];
+      G[2].m[c][d] = P[1][0].m[c][d] - P[0][0].m[c][d];
+      G[3].m[c][d] = P[0][0].m[c][d] + P[1][0].m[c][d];
+      G[4].m[c][d] = P[0][1].m[c][d] - P[1][1].m[c][d];
+      G[5].m[c][d] = P[1][2].m[c][d] - P[0][2].m[c][d];
+    }
+}
+
+__device__ __forceinline__ double* hptr(double* Hc, const Geom& g, int p, int plane, int a) {
+  return Hc + (size_t)((p * 6 + plane) * 8 + a) * g.Vh;
+}
+
+// Hc[p] += coef (G~ + G~^dag) for G(a, b): h_a += 4 coef Re tr(T_a G) = 2 coef Re tr(lambda_a G)
+__global__ void k_clover_insert(double* Hc, Geom g, int p, const double2* A, const double2* B, double coef) {
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  Spinor<double> a, b;
+  load_spinor(a, A, cb, g.Vh);
+  load_spinor(b, B, cb, g.Vh);
+  Mat3<double> G[6];
+  plane_G(a, b, G);
+  for (int pl = 0; pl < 6; ++pl) {
+    cplx<double> t[8];
+    tr_lambda(G[pl], t);
+    for (int k = 0; k < 8; ++k) hptr(Hc, g, p, pl, k)[cb] += 2.0 * coef * t[k].re;
+  }
+}
+
+// Hc[odd] += coef (G~ + G~^dag) with G = sum_{ij} sigma_{ji} Ainv_block(i, j) (det force)
+__global__ void k_clover_insert_det(double* Hc, Geom g, const double2* Ainv, double coef) {
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  HermBlock<double> B[2];
+  load_clover(B, Ainv, cb, g.Vh);
+  // full 6x6 blocks
+  Mat3<double> P[2][3];
+  for (int blk = 0; blk < 2; ++blk) {
+    cplx<double> M[6][6];
+    for (int i = 0; i < 6; ++i) M[i][i] = mk(B[blk].d[i], 0.0);
+    for (int i = 1; i < 6; ++i)
+      for (int j = 0; j < i; ++j) {
+        M[i][j] = B[blk].o[tri_index(i, j)];
+        M[j][i] = conj(M[i][j]);
+      }
+    // colour block (i, j) of spins (2 blk + i, 2 blk + j): M[3i + c][3j + d]
+    // G = sum_{ij} sigma_{ji} X_ij; sigma_k blocks: s1 -> X01 + X10, s2 -> i X01 - i X10, s3 -> X00 - X11
+    // (sigma_{ji}: s2_{10} = i multiplies X_01, s2_{01} = -i multiplies X_10)
+    for (int c = 0; c < 3; ++c)
+      for (int d = 0; d < 3; ++d) {
+        cplx<double> x00 = M[c][d], x01 = M[c][3 + d], x10 = M[3 + c][d], x11 = M[3 + c][3 + d];
+        P[blk][0].m[c][d] = x01 + x10;
+        P[blk][1].m[c][d] = times_i(x01 - x10);
+        P[blk][2].m[c][d] = x00 - x11;
+      }
+  }
+  Mat3<double> G[6];
+  for (int c = 0; c < 3; ++c)
+    for (int d = 0; d < 3; ++d) {
+      G[0].m[c][d] = P[0][2].m[c][d] + P[1][2].m[c][d];
+      G[1].m[c][d] = P[0][1].m[c][d] + P[1][1].m[c][d];
+      G[2].m[c][d] = P[1][0].m[c][d] - P[0][0].m[c][d];
+      G[3].m[c][d] = P[0][0].m[c][d] + P[1][0].m[c][d];
+      G[4].m[c][d] = P[0][1].m[c][d] - P[1][1].m[c][d];
+      G[5].m[c][d] = P[1][2].m[c][d] - P[0][2].m[c][d];
+    }
+  for (int pl = 0; pl < 6; ++pl) {
+    cplx<double> t[8];
+    tr_lambda(G[pl], t);
+    for (int k = 0; k < 8; ++k) hptr(Hc, g, 1, pl, k)[cb] += 2.0 * coef * t[k].re;
+  }
+}
+
+__device__ __forceinline__ Mat3<double> load_H(const double* Hc, const Geom& g, const int x[4], int plane, double sgn) {
+  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+  const int cb = cb_index(g, x);
+  double h[8];
+  for (int a = 0; a < 8; ++a) h[a] = sgn * Hc[(size_t)((p * 6 + plane) * 8 + a) * g.Vh + cb];
+  return from_algebra(h);
+}
+
+__device__ __forceinline__ int plane_index(int mu, int nu) {
+  // (0,1)=0 (0,2)=1 (0,3)=2 (1,2)=3 (1,3)=4 (2,3)=5
+  const int a = mu < nu ? mu : nu, b = mu < nu ? nu : mu;
+  return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
+}
+
+// F[p] += (1/8) Re tr(T_a [U X_above - Y_below U^dag]) summed over the three planes
+__global__ void k_clover_force(double* F, const double2* U64, const double* Hc, Geom g, int p) {
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  int z[4];
+  cb_coords(g, cb, p, z);
+  for (int mu = 0; mu < 4; ++mu) {
+    const Mat3<double> U = mlink(U64, g, z, mu);
+    Mat3<double> Zs = mat_zero<double>();
+    for (int nu = 0; nu < 4; ++nu) {
+      if (nu == mu) continue;
+      const int pl = plane_index(mu, nu);
+      const double sg = mu < nu ? 1.0 : -1.0;
+      int zpm[4], zpmpn[4], zpn[4], zmn[4], zmnpm[4];
+      shift(g, z, mu, 1, zpm);
+      shift(g, zpm, nu, 1, zpmpn);
+      shift(g, z, nu, 1, zpn);
+      shift(g, z, nu, -1, zmn);
+      shift(g, zmn, mu, 1, zmnpm);
+      const Mat3<double> V1 = mlink(U64, g, zpm, nu);
+      const Mat3<double> V2 = dagger(mlink(U64, g, zpn, mu));
+      const Mat3<double> V3 = dagger(mlink(U64, g, z, nu));
+      const Mat3<double> W1 = dagger(mlink(U64, g, zmn, nu));
+      const Mat3<double> W2 = mlink(U64, g, zmn, mu);
+      const Mat3<double> W3 = mlink(U64, g, zmnpm, nu);
+      const Mat3<double> V12 = matmul(V1, V2), V23 = matmul(V2, V3), V123 = matmul(V12, V3);
+      const Mat3<double> W12 = matmul(W1, W2), W23 = matmul(W2, W3), W123 = matmul(W12, W3);
+      Mat3<double> X = matmul(load_H(Hc, g, zpm, pl, sg), V123);
+      X = mat_add(X, matmul(matmul(V1, load_H(Hc, g, zpmpn, pl, sg)), V23));
+      X = mat_add(X, matmul(matmul(V12, load_H(Hc, g, zpn, pl, sg)), V3));
+      X = mat_add(X, matmul(V123, load_H(Hc, g, z, pl, sg)));
+      Mat3<double> Y = matmul(load_H(Hc, g, z, pl, sg), W123);
+      Y = mat_add(Y, matmul(matmul(W1, load_H(Hc, g, zmn, pl, sg)), W23));
+      Y = mat_add(Y, matmul(matmul(W12, load_H(Hc, g, zmnpm, pl, sg)), W3));
+      Y = mat_add(Y, matmul(W123, load_H(Hc, g, zpm, pl, sg)));
+      const Mat3<double> A = matmul(U, X), B = matmul_nd(Y, U);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Zs.m[i][j] = Zs.m[i][j] + A.m[i][j] - B.m[i][j];
+    }
+    cplx<double> t[8];
+    tr_lambda(Zs, t);
+    // (1/8) Re tr(T_a Z) = (1/16) Re tr(lambda_a Z)
+    for (int a = 0; a < 8; ++a) fptr(F, g, p, mu, a)[cb] += 0.0625 * t[a].re;
+  }
+}
+
+// F += (beta/3) Im tr(T_a U S) = (beta/6) Im tr(lambda_a U S)
+__global__ void k_gauge_force(double* F, const double2* U64, Geom g, int p, double beta) {
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  int z[4];
+  cb_coords(g, cb, p, z);
+  for (int mu = 0; mu < 4; ++mu) {
+    Mat3<double> S = mat_zero<double>();
+    int zpm[4];
+    shift(g, z, mu, 1, zpm);
+    for (int nu = 0; nu < 4; ++nu) {
+      if (nu == mu) continue;
+      int zpn[4], zmn[4], zpmmn[4];
+      shift(g, z, nu, 1, zpn);
+      shift(g, z, nu, -1, zmn);
+      shift(g, zpm, nu, -1, zpmmn);
+      // upper staple U_nu(z+mu) U_mu(z+nu)^dag U_nu(z)^dag
+      S = mat_add(S, matmul_nd(matmul_nd(mlink(U64, g, zpm, nu), mlink(U64, g, zpn, mu)), mlink(U64, g, z, nu)));
+      // lower staple U_nu(z+mu-nu)^dag U_mu(z-nu)^dag U_nu(z-nu)
+      S = mat_add(S, matmul(matmul_dn(mlink(U64, g, zpmmn, nu), dagger(mlink(U64, g, zmn, mu))), mlink(U64, g, zmn, nu)));
+    }
+    const Mat3<double> US = matmul(mlink(U64, g, z, mu), S);
+    cplx<double> t[8];
+    tr_lambda(US, t);
+    for (int a = 0; a < 8; ++a) fptr(F, g, p, mu, a)[cb] += beta / 6.0 * t[a].im;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+void force_hop(pfmp_ctx* c, double* F, int pz, const void* Lf, const void* Rf, const void* Lb, const void* Rb,
+               double coef) {
+  k_force_hop<<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(F, c->U64, c->g, pz, (const double2*)Lf,
+                                                            (const double2*)Rf, (const double2*)Lb,
+                                                            (const double2*)Rb, coef);
+  PFMP_CHECK_LAUNCH();
+}
+void clover_insert(pfmp_ctx* c, double* Hc, int p, const void* a, const void* b, double coef) {
+  k_clover_insert<<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(Hc, c->g, p, (const double2*)a, (const double2*)b,
+                                                                coef);
+  PFMP_CHECK_LAUNCH();
+}
+void clover_insert_det(pfmp_op* op, double* Hc, double coef) {
+  pfmp_ctx* c = op->ctx;
+  k_clover_insert_det<<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(Hc, c->g, op->clov64[1], coef);
+  PFMP_CHECK_LAUNCH();
+}
+void clover_force(pfmp_ctx* c, double* F, const double* Hc) {
+  for (int p = 0; p < 2; ++p) {
+    k_clover_force<<<nblocks(c->g.Vh, 64), 64, 0, c->stream>>>(F, c->U64, Hc, c->g, p);
+    PFMP_CHECK_LAUNCH();
+  }
+}
+void gauge_force(pfmp_ctx* c, double* F, double beta) {
+  for (int p = 0; p < 2; ++p) {
+    k_gauge_force<<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(F, c->U64, c->g, p, beta);
+    PFMP_CHECK_LAUNCH();
+  }
+}
+
+// Re[a^dag dM-hat b] * coef  ->  F (hop terms) and Hc (clover terms); a, b even FP64
+void deriv_mhat(pfmp_op* op, double* F, double* Hc, const void* a, const void* b, double coef, void* y, void* w) {
+  pfmp_ctx* c = op->ctx;
+  const double k2 = op->kappa * op->kappa;
+  const double kc = op->kappa * op->csw;
+  // y = A_oo^{-1} H_oe b, w = A_oo^{-1} H^dag_oe a (odd)
+  hop_clov_odd(op, y, b, false);
+  hop_clov_odd(op, w, a, true);
+  (void)c;
+  force_hop(c, F, 0, a, y, w, b, -k2 * coef);
+  force_hop(c, F, 1, w, b, a, y, -k2 * coef);
+  if (op->csw != 0.0) {
+    clover_insert(c, Hc, 0, a, b, -kc * coef);
+    clover_insert(c, Hc, 1, w, y, k2 * (-kc) * coef);
+  }
+}
+
+}  // namespace pfmp
