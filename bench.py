@@ -406,7 +406,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--delta", type=float, default=0.1, help="reliable-update threshold of the mixed solver")
+    ap.add_argument("--delta", type=float, default=1e-4, help="reliable-update threshold of the mixed solver")
     ap.add_argument("--chunk", type=int, default=8, help="CG iterations per CUDA-graph chunk")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only apply K (FP32) --kernel-reps times on --kernel-dims: the small case for ncu")
