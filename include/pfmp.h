@@ -259,6 +259,23 @@ int pfmp_trajectory(pfmp_action* action, int len, const double* T, int nlevels, 
                     const int term_level[5], const double* mom, const double* xi, int where, double u,
                     pfmp_traj_info* info);
 
+/* ---- batched solves ------------------------------------------------------------------
+ * Many independent systems K_s x = b (each operator on its own context: lattice, gauge
+ * field, kappa; nrhs[s] right-hand sides each, 1..64) solved together by grouped kernels:
+ * one launch per CG phase covers every (system, site block, rhs) tile, a chunk of
+ * iterations is one CUDA graph, FP32 iterations with FP64 reliable updates per rhs as in
+ * PFMP_SOLVER_CG_MIXED.  All contexts must live on the current device; the first
+ * operator's stream is used for everything during a solve.  x and b are the
+ * sum(nrhs) FP64 even device fields in system order.  pfmp_batch_tune times one graph
+ * replay for block sizes 64/128/256 and keeps the fastest (call before a solve; it
+ * overwrites the batch workspace).  infos (optional) receives one entry per rhs.       */
+typedef struct pfmp_batch pfmp_batch;
+int pfmp_batch_create(int nsys, pfmp_op* const* ops, const int* nrhs, pfmp_batch** batch);
+int pfmp_batch_destroy(pfmp_batch* batch);
+int pfmp_batch_tune(pfmp_batch* batch, int chunk, int* block, double* ms_per_chunk);
+int pfmp_batch_solve(pfmp_batch* batch, const pfmp_solver_params* params, void* const* x, const void* const* b,
+                     pfmp_solve_info* infos);
+
 /* ---- kernel timing (tracing) ------------------------------------------------------
  * pfmp_profile_begin: from now on every stencil launch of this context is bracketed by
  * CUDA events on the context's stream.  pfmp_profile_end (synchronises) stops recording

@@ -112,6 +112,10 @@ SIGNATURES = {
     "pfmp_schedule_2mn": (I, [I, D, D, DP, DP]),
     "pfmp_schedule_merge": (I, [I, C.POINTER(I), DP, DP, I, DP, DP, C.POINTER(I)]),
     "pfmp_trajectory": (I, [P, I, DP, I, DP, C.POINTER(I), P, P, I, D, C.POINTER(TrajInfo)]),
+    "pfmp_batch_create": (I, [I, C.POINTER(P), C.POINTER(I), C.POINTER(P)]),
+    "pfmp_batch_destroy": (I, [P]),
+    "pfmp_batch_tune": (I, [P, I, C.POINTER(I), DP]),
+    "pfmp_batch_solve": (I, [P, C.POINTER(SolverParams), C.POINTER(P), C.POINTER(P), C.POINTER(SolveInfo)]),
     "pfmp_profile_begin": (I, [P]),
     "pfmp_profile_end": (I, [P, I, C.POINTER(C.c_int64), DP, DP]),
 }
@@ -391,3 +395,32 @@ def pfmp_trajectory(a, T, S_levels, term_level, mom, xi, u, where=PFMP_HOST):
     check(lib().pfmp_trajectory(a, len(T), pT, np.asarray(S_levels).shape[0], pS, tl, _ptr(mom), _ptr(xi), where,
                                 float(u), C.byref(info)))
     return info
+
+
+def pfmp_batch_create(ops, nrhs):
+    h = P()
+    arr = (P * len(ops))(*[o.value if isinstance(o, P) else o for o in ops])
+    nr = (I * len(nrhs))(*nrhs)
+    check(lib().pfmp_batch_create(len(ops), arr, nr, C.byref(h)))
+    return h
+
+
+def pfmp_batch_destroy(b):
+    check(lib().pfmp_batch_destroy(b))
+
+
+def pfmp_batch_tune(b, chunk=8):
+    blk, ms = I(), C.c_double()
+    check(lib().pfmp_batch_tune(b, chunk, C.byref(blk), C.byref(ms)))
+    return blk.value, ms.value
+
+
+def pfmp_batch_solve(b, params, xs, bs, raise_on_error=True):
+    n = len(xs)
+    xa = (P * n)(*[_ptr(v) for v in xs])
+    ba = (P * n)(*[_ptr(v) for v in bs])
+    infos = (SolveInfo * n)()
+    st = lib().pfmp_batch_solve(b, C.byref(params), xa, ba, infos)
+    if raise_on_error:
+        check(st)
+    return list(infos)

@@ -32,6 +32,11 @@ int schedule_merge(int ns, const int* len, const double* T, const double* S, int
 void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int term_level[5],
                 const double* mom, int where, const void* const xi[3], double u, pfmp_traj_info* info);
 pfmp_ctx* action_ctx(pfmp_action* A);
+pfmp_batch* batch_create(int nsys, pfmp_op* const* ops, const int* nrhs);
+void batch_destroy(pfmp_batch* B);
+int batch_solve(pfmp_batch* B, double tol, int max_iter, double delta, int check, void* const* x, const void* const* b,
+                pfmp_solve_info* infos);
+int batch_tune(pfmp_batch* B, int chunk, double* best_ms);
 void profile_end(pfmp_ctx* c, int cls, long* launches, double* ms, double* bytes);
 }  // namespace pfmp
 
@@ -521,6 +526,39 @@ int pfmp_trajectory(pfmp_action* A, int len, const double* T, int nlev, const do
     throw;
   }
   for (auto p : d) dev_free(p);
+  API_END
+}
+
+int pfmp_batch_create(int nsys, pfmp_op* const* ops, const int* nrhs, pfmp_batch** out) {
+  API_BEGIN
+  PFMP_REQUIRE(out, PFMP_E_INVALID, "null argument");
+  *out = batch_create(nsys, ops, nrhs);
+  API_END
+}
+
+int pfmp_batch_destroy(pfmp_batch* B) {
+  API_BEGIN
+  batch_destroy(B);
+  API_END
+}
+
+int pfmp_batch_tune(pfmp_batch* B, int chunk, int* block, double* ms) {
+  API_BEGIN
+  PFMP_REQUIRE(B && chunk >= 1, PFMP_E_INVALID, "bad argument");
+  int bl = batch_tune(B, chunk, ms);
+  if (block) *block = bl;
+  API_END
+}
+
+int pfmp_batch_solve(pfmp_batch* B, const pfmp_solver_params* prm, void* const* x, const void* const* b,
+                     pfmp_solve_info* infos) {
+  API_BEGIN
+  PFMP_REQUIRE(B && prm && x && b, PFMP_E_INVALID, "null argument");
+  int st = batch_solve(B, prm->tol, prm->max_iter, prm->delta, prm->check_every, x, b, infos);
+  if (st != PFMP_OK) {
+    set_last_error(pfmp_strerror(st));
+    return st;
+  }
   API_END
 }
 

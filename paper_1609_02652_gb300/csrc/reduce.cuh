@@ -73,3 +73,42 @@ __device__ __forceinline__ bool grid_sum(double v[N], ReduceBuf rb, double out[N
 }
 
 }  // namespace pfmp
+
+namespace pfmp {
+
+// The same deterministic sum over a group of blocks that belong together (e.g. one
+// system of a batch): block `idx` of `nblk` writes its partials to partials[idx*N..],
+// takes a ticket from *ticket, and the last one adds the partials in index order.
+template <int N>
+__device__ __forceinline__ bool group_sum(double v[N], double* partials, unsigned* ticket, unsigned nblk, unsigned idx,
+                                          double out[N]) {
+  __shared__ double sh[N * 32];
+  __shared__ bool last;
+  block_sum<N>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) partials[(size_t)idx * N + k] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    last = (t == nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double w[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) w[k] = 0.0;
+  for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] += ((volatile double*)partials)[(size_t)b * N + k];
+  block_sum<N>(w, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = w[k];
+    *ticket = 0u;
+    return true;
+  }
+  return false;
+}
+
+}  // namespace pfmp
