@@ -50,3 +50,19 @@ def uniform_range(seed, lo, hi, n):
 
 def integers(seed, lo, hi, n):
     return _rng(seed, 6).integers(lo, hi + 1, n)
+
+
+def nn_weights(channels, seed, scale=0.3):
+    """Initial weights of the gauge-covariant network: per layer a complex array
+    W[9][c_out][c_in][4][4] of Gaussians scaled by scale / (4 sqrt(9 c_in)), with the
+    identity added to the on-site 4x4 block of matching channels (c < min(c_in, c_out))
+    so that the untrained network starts near a multiple of the identity map."""
+    g = _rng(seed, 7)
+    ws = []
+    for cin, cout in zip(channels[:-1], channels[1:]):
+        w = (g.standard_normal((9, cout, cin, 4, 4)) + 1j * g.standard_normal((9, cout, cin, 4, 4)))
+        w *= scale / (4.0 * np.sqrt(9 * cin))
+        for c in range(min(cin, cout)):
+            w[0, c, c] += np.eye(4)
+        ws.append(w)
+    return ws
