@@ -162,6 +162,7 @@ typedef struct {
   int max_iter;      /* iteration cap -> PFMP_E_NOT_CONVERGED                              */
   double delta;      /* mixed: reliable update when the sloppy residual fell by delta      */
   int check_every;   /* iterations per CUDA-graph chunk between host checks (0: default 8) */
+  int restart;       /* FGCR: directions kept before a restart (0: default 16)            */
 } pfmp_solver_params;
 
 typedef struct {
@@ -275,6 +276,43 @@ int pfmp_batch_destroy(pfmp_batch* batch);
 int pfmp_batch_tune(pfmp_batch* batch, int chunk, int* block, double* ms_per_chunk);
 int pfmp_batch_solve(pfmp_batch* batch, const pfmp_solver_params* params, void* const* x, const void* const* b,
                      pfmp_solve_info* infos);
+
+/* ---- learned preconditioner (no counterpart in the paper) ---------------------------
+ * A gauge-covariant linear network N used as the preconditioner of FGCR: layer l maps
+ * C_l channels to C_{l+1}, y_o(x) = sum_i [W0 a_i(x) + sum_mu (Wf_mu U_mu(x) a_i(x+mu)
+ * + Wb_mu U_mu(x-mu)^dag a_i(x-mu))] with complex 4x4 spin matrices W (9 per channel
+ * pair) and the fermion boundary factor on time hops; channels[0] = channels[L] = 1;
+ * input embedded on even sites, output read on even sites.  prec is the arithmetic of
+ * the network kernels (FP32 for use in FGCR, FP64 for gradient checks).  Weights are
+ * host arrays of complex doubles (re, im interleaved), layers concatenated, each
+ * W[9][c_out][c_in][4][4] with index 0 = site, 1+mu forward hop, 5+mu backward hop.
+ * Training: Adam (beta 0.9, 0.999) over (b, x = K^{-1} b) pairs of FP64 even device
+ * fields, batch pairs per step, cycling through the pairs, on one of two losses:
+ *   PFMP_NN_LOSS_SOLUTION  L = ||N(b) - x||^2 / ||x||^2
+ *   PFMP_NN_LOSS_RESIDUAL  L = ||K N(b) - b||^2 / ||b||^2 (needs op; K N close to the
+ *                          identity is what a right preconditioner of K needs)        */
+#define PFMP_NN_LOSS_SOLUTION 0
+#define PFMP_NN_LOSS_RESIDUAL 1
+typedef struct pfmp_nn pfmp_nn;
+int pfmp_nn_create(pfmp_ctx* ctx, int nlayers, const int* channels, int prec, pfmp_nn** nn);
+int pfmp_nn_destroy(pfmp_nn* nn);
+int64_t pfmp_nn_num_weights(const pfmp_nn* nn);
+int pfmp_nn_set_weights(pfmp_nn* nn, const double* w);
+int pfmp_nn_get_weights(pfmp_nn* nn, double* w);
+/* out = N(in), even fields of precision prec in the library layout                     */
+int pfmp_nn_apply(pfmp_nn* nn, int prec, void* out, const void* in);
+/* loss of one pair and its gradient dL/dRe W + i dL/dIm W (grad: host, may be NULL)     */
+int pfmp_nn_loss_grad(pfmp_nn* nn, pfmp_op* op, int kind, const void* b, const void* x, double* loss, double* grad);
+int pfmp_nn_train(pfmp_nn* nn, pfmp_op* op, int kind, int npairs, const void* const* b, const void* const* x, int steps,
+                  int batch, double lr, double* final_loss);
+/* FGCR on K with N as the flexible preconditioner (nn = NULL: GCR), FP32 inner
+ * iterations of params->restart directions, stopped when the inner residual fell by
+ * params->delta; FP64 outer correction x += e and true residual b - K x; after two
+ * outer passes without a 10% gain the rest is solved by the mixed CG (info->
+ * reliable_updates then counts those CG iterations).  info->iters counts inner FGCR
+ * iterations.  FP64 x, b.                                                              */
+int pfmp_solve_fgcr(pfmp_op* op, pfmp_nn* nn, const pfmp_solver_params* params, void* x, const void* b,
+                    pfmp_solve_info* info);
 
 /* ---- kernel timing (tracing) ------------------------------------------------------
  * pfmp_profile_begin: from now on every stencil launch of this context is bracketed by

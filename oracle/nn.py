@@ -61,6 +61,21 @@ def loss(lat, U, weights, b, x_true):
     return (d.abs() ** 2).sum() / ((lat.even * x_true).abs() ** 2).sum()
 
 
+def residual_loss(lat, U, weights, b, K):
+    """|| K N(b) - b ||^2 / ||b||^2 on even sites: K N close to the identity, the
+    property a right preconditioner of K needs (K = M-hat^dag M-hat)."""
+    y = network_apply(lat, U, weights, b)
+    d = lat.even * (K(y) - b)
+    return (d.abs() ** 2).sum() / ((lat.even * b).abs() ** 2).sum()
+
+
+def residual_grads(lat, U, weights, b, K):
+    ws = [w.clone().requires_grad_(True) for w in weights]
+    L = residual_loss(lat, U, ws, b, K)
+    g = torch.autograd.grad(L, ws)
+    return L.detach(), [t.detach() for t in g]
+
+
 def init_weights(channels, seed):
     """Initial weights drawn by pfmp_inputs (shared with the GPU side)."""
     import pfmp_inputs as pin

@@ -40,7 +40,7 @@ class PfmpError(RuntimeError):
 
 class SolverParams(C.Structure):
     _fields_ = [("method", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("delta", C.c_double),
-                ("check_every", C.c_int)]
+                ("check_every", C.c_int), ("restart", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -116,6 +116,15 @@ SIGNATURES = {
     "pfmp_batch_destroy": (I, [P]),
     "pfmp_batch_tune": (I, [P, I, C.POINTER(I), DP]),
     "pfmp_batch_solve": (I, [P, C.POINTER(SolverParams), C.POINTER(P), C.POINTER(P), C.POINTER(SolveInfo)]),
+    "pfmp_nn_create": (I, [P, I, C.POINTER(I), I, C.POINTER(P)]),
+    "pfmp_nn_destroy": (I, [P]),
+    "pfmp_nn_num_weights": (C.c_int64, [P]),
+    "pfmp_nn_set_weights": (I, [P, DP]),
+    "pfmp_nn_get_weights": (I, [P, DP]),
+    "pfmp_nn_apply": (I, [P, I, P, P]),
+    "pfmp_nn_loss_grad": (I, [P, P, I, P, P, DP, DP]),
+    "pfmp_nn_train": (I, [P, P, I, I, C.POINTER(P), C.POINTER(P), I, I, D, DP]),
+    "pfmp_solve_fgcr": (I, [P, P, C.POINTER(SolverParams), P, P, C.POINTER(SolveInfo)]),
     "pfmp_profile_begin": (I, [P]),
     "pfmp_profile_end": (I, [P, I, C.POINTER(C.c_int64), DP, DP]),
 }
@@ -424,3 +433,77 @@ def pfmp_batch_solve(b, params, xs, bs, raise_on_error=True):
     if raise_on_error:
         check(st)
     return list(infos)
+
+
+def pfmp_nn_create(ctx, channels, prec=PFMP_F32):
+    h = P()
+    ch = (I * len(channels))(*channels)
+    check(lib().pfmp_nn_create(ctx, len(channels) - 1, ch, prec, C.byref(h)))
+    return h
+
+
+def pfmp_nn_destroy(nn):
+    check(lib().pfmp_nn_destroy(nn))
+
+
+def pfmp_nn_num_weights(nn):
+    return int(lib().pfmp_nn_num_weights(nn))
+
+
+def pfmp_nn_set_weights(nn, weights):
+    """weights: list of complex arrays W[9][c_out][c_in][4][4] (one per layer)."""
+    flat = np.concatenate([np.ascontiguousarray(w, dtype=np.complex128).reshape(-1) for w in weights])
+    a = np.ascontiguousarray(flat.view(np.float64))
+    check(lib().pfmp_nn_set_weights(nn, a.ctypes.data_as(DP)))
+
+
+def _unflatten(nn_shapes, flat):
+    out, off = [], 0
+    for shp in nn_shapes:
+        n = int(np.prod(shp))
+        out.append(flat[off:off + n].reshape(shp))
+        off += n
+    return out
+
+
+def pfmp_nn_get_weights(nn, shapes):
+    n = pfmp_nn_num_weights(nn)
+    a = np.zeros(2 * n)
+    check(lib().pfmp_nn_get_weights(nn, a.ctypes.data_as(DP)))
+    return _unflatten(shapes, a.view(np.complex128))
+
+
+def pfmp_nn_apply(nn, prec, out, inp):
+    check(lib().pfmp_nn_apply(nn, prec, _ptr(out), _ptr(inp)))
+
+
+PFMP_NN_LOSS_SOLUTION = 0
+PFMP_NN_LOSS_RESIDUAL = 1
+
+
+def pfmp_nn_loss_grad(nn, b, x, shapes=None, op=None, kind=PFMP_NN_LOSS_SOLUTION):
+    loss = C.c_double()
+    if shapes is None:
+        check(lib().pfmp_nn_loss_grad(nn, op, kind, _ptr(b), _ptr(x), C.byref(loss), None))
+        return loss.value, None
+    n = pfmp_nn_num_weights(nn)
+    a = np.zeros(2 * n)
+    check(lib().pfmp_nn_loss_grad(nn, op, kind, _ptr(b), _ptr(x), C.byref(loss), a.ctypes.data_as(DP)))
+    return loss.value, _unflatten(shapes, a.view(np.complex128))
+
+
+def pfmp_nn_train(nn, bs, xs, steps, batch, lr, op=None, kind=PFMP_NN_LOSS_SOLUTION):
+    n = len(bs)
+    ba = (P * n)(*[_ptr(v) for v in bs])
+    xa = (P * n)(*[_ptr(v) for v in xs])
+    loss = C.c_double()
+    check(lib().pfmp_nn_train(nn, op, kind, n, ba, xa, steps, batch, lr, C.byref(loss)))
+    return loss.value
+
+
+def pfmp_solve_fgcr(op, nn, params, x, b, raise_on_error=True):
+    info = SolveInfo()
+    st = lib().pfmp_solve_fgcr(op, nn, C.byref(params), _ptr(x), _ptr(b), C.byref(info))
+    if raise_on_error:
+        check(st)
+    return info

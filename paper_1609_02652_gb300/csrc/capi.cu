@@ -37,6 +37,19 @@ void batch_destroy(pfmp_batch* B);
 int batch_solve(pfmp_batch* B, double tol, int max_iter, double delta, int check, void* const* x, const void* const* b,
                 pfmp_solve_info* infos);
 int batch_tune(pfmp_batch* B, int chunk, double* best_ms);
+pfmp_nn* nn_create(pfmp_ctx* c, int nl, const int* ch, int prec);
+void nn_destroy(pfmp_nn* N);
+long nn_num_weights(const pfmp_nn* N);
+void nn_set_weights(pfmp_nn* N, const double* w);
+void nn_get_weights(pfmp_nn* N, double* w);
+void nn_get_grads(pfmp_nn* N, double* w);
+void nn_apply(pfmp_nn* N, void* out, const void* in, int prec_io);
+void nn_zero_grad(pfmp_nn* N);
+double nn_loss_grad(pfmp_nn* N, pfmp_op* op, int kind, const void* b, const void* x, double scale);
+double nn_train(pfmp_nn* N, pfmp_op* op, int kind, int npairs, const void* const* b, const void* const* x, int steps,
+                int batch, double lr);
+int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, double delta, void* x, const void* b,
+               int* iters, int* outer, double* true_res, long* kapply, int* fallback_iters);
 void profile_end(pfmp_ctx* c, int cls, long* launches, double* ms, double* bytes);
 }  // namespace pfmp
 
@@ -555,6 +568,83 @@ int pfmp_batch_solve(pfmp_batch* B, const pfmp_solver_params* prm, void* const* 
   API_BEGIN
   PFMP_REQUIRE(B && prm && x && b, PFMP_E_INVALID, "null argument");
   int st = batch_solve(B, prm->tol, prm->max_iter, prm->delta, prm->check_every, x, b, infos);
+  if (st != PFMP_OK) {
+    set_last_error(pfmp_strerror(st));
+    return st;
+  }
+  API_END
+}
+
+int pfmp_nn_create(pfmp_ctx* ctx, int nl, const int* ch, int prec, pfmp_nn** out) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && ch && out, PFMP_E_INVALID, "null argument");
+  *out = nn_create(ctx, nl, ch, prec);
+  API_END
+}
+
+int pfmp_nn_destroy(pfmp_nn* nn) {
+  API_BEGIN
+  nn_destroy(nn);
+  API_END
+}
+
+int64_t pfmp_nn_num_weights(const pfmp_nn* nn) { return nn ? (int64_t)nn_num_weights(nn) : -1; }
+
+int pfmp_nn_set_weights(pfmp_nn* nn, const double* w) {
+  API_BEGIN
+  PFMP_REQUIRE(nn && w, PFMP_E_INVALID, "null argument");
+  nn_set_weights(nn, w);
+  API_END
+}
+
+int pfmp_nn_get_weights(pfmp_nn* nn, double* w) {
+  API_BEGIN
+  PFMP_REQUIRE(nn && w, PFMP_E_INVALID, "null argument");
+  nn_get_weights(nn, w);
+  API_END
+}
+
+int pfmp_nn_apply(pfmp_nn* nn, int prec, void* out, const void* in) {
+  API_BEGIN
+  PFMP_REQUIRE(nn && out && in && out != in, PFMP_E_INVALID, "bad argument");
+  check_prec(prec);
+  nn_apply(nn, out, in, prec);
+  API_END
+}
+
+int pfmp_nn_loss_grad(pfmp_nn* nn, pfmp_op* op, int kind, const void* b, const void* x, double* loss, double* grad) {
+  API_BEGIN
+  PFMP_REQUIRE(nn && b && x && loss, PFMP_E_INVALID, "null argument");
+  nn_zero_grad(nn);
+  *loss = nn_loss_grad(nn, op, kind, b, x, 1.0);
+  if (grad) nn_get_grads(nn, grad);
+  API_END
+}
+
+int pfmp_nn_train(pfmp_nn* nn, pfmp_op* op, int kind, int npairs, const void* const* b, const void* const* x, int steps,
+                  int batch, double lr, double* final_loss) {
+  API_BEGIN
+  PFMP_REQUIRE(nn && b && x, PFMP_E_INVALID, "null argument");
+  double l = nn_train(nn, op, kind, npairs, b, x, steps, batch, lr);
+  if (final_loss) *final_loss = l;
+  API_END
+}
+
+int pfmp_solve_fgcr(pfmp_op* op, pfmp_nn* nn, const pfmp_solver_params* prm, void* x, const void* b,
+                    pfmp_solve_info* info) {
+  API_BEGIN
+  PFMP_REQUIRE(op && prm && x && b && x != b, PFMP_E_INVALID, "bad argument");
+  int it = 0, outer = 0, fb = 0;
+  double res = 0;
+  long kap = 0;
+  int st = solve_fgcr(op, nn, prm->tol, prm->max_iter, prm->restart, prm->delta, x, b, &it, &outer, &res, &kap, &fb);
+  if (info) {
+    info->iters = it;
+    info->reliable_updates = fb;
+    info->true_rel_res = res;
+    info->k_apply = kap;
+    info->status = st;
+  }
   if (st != PFMP_OK) {
     set_last_error(pfmp_strerror(st));
     return st;
