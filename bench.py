@@ -280,6 +280,8 @@ def run_ours(args, rank, world):
         capi.pfmp_solve_host(op, mixed, xh.data_ptr(), bh.data_ptr())
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = allmax(statistics.mean(e2e), world) / world
+    learn = None if args.no_learned else learned(capi, stream, l2_flush, args, ctx, op, b, x)
+    traj = trajectory_4x4x4x4(capi, stream)
     capi.pfmp_op_destroy(op)
     capi.pfmp_ctx_destroy(ctx)
 
@@ -302,6 +304,8 @@ def run_ours(args, rank, world):
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 8),
                 "d2h_bytes_per_step": int(xh.numel() * 8)},
         "roofline": roof,
+        "learned": learn,
+        "trajectory_4x4x4x4": traj,
         "batched": batched,
         "hop_in_solve": {"launches": n_hop, "avg_us": hop_ms * 1e3 / max(n_hop, 1), "algorithmic_gbs": hop_gbs_l2,
                          "note": "16^3x32 FP32 working set (~75 MB) is L2-resident inside a solve"},
@@ -395,6 +399,99 @@ def batched_96(capi, stream, l2_flush, args):
             "workload": "32x 8^4 + 32x 12^3x24 + 32x 16^3x32, eps=0.4, kappa~U[0.120,0.134], 1-8 rhs, 1e-10"}
 
 
+def learned(capi, stream, l2_flush, args, ctx, op, b, x):
+    """Mixed + learned: a [1,4,4,1] network trained (residual loss, Adam, the project's
+    kernels) on (b, K^{-1} b) pairs from the mixed solver on a held-out 8^3x16 gauge field
+    (eps = 0.5, seed 2, same kappa and c_sw), then used as the FGCR preconditioner on the
+    16^3x32 benchmark system; GCR (no network) alongside."""
+    import torch
+
+    import pfmp_inputs as pin
+
+    tdims = (8, 8, 8, 16)
+    tctx = capi.pfmp_ctx_create(tdims, -1, stream.cuda_stream)
+    h = torch.tensor(np.ascontiguousarray(pin.gauge_algebra(tdims, 2)).reshape(-1), device="cuda")
+    torch.cuda.synchronize()
+    capi.pfmp_gauge_from_algebra(tctx, h, EPS, capi.PFMP_DEVICE)
+    top = capi.pfmp_op_create(tctx, KAPPA, CSW)
+    n64 = capi.pfmp_spinor_bytes(tctx, capi.PFMP_F64) // 8
+    mixed = capi.SolverParams(method=capi.PFMP_SOLVER_CG_MIXED, tol=TOL, max_iter=20000, delta=1e-4, check_every=8)
+    bs, xs = [], []
+    t0 = time.perf_counter()
+    for i in range(16):
+        bc = torch.tensor(np.ascontiguousarray(pin.spinor(tdims, 3000 + i)).view(np.float64).reshape(-1), device="cuda")
+        bb = torch.zeros(n64, dtype=torch.float64, device="cuda")
+        capi.pfmp_spinor_pack(tctx, bb, capi.PFMP_F64, bc, capi.PFMP_DEVICE, 0)
+        xx = torch.zeros_like(bb)
+        capi.pfmp_solve(top, mixed, xx, bb)
+        bs.append(bb)
+        xs.append(xx)
+    t_pairs = time.perf_counter() - t0
+    ch = [1, 4, 4, 1]
+    net = capi.pfmp_nn_create(tctx, ch, capi.PFMP_F32)
+    capi.pfmp_nn_set_weights(net, pin.nn_weights(ch, 5))
+    t0 = time.perf_counter()
+    loss = capi.pfmp_nn_train(net, bs, xs, steps=args.nn_steps, batch=4, lr=5e-3, op=top,
+                              kind=capi.PFMP_NN_LOSS_RESIDUAL)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    shapes = [(9, co, ci, 4, 4) for ci, co in zip(ch[:-1], ch[1:])]
+    w = capi.pfmp_nn_get_weights(net, shapes)
+    capi.pfmp_nn_destroy(net)
+    capi.pfmp_op_destroy(top)
+    capi.pfmp_ctx_destroy(tctx)
+    net = capi.pfmp_nn_create(ctx, ch, capi.PFMP_F32)
+    capi.pfmp_nn_set_weights(net, w)
+    prm = capi.SolverParams(method=0, tol=TOL, max_iter=20000, delta=1e-3, check_every=8, restart=16)
+    out = {"train_lattice": "8x8x8x16 (held-out field, seed 2)", "pairs": 16, "pairs_s": t_pairs,
+           "train_steps": args.nn_steps, "train_s": t_train, "final_train_loss": loss, "network": ch}
+    for name, n in (("fgcr_nn", net), ("gcr", None)):
+        capi.pfmp_solve_fgcr(op, n, prm, x, b)  # warm
+        l2_flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = capi.pfmp_solve_fgcr(op, n, prm, x, b)
+        e1.record(stream)
+        e1.synchronize()
+        out[name] = {"ms": e0.elapsed_time(e1), "iterations": info.iters, "cg_fallback_iterations": info.reliable_updates,
+                     "true_rel_res": info.true_rel_res}
+    capi.pfmp_nn_destroy(net)
+    return out
+
+
+def trajectory_4x4x4x4(capi, stream):
+    """One PF-MP trajectory of the 4^4 parity configuration (eps 0.3, beta 5.5, c_sw 1,
+    kappa 0.120, kappa' 0.110, order-8 filter, 2MN 8 x 16 steps, tau 0.5, FP64, CG 1e-12)."""
+    import torch
+
+    import pfmp_inputs as pin
+
+    dims = (4, 4, 4, 4)
+    V = 256
+    ctx = capi.pfmp_ctx_create(dims, -1, stream.cuda_stream)
+    capi.pfmp_gauge_from_algebra(ctx, np.ascontiguousarray(pin.gauge_algebra(dims, 1)).reshape(-1), 0.3, capi.PFMP_HOST)
+    ap = capi.ActionParams(beta=5.5, kappa=0.120, kappa_h=0.110, csw=1.0, n=8, mu=1.2, nu=0.9, tol=1e-12,
+                           max_iter=5000)
+    A = capi.pfmp_action_create(ctx, ap)
+    lam = 0.1931833275037836
+    T, S = capi.pfmp_schedule_merge([capi.pfmp_schedule_2mn(8, 0.5, lam), capi.pfmp_schedule_2mn(16, 0.5, lam)])
+    xi = np.concatenate([np.ascontiguousarray(pin.spinor(dims, 10 + i)).view(np.float64).reshape(-1) for i in range(3)])
+    mom = np.ascontiguousarray(pin.momenta(dims, 5)).reshape(-1)
+    U0 = np.zeros(V * 72)
+    capi.pfmp_gauge_get(ctx, U0, capi.PFMP_HOST)
+    capi.pfmp_trajectory(A, T, S, [1, 1, 1, 0, 0], mom, xi, 2.0)  # warm (u = 2: reject, U restored)
+    capi.pfmp_gauge_set(ctx, U0, capi.PFMP_HOST)
+    capi.pfmp_action_refresh(A)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = capi.pfmp_trajectory(A, T, S, [1, 1, 1, 0, 0], mom, xi, float(pin.uniform(6)[0]))
+    ms = (time.perf_counter() - t0) * 1e3
+    capi.pfmp_action_destroy(A)
+    capi.pfmp_ctx_destroy(ctx)
+    return {"ms": ms, "dH": info.dH, "accepted": bool(info.accepted), "k_apply": int(info.k_apply),
+            "force_evals": int(info.force_evals), "steps": len(T)}
+
+
 def recorded_traffic():
     """DRAM bytes per launch of the FP32 stencil at 32^3x64 from the committed ncu summary,
     or None when the kernel source changed since those counters were taken."""
@@ -482,6 +579,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 96-system batched-solve measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner measurement")
+    ap.add_argument("--nn-steps", type=int, default=300, help="training steps of the learned preconditioner")
     ap.add_argument("--delta", type=float, default=1e-4, help="reliable-update threshold of the mixed solver")
     ap.add_argument("--chunk", type=int, default=8, help="CG iterations per CUDA-graph chunk")
     ap.add_argument("--kernel-only", action="store_true",

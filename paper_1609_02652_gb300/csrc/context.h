@@ -51,8 +51,8 @@ struct pfmp_ctx {
   double2* U64c = nullptr;   // compressed [2][4][6][Vh]
   float4* U32 = nullptr;     // compressed [2][4][3][Vh]
   pfmp::ReduceBuf rb{};
-  double* d_sums = nullptr;  // [8] results of generic reductions
-  double* h_sums = nullptr;  // pinned mirror
+  double* d_sums = nullptr;  // [64] results of generic reductions
+  double* h_sums = nullptr;  // pinned mirror [64]
   double* canon = nullptr;   // canonical full-lattice scratch (V*24 doubles)
   long gauge_version = 0;
 };

@@ -208,8 +208,8 @@ pfmp_ctx* ctx_create(const int dims[4], int bc_t, void* stream) {
     c->rb.partials = (double*)dev_alloc((size_t)kMaxReduceBlocks * kMaxSums * sizeof(double));
     c->rb.counter = (unsigned*)dev_alloc(sizeof(unsigned));
     PFMP_CUDA(cudaMemset(c->rb.counter, 0, sizeof(unsigned)));
-    c->d_sums = (double*)dev_alloc(16 * sizeof(double));
-    PFMP_CUDA(cudaMallocHost(&c->h_sums, 16 * sizeof(double)));
+    c->d_sums = (double*)dev_alloc(64 * sizeof(double));
+    PFMP_CUDA(cudaMallocHost(&c->h_sums, 64 * sizeof(double)));
   } catch (...) {
     dev_free(c->U64);
     dev_free(c->U64c);

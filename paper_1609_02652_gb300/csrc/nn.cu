@@ -149,6 +149,54 @@ __global__ void k_nn_layer(Geom g, const double2* __restrict__ U, const typename
   for (int k = 0; k < 12; ++k) st<T>(out, ((size_t)oc * 12 + k) * g.V + s, acc[k]);
 }
 
+// forward layer with every output channel of a site in one thread (COUT small): the
+// parallel transports are computed once per (direction, input channel) and the layer's
+// weights sit in shared memory
+template <typename T, int COUT>
+__global__ void __launch_bounds__(128) k_nn_layer_site(Geom g, const double2* __restrict__ U,
+                                                       const typename C2<T>::t* __restrict__ W, int cin,
+                                                       const typename C2<T>::t* __restrict__ in,
+                                                       typename C2<T>::t* __restrict__ out) {
+  extern __shared__ unsigned char smem_raw[];
+  typename C2<T>::t* Ws = reinterpret_cast<typename C2<T>::t*>(smem_raw);
+  const int nw = 9 * COUT * cin * 16;
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) Ws[i] = W[i];
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int x[4];
+  lex_coords(g, s, x);
+  cplx<T> acc[COUT][12];
+#pragma unroll
+  for (int o = 0; o < COUT; ++o)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[o][k] = mk<T>(0, 0);
+  for (int d = 0; d < 9; ++d) {
+    const int kind = d == 0 ? 0 : (d <= 4 ? 1 : 2);
+    const int mu = d == 0 ? 0 : (d - 1) % 4;
+    for (int ic = 0; ic < cin; ++ic) {
+      cplx<T> t[12];
+      transport<T>(in + (size_t)ic * 12 * g.V, U, g, x, kind, mu, t);
+#pragma unroll
+      for (int o = 0; o < COUT; ++o) {
+        const typename C2<T>::t* w0 = Ws + widx(d, o, ic, COUT, cin);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const cplx<T> w = mk(w0[a * 4 + b].x, w0[a * 4 + b].y);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[o][a * 3 + c] = acc[o][a * 3 + c] + w * t[b * 3 + c];
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < COUT; ++o)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) st<T>(out, ((size_t)o * 12 + k) * g.V + s, acc[o][k]);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -273,6 +321,118 @@ __global__ void k_adam(T* __restrict__ w, const T* __restrict__ gw, T* __restric
   }
 }
 
+// ---- fused FGCR steps (FP32 fields, FP64 sums) --------------------------------------
+struct CoefList {
+  float2 h[32];
+};
+
+// runtime-length block sum of v[0..nv) (nv <= 34); returns true in thread 0 of the last
+// block, whose out[0..nv) then holds the grid totals (deterministic order).  The last
+// block adds the per-block partials with all its threads, one value at a time.
+__device__ bool grid_sum_n(double* v, int nv, double* partials, unsigned* ticket, double* out) {
+  __shared__ double sh[34][32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int k = 0; k < nv; ++k) {
+    double t = v[k];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[k][warp] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0;
+    for (int w = 0; w < nw; ++w) t += sh[threadIdx.x][w];
+    partials[(size_t)blockIdx.x * nv + threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  for (int k = 0; k < nv; ++k) {
+    double t = 0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += ((volatile double*)partials)[(size_t)b * nv + k];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[k][warp] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0;
+    for (int w = 0; w < nw; ++w) t += sh[threadIdx.x][w];
+    out[threadIdx.x] = t;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return threadIdx.x == 0;
+}
+
+// h_j = <W_j, w> (j < k) and <w, r>: out[2j], out[2j+1], out[2k], out[2k+1]
+__global__ void k_fgcr_dots(float4* const* __restrict__ Wp, int k, const float4* __restrict__ w,
+                            const float4* __restrict__ r, long n, double* partials, unsigned* ticket, double* out) {
+  double v[34];
+  for (int j = 0; j < 2 * k + 2; ++j) v[j] = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float4 a = w[i];
+    for (int j = 0; j < k; ++j) {
+      const float4 q = Wp[j][i];
+      v[2 * j] += (double)q.x * a.x + (double)q.y * a.y + (double)q.z * a.z + (double)q.w * a.w;
+      v[2 * j + 1] += (double)q.x * a.y - (double)q.y * a.x + (double)q.z * a.w - (double)q.w * a.z;
+    }
+    const float4 rr = r[i];
+    v[2 * k] += (double)a.x * rr.x + (double)a.y * rr.y + (double)a.z * rr.z + (double)a.w * rr.w;
+    v[2 * k + 1] += (double)a.x * rr.y - (double)a.y * rr.x + (double)a.z * rr.w - (double)a.w * rr.z;
+  }
+  grid_sum_n(v, 2 * k + 2, partials, ticket, out);
+}
+
+// w -= sum_j h_j W_j, z -= sum_j h_j Z_j, out[0] = |w|^2
+__global__ void k_fgcr_orth(float4* const* __restrict__ Wp, float4* const* __restrict__ Zp, int k, CoefList h,
+                            float4* __restrict__ w, float4* __restrict__ z, long n, double* partials, unsigned* ticket,
+                            double* out) {
+  double v[1] = {0.0};
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    float4 a = w[i], b = z[i];
+    for (int j = 0; j < k; ++j) {
+      const float2 c = h.h[j];
+      const float4 q = Wp[j][i], p = Zp[j][i];
+      a.x -= c.x * q.x - c.y * q.y;
+      a.y -= c.x * q.y + c.y * q.x;
+      a.z -= c.x * q.z - c.y * q.w;
+      a.w -= c.x * q.w + c.y * q.z;
+      b.x -= c.x * p.x - c.y * p.y;
+      b.y -= c.x * p.y + c.y * p.x;
+      b.z -= c.x * p.z - c.y * p.w;
+      b.w -= c.x * p.w + c.y * p.z;
+    }
+    w[i] = a;
+    z[i] = b;
+    v[0] += (double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z + (double)a.w * a.w;
+  }
+  grid_sum_n(v, 1, partials, ticket, out);
+}
+
+// r -= alpha w, e += alpha z, then w, z scaled by s (to unit |w|)
+__global__ void k_fgcr_step(float4* __restrict__ w, float4* __restrict__ z, float4* __restrict__ r,
+                            float4* __restrict__ e, float2 al, float s, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    float4 a = w[i], b = z[i], rr = r[i], ee = e[i];
+    rr.x -= al.x * a.x - al.y * a.y;
+    rr.y -= al.x * a.y + al.y * a.x;
+    rr.z -= al.x * a.z - al.y * a.w;
+    rr.w -= al.x * a.w + al.y * a.z;
+    ee.x += al.x * b.x - al.y * b.y;
+    ee.y += al.x * b.y + al.y * b.x;
+    ee.z += al.x * b.z - al.y * b.w;
+    ee.w += al.x * b.w + al.y * b.z;
+    r[i] = rr;
+    e[i] = ee;
+    w[i] = make_float4(s * a.x, s * a.y, s * a.z, s * a.w);
+    z[i] = make_float4(s * b.x, s * b.y, s * b.z, s * b.w);
+  }
+}
+
 __global__ void k_scale32(float4* x, float a, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     float4 v = x[i];
@@ -389,12 +549,28 @@ static void copy_out(pfmp_nn* N, const std::vector<void*>& src, double* w) {
 void nn_get_weights(pfmp_nn* N, double* w) { copy_out(N, N->W, w); }
 void nn_get_grads(pfmp_nn* N, double* w) { copy_out(N, N->gW, w); }
 
+template <typename T, int CO>
+static bool layer_site(pfmp_ctx* c, const void* W, int cin, const void* in, void* out) {
+  using C = typename C2<T>::t;
+  const size_t sm = (size_t)9 * CO * cin * 16 * sizeof(C);
+  if (sm > 48 * 1024) return false;
+  k_nn_layer_site<T, CO><<<nblocks(c->g.V, 128), 128, sm, c->stream>>>(c->g, c->U64, (const C*)W, cin, (const C*)in,
+                                                                      (C*)out);
+  PFMP_CHECK_LAUNCH();
+  return true;
+}
+
 template <typename T>
 static void forward_t(pfmp_nn* N) {
   pfmp_ctx* c = N->ctx;
   using C = typename C2<T>::t;
   for (size_t l = 0; l < N->W.size(); ++l) {
     const int cin = N->ch[l], cout = N->ch[l + 1];
+    bool done = false;
+    if (cout == 1) done = layer_site<T, 1>(c, N->W[l], cin, N->act[l], N->act[l + 1]);
+    else if (cout == 2) done = layer_site<T, 2>(c, N->W[l], cin, N->act[l], N->act[l + 1]);
+    else if (cout == 4) done = layer_site<T, 4>(c, N->W[l], cin, N->act[l], N->act[l + 1]);
+    if (done) continue;
     const long n = (long)c->g.V * cout;
     k_nn_layer<T, false><<<nblocks(n, 128), 128, 0, c->stream>>>(c->g, c->U64, (const C*)N->W[l], cin, cout,
                                                                   (const C*)N->act[l], (C*)N->act[l + 1]);
@@ -590,6 +766,11 @@ static std::complex<double> cdot_sync(pfmp_ctx* c, int prec, const void* x, cons
 struct FgcrWork {
   std::vector<float4*> Z, W;
   float4 *r = nullptr, *e = nullptr, *z = nullptr, *w = nullptr;
+  float4** dW = nullptr;
+  float4** dZ = nullptr;
+  double* part = nullptr;
+  unsigned* ticket = nullptr;
+  double* out = nullptr;
   ~FgcrWork() {
     for (auto p : Z) dev_free(p);
     for (auto p : W) dev_free(p);
@@ -597,6 +778,11 @@ struct FgcrWork {
     dev_free(e);
     dev_free(z);
     dev_free(w);
+    dev_free(dW);
+    dev_free(dZ);
+    dev_free(part);
+    dev_free(ticket);
+    dev_free(out);
   }
 };
 
@@ -606,6 +792,7 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
   const Geom& g = c->g;
   PFMP_REQUIRE(!nn || nn->ctx == c, PFMP_E_INVALID, "the network must live on the operator's context");
   if (restart <= 0) restart = 16;
+  PFMP_REQUIRE(restart <= 16, PFMP_E_INVALID, "FGCR restart length must be <= 16");
   if (!(delta > 0 && delta < 1)) delta = 1e-3;
   const size_t b32 = spinor_bytes(g, PFMP_F32), b64 = spinor_bytes(g, PFMP_F64);
   const long n32 = 6L * g.Vh;
@@ -616,6 +803,15 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
   }
   wk.r = (float4*)dev_alloc(b32);
   wk.e = (float4*)dev_alloc(b32);
+  const int fgrid = (int)std::min<long>(nblocks(n32), 152 * 2);
+  wk.dW = (float4**)dev_alloc(restart * sizeof(float4*));
+  wk.dZ = (float4**)dev_alloc(restart * sizeof(float4*));
+  PFMP_CUDA(cudaMemcpy(wk.dW, wk.W.data(), restart * sizeof(float4*), cudaMemcpyHostToDevice));
+  PFMP_CUDA(cudaMemcpy(wk.dZ, wk.Z.data(), restart * sizeof(float4*), cudaMemcpyHostToDevice));
+  wk.part = (double*)dev_alloc((size_t)fgrid * 34 * sizeof(double));
+  wk.ticket = (unsigned*)dev_alloc(sizeof(unsigned));
+  PFMP_CUDA(cudaMemset(wk.ticket, 0, sizeof(unsigned)));
+  wk.out = (double*)dev_alloc(34 * sizeof(double));
   *iters = *outer = *fallback_iters = 0;
   *kapply = 0;
   blas_norm2(c, PFMP_F64, b, c->d_sums);
@@ -635,6 +831,7 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
     blas_copy(c, wk.r, PFMP_F32, r64, PFMP_F64);
     blas_zero(c, PFMP_F32, wk.e);
     const double rn0 = std::sqrt(std::max(cdot_sync(c, PFMP_F32, wk.r, wk.r).real(), 0.0));
+    double rr = rn0 * rn0;
     for (int k = 0; k < restart && *iters < max_iter; ++k) {
       float4* z = wk.Z[k];
       float4* w = wk.W[k];
@@ -644,23 +841,31 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
         PFMP_CUDA(cudaMemcpyAsync(z, wk.r, b32, cudaMemcpyDeviceToDevice, c->stream));
       kop(op, PFMP_F32, w, z, nullptr, nullptr);
       *kapply += 1;
-      for (int j = 0; j < k; ++j) {
-        const std::complex<double> h = cdot_sync(c, PFMP_F32, wk.W[j], w);
-        blas_axpy(c, PFMP_F32, -h.real(), -h.imag(), wk.W[j], w);
-        blas_axpy(c, PFMP_F32, -h.real(), -h.imag(), wk.Z[j], z);
-      }
-      const double nw = std::sqrt(std::max(cdot_sync(c, PFMP_F32, w, w).real(), 0.0));
-      PFMP_REQUIRE(std::isfinite(nw), PFMP_E_NAN, "FGCR direction is not finite");
-      if (nw == 0) break;
-      k_scale32<<<nblocks(n32), kBlock, 0, c->stream>>>(w, (float)(1.0 / nw), n32);
+      // classical Gram-Schmidt against the orthonormal W_j: all <W_j, w> and <w, r> in
+      // one pass (r is orthogonal to every W_j, so <w', r> = <w, r>)
+      k_fgcr_dots<<<fgrid, kBlock, 0, c->stream>>>(wk.dW, k, w, wk.r, n32, wk.part, wk.ticket, wk.out);
       PFMP_CHECK_LAUNCH();
-      k_scale32<<<nblocks(n32), kBlock, 0, c->stream>>>(z, (float)(1.0 / nw), n32);
+      double hv[34];
+      PFMP_CUDA(cudaMemcpyAsync(c->h_sums, wk.out, (2 * k + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      PFMP_CUDA(cudaStreamSynchronize(c->stream));
+      for (int j = 0; j < 2 * k + 2; ++j) hv[j] = c->h_sums[j];
+      CoefList cl;
+      for (int j = 0; j < k; ++j) cl.h[j] = make_float2((float)hv[2 * j], (float)hv[2 * j + 1]);
+      const std::complex<double> wr(hv[2 * k], hv[2 * k + 1]);
+      k_fgcr_orth<<<fgrid, kBlock, 0, c->stream>>>(wk.dW, wk.dZ, k, cl, w, z, n32, wk.part, wk.ticket, wk.out);
       PFMP_CHECK_LAUNCH();
-      const std::complex<double> a = cdot_sync(c, PFMP_F32, w, wk.r);
-      blas_axpy(c, PFMP_F32, a.real(), a.imag(), z, wk.e);
-      blas_axpy(c, PFMP_F32, -a.real(), -a.imag(), w, wk.r);
+      PFMP_CUDA(cudaMemcpyAsync(c->h_sums, wk.out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      PFMP_CUDA(cudaStreamSynchronize(c->stream));
+      const double n2 = c->h_sums[0];
+      PFMP_REQUIRE(std::isfinite(n2), PFMP_E_NAN, "FGCR direction is not finite");
+      if (!(n2 > 0)) break;
+      const std::complex<double> al = wr / n2;
+      k_fgcr_step<<<fgrid, kBlock, 0, c->stream>>>(w, z, wk.r, wk.e, make_float2((float)al.real(), (float)al.imag()),
+                                                   (float)(1.0 / std::sqrt(n2)), n32);
+      PFMP_CHECK_LAUNCH();
       *iters += 1;
-      const double rn = std::sqrt(std::max(cdot_sync(c, PFMP_F32, wk.r, wk.r).real(), 0.0));
+      rr = std::max(rr - std::norm(wr) / n2, 0.0);  // |r - <w^,r> w^|^2
+      const double rn = std::sqrt(rr);
       if (rn < delta * rn0 || rn * rn < 0.25 * tol * tol * bb) break;
     }
     // outer FP64 correction
