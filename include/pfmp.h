@@ -119,6 +119,17 @@ int pfmp_op_update(pfmp_op* op);
 int pfmp_op_destroy(pfmp_op* op);
 /* sum over odd sites of log det A(x) (host scalar; synchronises).                    */
 int pfmp_op_logdet(pfmp_op* op, double* logdet_oo);
+/* Threads per output site of the stencil kernels of this operator for one arithmetic
+ * (prec = PFMP_F64, PFMP_F32 or PFMP_DF): 1, 2, 4 or 8.  Splitting a site's 8 hop terms
+ * across threads adds parallelism where the kernel is latency- or ALU-bound (small
+ * lattices, FP64, double-float).  Results differ only by summation order.  The default
+ * comes from pfmp_op_create (a fixed rule on precision and lattice size, so runs are
+ * reproducible); pfmp_op_get_split reads it.                                         */
+int pfmp_op_set_split(pfmp_op* op, int prec, int nsplit);
+int pfmp_op_get_split(pfmp_op* op, int prec, int* nsplit);
+/* Threads per block of this operator's stencil kernels (32, 64, 96 or 128; default from
+ * pfmp_op_create: the lattice's sites per parity spread over the SMs in whole waves).  */
+int pfmp_op_set_block(pfmp_op* op, int threads);
 
 /* Wilson hop restricted to one parity: out (parity out_parity) = H_{out,in} in; with
  * dagger = 1 the adjoint hop H^dag (projectors (1 + g_mu) forward, (1 - g_mu) back).  */
@@ -145,6 +156,13 @@ int pfmp_mhat_noalloc(pfmp_op* op, int prec, void* out, const void* in, int dagg
 /* out = K in = M-hat^dag M-hat in; if in_K_in is not NULL it receives <in, K in> =
  * ||M-hat in||^2 in FP64 (synchronises).                                             */
 int pfmp_kop(pfmp_op* op, int prec, void* out, const void* in, double* in_K_in);
+
+/* True residual r = b - K x of FP64 even fields (x, b, r), K applied in FP64
+ * (arith = PFMP_F64) or in double-float, FP32 pairs on the FP32 pipe with ~48-bit
+ * significands (arith = PFMP_DF, what the mixed solvers use for their reliable updates).
+ * rel (host, may be NULL) receives ||r|| / ||b||.  Synchronises.                     */
+#define PFMP_DF 2
+int pfmp_true_residual(pfmp_op* op, int arith, void* r, const void* x, const void* b, double* rel);
 
 /* ---- BLAS-1 on single-parity fields (FP64 global sums) ----------------------------- */
 int pfmp_norm2(pfmp_ctx* ctx, int prec, const void* x, double* result);  /* synchronises */
@@ -323,6 +341,7 @@ int pfmp_solve_fgcr(pfmp_op* op, pfmp_nn* nn, const pfmp_solver_params* params, 
  * local-input reals for the fused even-odd epilogues).                              */
 #define PFMP_KERNEL_HOP_F32 0
 #define PFMP_KERNEL_HOP_F64 1
+#define PFMP_KERNEL_HOP_DF 2   /* double-float (FP32-pair) stencil of the true residual   */
 int pfmp_profile_begin(pfmp_ctx* ctx);
 int pfmp_profile_end(pfmp_ctx* ctx, int kernel_class, int64_t* launches, double* total_ms, double* total_bytes);
 

@@ -24,6 +24,7 @@ PFMP_E_NAN = 6
 PFMP_E_UNSUPPORTED = 7
 PFMP_F64 = 0
 PFMP_F32 = 1
+PFMP_DF = 2
 PFMP_HOST = 0
 PFMP_DEVICE = 1
 PFMP_KERNEL_HOP_F32 = 0
@@ -87,11 +88,15 @@ SIGNATURES = {
     "pfmp_op_update": (I, [P]),
     "pfmp_op_destroy": (I, [P]),
     "pfmp_op_logdet": (I, [P, DP]),
+    "pfmp_op_set_split": (I, [P, I, I]),
+    "pfmp_op_get_split": (I, [P, I, C.POINTER(I)]),
+    "pfmp_op_set_block": (I, [P, I]),
     "pfmp_dslash": (I, [P, I, P, P, I, I]),
     "pfmp_clover_apply": (I, [P, I, P, P, I, I]),
     "pfmp_mhat": (I, [P, I, P, P, I]),
     "pfmp_mhat_noalloc": (I, [P, I, P, P, I]),
     "pfmp_kop": (I, [P, I, P, P, DP]),
+    "pfmp_true_residual": (I, [P, I, P, P, P, DP]),
     "pfmp_norm2": (I, [P, I, P, DP]),
     "pfmp_cdot": (I, [P, I, P, P, DP]),
     "pfmp_axpy": (I, [P, I, D, D, P, P]),
@@ -240,6 +245,20 @@ def pfmp_op_logdet(op):
     return v.value
 
 
+def pfmp_op_set_split(op, prec, ns):
+    check(lib().pfmp_op_set_split(op, prec, ns))
+
+
+def pfmp_op_set_block(op, threads):
+    check(lib().pfmp_op_set_block(op, threads))
+
+
+def pfmp_op_get_split(op, prec):
+    v = I()
+    check(lib().pfmp_op_get_split(op, prec, C.byref(v)))
+    return v.value
+
+
 def pfmp_dslash(op, prec, out, inp, out_parity, dagger=0):
     check(lib().pfmp_dslash(op, prec, _ptr(out), _ptr(inp), out_parity, dagger))
 
@@ -260,6 +279,12 @@ def pfmp_kop(op, prec, out, inp, want_norm=False):
     v = C.c_double()
     check(lib().pfmp_kop(op, prec, _ptr(out), _ptr(inp), C.byref(v) if want_norm else None))
     return v.value if want_norm else None
+
+
+def pfmp_true_residual(op, arith, r, x, b):
+    v = C.c_double()
+    check(lib().pfmp_true_residual(op, arith, _ptr(r), _ptr(x), _ptr(b), C.byref(v)))
+    return v.value
 
 
 def pfmp_norm2(ctx, prec, x):

@@ -412,12 +412,7 @@ int batch_solve(pfmp_batch* B, double tol, int max_iter, double delta, int check
           // reliable update in FP64
           blas_add_lo(c, x[idx], S.x + r * S.fw);
           void* r64 = op->cg64[0];
-          void* Ax = op->cg64[2];
-          kop(op, PFMP_F64, Ax, x[idx], nullptr, nullptr);
-          blas_xmy_norm(c, b[idx], Ax, r64, c->d_sums);
-          PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-          PFMP_CUDA(cudaStreamSynchronize(c->stream));
-          R.rr_true = c->h_sums[0];
+          R.rr_true = true_residual_df(op, x[idx], b[idx], r64);
           R.rel += 1;
           R.res = std::sqrt(R.rr_true / R.bb);
           if (R.res < tol) {

@@ -88,7 +88,12 @@ void pfmp::op_delete(pfmp_op* op) {
   for (int p = 0; p < 2; ++p) {
     dev_free(op->clov64[p]);
     dev_free(op->clov32[p]);
+    dev_free(op->clovdf[p]);
   }
+  dev_free(op->tdf);
+  dev_free(op->edf);
+  dev_free(op->xdf);
+  dev_free(op->kdf);
   dev_free(op->t64);
   dev_free(op->t32);
   dev_free(op->e64);
@@ -115,7 +120,12 @@ pfmp_op* pfmp::op_new(pfmp_ctx* ctx, double kappa, double csw) {
     for (int p = 0; p < 2; ++p) {
       op->clov64[p] = (double2*)dev_alloc((size_t)g.Vh * 36 * sizeof(double2));
       op->clov32[p] = (float4*)dev_alloc((size_t)g.Vh * 18 * sizeof(float4));
+      op->clovdf[p] = (float4*)dev_alloc((size_t)g.Vh * 36 * sizeof(float4));
     }
+    op->tdf = (float4*)dev_alloc((size_t)g.Vh * 12 * sizeof(float4));
+    op->edf = (float4*)dev_alloc((size_t)g.Vh * 12 * sizeof(float4));
+    op->xdf = (float4*)dev_alloc((size_t)g.Vh * 12 * sizeof(float4));
+    op->kdf = (float4*)dev_alloc((size_t)g.Vh * 12 * sizeof(float4));
     op->t64 = (double2*)dev_alloc(spinor_bytes(g, PFMP_F64));
     op->e64 = (double2*)dev_alloc(spinor_bytes(g, PFMP_F64));
     op->t32 = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
@@ -255,6 +265,41 @@ int pfmp_op_logdet(pfmp_op* op, double* ld) {
   API_END
 }
 
+static int split_slot(int prec) { return prec == PFMP_F64 ? 0 : (prec == PFMP_F32 ? 1 : (prec == PFMP_DF ? 2 : -1)); }
+
+int pfmp_op_set_split(pfmp_op* op, int prec, int ns) {
+  API_BEGIN
+  PFMP_REQUIRE(op && split_slot(prec) >= 0, PFMP_E_INVALID, "bad operator or precision");
+  PFMP_REQUIRE(ns == 1 || ns == 2 || ns == 4 || ns == 8, PFMP_E_INVALID, "threads per site must be 1, 2, 4 or 8");
+  op->nsplit[split_slot(prec)] = ns;
+  for (auto& G : op->graph)
+    if (G.exec) {
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+    }
+  API_END
+}
+
+int pfmp_op_set_block(pfmp_op* op, int threads) {
+  API_BEGIN
+  PFMP_REQUIRE(op && threads >= 32 && threads <= 128 && threads % 32 == 0, PFMP_E_INVALID,
+               "threads per block must be 32, 64, 96 or 128");
+  op->hop_block = threads;
+  for (auto& G : op->graph)
+    if (G.exec) {
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+    }
+  API_END
+}
+
+int pfmp_op_get_split(pfmp_op* op, int prec, int* ns) {
+  API_BEGIN
+  PFMP_REQUIRE(op && ns && split_slot(prec) >= 0, PFMP_E_INVALID, "bad argument");
+  *ns = op->nsplit[split_slot(prec)];
+  API_END
+}
+
 int pfmp_dslash(pfmp_op* op, int prec, void* out, const void* in, int out_parity, int dagger) {
   API_BEGIN
   PFMP_REQUIRE(op && out && in && out != in && (out_parity == 0 || out_parity == 1), PFMP_E_INVALID, "bad argument");
@@ -291,6 +336,31 @@ int pfmp_kop(pfmp_op* op, int prec, void* out, const void* in, double* in_K_in) 
     PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     PFMP_CUDA(cudaStreamSynchronize(c->stream));
     *in_K_in = c->h_sums[0];
+  }
+  API_END
+}
+
+int pfmp_true_residual(pfmp_op* op, int arith, void* r, const void* x, const void* b, double* rel) {
+  API_BEGIN
+  PFMP_REQUIRE(op && r && x && b && r != x && r != b, PFMP_E_INVALID, "bad argument");
+  PFMP_REQUIRE(arith == PFMP_F64 || arith == PFMP_DF, PFMP_E_INVALID, "arith must be PFMP_F64 or PFMP_DF");
+  pfmp_ctx* c = op->ctx;
+  double rr;
+  if (arith == PFMP_DF) {
+    rr = true_residual_df(op, x, b, r);
+  } else {
+    void* Ax = op->cg64[2];
+    kop(op, PFMP_F64, Ax, x, nullptr, nullptr);
+    blas_xmy_norm(c, b, Ax, r, c->d_sums);
+    PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    PFMP_CUDA(cudaStreamSynchronize(c->stream));
+    rr = c->h_sums[0];
+  }
+  if (rel) {
+    blas_norm2(c, PFMP_F64, b, c->d_sums);
+    PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    PFMP_CUDA(cudaStreamSynchronize(c->stream));
+    *rel = c->h_sums[0] > 0 ? std::sqrt(rr / c->h_sums[0]) : 0.0;
   }
   API_END
 }
@@ -662,7 +732,8 @@ int pfmp_profile_begin(pfmp_ctx* ctx) {
 int pfmp_profile_end(pfmp_ctx* ctx, int cls, int64_t* launches, double* total_ms, double* total_bytes) {
   API_BEGIN
   PFMP_REQUIRE(ctx && launches && total_ms && total_bytes, PFMP_E_INVALID, "null argument");
-  PFMP_REQUIRE(cls == PFMP_KERNEL_HOP_F32 || cls == PFMP_KERNEL_HOP_F64, PFMP_E_INVALID, "bad kernel class");
+  PFMP_REQUIRE(cls == PFMP_KERNEL_HOP_F32 || cls == PFMP_KERNEL_HOP_F64 || cls == PFMP_KERNEL_HOP_DF, PFMP_E_INVALID,
+               "bad kernel class");
   long n = 0;
   profile_end(ctx, cls, &n, total_ms, total_bytes);
   *launches = n;

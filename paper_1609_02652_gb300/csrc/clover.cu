@@ -10,6 +10,7 @@
 #include <cstring>
 
 #include "context.h"
+#include "dfloat.cuh"
 #include "fields.cuh"
 
 namespace pfmp {
@@ -79,8 +80,18 @@ struct CloverOut {
   double2* Ai64;  // odd: A^{-1}
   float4* A32;
   float4* Ai32;
+  float4* Adf;    // double-float copies of A64 / Ai64
+  float4* Aidf;
   int* bad;
 };
+
+__device__ void store_clover_df(float4* f, const HermBlock<double> b[2], int cb, int Vh) {
+  for (int blk = 0; blk < 2; ++blk) {
+    float4* g = f + (size_t)(18 * blk) * Vh;
+    for (int k = 0; k < 3; ++k) g[(size_t)k * Vh + cb] = split2(make_double2(b[blk].d[2 * k], b[blk].d[2 * k + 1]));
+    for (int k = 0; k < 15; ++k) g[(size_t)(3 + k) * Vh + cb] = split2(make_double2(b[blk].o[k].re, b[blk].o[k].im));
+  }
+}
 
 __device__ void store_block32(float4* f, const HermBlock<double>& b, int blk, int cb, int Vh) {
   float4* g = f + (size_t)(9 * blk) * Vh;
@@ -178,10 +189,12 @@ __global__ void k_clover_build(Geom g, const double2* __restrict__ U, double kc,
     }
     if (p == 0) {
       store_clover(out.A64, B, cb, g.Vh);
+      store_clover_df(out.Adf, B, cb, g.Vh);
       store_block32(out.A32, B[0], 0, cb, g.Vh);
       store_block32(out.A32, B[1], 1, cb, g.Vh);
     } else {
       store_clover(out.Ai64, B, cb, g.Vh);
+      store_clover_df(out.Aidf, B, cb, g.Vh);
       store_block32(out.Ai32, B[0], 0, cb, g.Vh);
       store_block32(out.Ai32, B[1], 1, cb, g.Vh);
     }
@@ -197,6 +210,8 @@ void clover_build(pfmp_op* op) {
   o.Ai64 = op->clov64[1];
   o.A32 = op->clov32[0];
   o.Ai32 = op->clov32[1];
+  o.Adf = op->clovdf[0];
+  o.Aidf = op->clovdf[1];
   o.bad = (int*)(c->d_sums + 8);
   PFMP_CUDA(cudaMemsetAsync(o.bad, 0, sizeof(int), c->stream));
   dim3 grid(nblocks(c->g.Vh, 128), 2);

@@ -50,6 +50,7 @@ struct pfmp_ctx {
   double2* U64 = nullptr;    // master [2][4][9][Vh]
   double2* U64c = nullptr;   // compressed [2][4][6][Vh]
   float4* U32 = nullptr;     // compressed [2][4][3][Vh]
+  float4* Udf = nullptr;     // double-float full links [2][4][9][Vh] (complex as hi/lo pairs)
   pfmp::ReduceBuf rb{};
   double* d_sums = nullptr;  // [64] results of generic reductions
   double* h_sums = nullptr;  // pinned mirror [64]
@@ -62,6 +63,11 @@ struct pfmp_op {
   double kappa = 0, csw = 0;
   double2* clov64[2] = {nullptr, nullptr};  // [0]: A on even sites, [1]: A^{-1} on odd sites
   float4* clov32[2] = {nullptr, nullptr};
+  float4* clovdf[2] = {nullptr, nullptr};   // double-float copy of clov64
+  float4* tdf = nullptr;                    // odd / even double-float temporaries
+  float4* edf = nullptr;
+  float4* xdf = nullptr;
+  float4* kdf = nullptr;
   double logdet_oo = 0;
   long built_version = -1;
   // workspace (odd temporaries and even scratch)
@@ -84,6 +90,8 @@ struct pfmp_op {
   cudaStream_t cap = nullptr;
   pfmp::MSWork* ms = nullptr;  // multi-shift workspace (grown on demand)
   long long kapply = 0;         // K applications issued (graph replays not included)
+  int nsplit[3] = {1, 1, 1};    // threads per site of the stencil kernels: FP64, FP32, double-float
+  int hop_block = 128;          // threads per block of the stencil kernels (32..128)
 };
 
 namespace pfmp {
@@ -114,6 +122,9 @@ void mhat(pfmp_op* op, int prec, void* out, const void* in, bool dagger, double*
 void kop(pfmp_op* op, int prec, void* out, const void* in, double* pKp_dev, CGScalars* scal);
 
 void hop_clov_odd(pfmp_op* op, void* out, const void* in, bool dagger);
+void kop_df(pfmp_op* op, void* out, const void* in);
+// r = b - K x with K applied in double-float; returns |r|^2 (synchronises)
+double true_residual_df(pfmp_op* op, const void* x64, const void* b64, void* r64);
 
 // force.cu
 void force_hop(pfmp_ctx* c, double* F, int pz, const void* Lf, const void* Rf, const void* Lb, const void* Rb,

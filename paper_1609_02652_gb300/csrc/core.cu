@@ -7,6 +7,7 @@
 #include "context.h"
 #include "fields.cuh"
 #include "su3.cuh"
+#include "dfloat.cuh"
 
 namespace pfmp {
 
@@ -77,7 +78,7 @@ __global__ void k_gauge_to_canonical(Geom g, const double2* __restrict__ U, doub
 }
 
 __global__ void k_gauge_compress(Geom g, const double2* __restrict__ U, double2* __restrict__ U64c,
-                                 float4* __restrict__ U32) {
+                                 float4* __restrict__ U32, float4* __restrict__ Udf) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   const int pm = blockIdx.y;  // parity*4 + mu
   if (cb >= g.Vh) return;
@@ -86,6 +87,8 @@ __global__ void k_gauge_compress(Geom g, const double2* __restrict__ U, double2*
   for (int k = 0; k < 6; ++k) v[k] = src[(size_t)k * g.Vh + cb];
   double2* d64 = U64c + (size_t)(pm * 6) * g.Vh;
   for (int k = 0; k < 6; ++k) d64[(size_t)k * g.Vh + cb] = v[k];
+  float4* ddf = Udf + (size_t)(pm * 9) * g.Vh;
+  for (int k = 0; k < 9; ++k) ddf[(size_t)k * g.Vh + cb] = split2(src[(size_t)k * g.Vh + cb]);
   float4* d32 = U32 + (size_t)(pm * 3) * g.Vh;
   for (int k = 0; k < 3; ++k)
     d32[(size_t)k * g.Vh + cb] =
@@ -169,7 +172,7 @@ static double* canon_scratch(pfmp_ctx* c, size_t doubles) {
 
 void gauge_refresh_compressed(pfmp_ctx* c) {
   dim3 grid(nblocks(c->g.Vh), 8);
-  k_gauge_compress<<<grid, kBlock, 0, c->stream>>>(c->g, c->U64, c->U64c, c->U32);
+  k_gauge_compress<<<grid, kBlock, 0, c->stream>>>(c->g, c->U64, c->U64c, c->U32, c->Udf);
   PFMP_CHECK_LAUNCH();
   c->gauge_version++;
 }
@@ -205,6 +208,7 @@ pfmp_ctx* ctx_create(const int dims[4], int bc_t, void* stream) {
     c->U64 = (double2*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 9 * sizeof(double2));
     c->U64c = (double2*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 6 * sizeof(double2));
     c->U32 = (float4*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 3 * sizeof(float4));
+    c->Udf = (float4*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 9 * sizeof(float4));
     c->rb.partials = (double*)dev_alloc((size_t)kMaxReduceBlocks * kMaxSums * sizeof(double));
     c->rb.counter = (unsigned*)dev_alloc(sizeof(unsigned));
     PFMP_CUDA(cudaMemset(c->rb.counter, 0, sizeof(unsigned)));
@@ -214,6 +218,7 @@ pfmp_ctx* ctx_create(const int dims[4], int bc_t, void* stream) {
     dev_free(c->U64);
     dev_free(c->U64c);
     dev_free(c->U32);
+    dev_free(c->Udf);
     dev_free(c->rb.partials);
     dev_free(c->rb.counter);
     dev_free(c->d_sums);
@@ -278,6 +283,7 @@ void ctx_destroy(pfmp_ctx* c) {
   dev_free(c->U64);
   dev_free(c->U64c);
   dev_free(c->U32);
+  dev_free(c->Udf);
   dev_free(c->rb.partials);
   dev_free(c->rb.counter);
   dev_free(c->d_sums);

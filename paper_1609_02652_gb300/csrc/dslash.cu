@@ -10,6 +10,7 @@
 //             an optional grid reduction of ||out||^2 feeding the CG scalars.
 // M-hat^dag uses the adjoint hop (projector signs swapped): A is Hermitian, so
 // M-hat^dag = A_ee - kappa^2 H^dag_eo A_oo^{-1} H^dag_oe.
+#include "dfloat.cuh"
 #include "hop.cuh"
 
 namespace pfmp {
@@ -57,7 +58,9 @@ static HopParams<PREC> params(pfmp_op* op, int p, void* out, const void* in) {
   a.p = p;
   a.out = (vec*)out;
   a.in = (const vec*)in;
-  a.gauge = PREC == PFMP_F64 ? (const vec*)(const void*)op->ctx->U64c : (const vec*)(const void*)op->ctx->U32;
+  a.gauge = PREC == PFMP_F64   ? (const vec*)(const void*)op->ctx->U64c
+            : PREC == PREC_DF  ? (const vec*)(const void*)op->ctx->Udf
+                               : (const vec*)(const void*)op->ctx->U32;
   a.clov = nullptr;
   a.x = nullptr;
   a.coef = 1.0;
@@ -72,22 +75,39 @@ static HopParams<PREC> params(pfmp_op* op, int p, void* out, const void* in) {
 // blocks (72 reals) and for EPI_XPAY the local input spinor
 template <int PREC>
 static double hop_bytes(int epi, int Vh) {
-  const double reals = 8 * 12 + 24 + 24 + (epi >= EPI_CLOV ? 72 : 0) + (epi == EPI_XPAY ? 24 : 0);
-  return reals * (PREC == PFMP_F64 ? 8 : 4) * (double)Vh;
+  const double link = PREC == PREC_DF ? 18 : 12;
+  const double reals = 8 * link + 24 + 24 + (epi >= EPI_CLOV ? 72 : 0) + (epi == EPI_XPAY ? 24 : 0);
+  return reals * (PREC == PFMP_F32 ? 4 : 8) * (double)Vh;
+}
+
+template <int PREC>
+static int split_of(const pfmp_op* op) {
+  return op->nsplit[PREC == PFMP_F64 ? 0 : (PREC == PFMP_F32 ? 1 : 2)];
 }
 
 template <int PREC, bool DAG, int EPI, bool RED>
-static void launch(const HopParams<PREC>& a, pfmp_ctx* c) {
+static void launch(const HopParams<PREC>& a, pfmp_op* op) {
+  pfmp_ctx* c = op->ctx;
   cudaEvent_t ev;
   prof_start(c, &ev);
-  k_hop<PREC, DAG, EPI, RED><<<nblocks(a.g.Vh, kHopBlock), kHopBlock, 0, c->stream>>>(a);
+  const int ns = split_of<PREC>(op);
+  const long n = (long)a.g.Vh * ns;
+  const int bs = op->hop_block;
+  switch (ns) {
+    case 2: k_hop_split<PREC, DAG, EPI, RED, 2><<<nblocks(n, bs), bs, 0, c->stream>>>(a); break;
+    case 4: k_hop_split<PREC, DAG, EPI, RED, 4><<<nblocks(n, bs), bs, 0, c->stream>>>(a); break;
+    case 8: k_hop_split<PREC, DAG, EPI, RED, 8><<<nblocks(n, bs), bs, 0, c->stream>>>(a); break;
+    default: k_hop<PREC, DAG, EPI, RED><<<nblocks(a.g.Vh, bs), bs, 0, c->stream>>>(a); break;
+  }
   PFMP_CHECK_LAUNCH();
-  prof_stop(c, PREC == PFMP_F64 ? PFMP_KERNEL_HOP_F64 : PFMP_KERNEL_HOP_F32, hop_bytes<PREC>(EPI, a.g.Vh), ev);
+  prof_stop(c, PREC == PFMP_F64 ? PFMP_KERNEL_HOP_F64 : (PREC == PREC_DF ? PFMP_KERNEL_HOP_DF : PFMP_KERNEL_HOP_F32),
+            hop_bytes<PREC>(EPI, a.g.Vh), ev);
 }
 
 template <int PREC>
 static const typename Prec<PREC>::vec* clov_ptr(pfmp_op* op, int parity) {
   if (PREC == PFMP_F64) return (const typename Prec<PREC>::vec*)(const void*)op->clov64[parity];
+  if (PREC == PREC_DF) return (const typename Prec<PREC>::vec*)(const void*)op->clovdf[parity];
   return (const typename Prec<PREC>::vec*)(const void*)op->clov32[parity];
 }
 
@@ -100,9 +120,9 @@ template <int PREC>
 static void hop_t(pfmp_op* op, void* out, const void* in, int p, bool dagger) {
   auto a = params<PREC>(op, p, out, in);
   if (dagger)
-    launch<PREC, true, EPI_PLAIN, false>(a, op->ctx);
+    launch<PREC, true, EPI_PLAIN, false>(a, op);
   else
-    launch<PREC, false, EPI_PLAIN, false>(a, op->ctx);
+    launch<PREC, false, EPI_PLAIN, false>(a, op);
 }
 
 void hop(pfmp_op* op, int prec, void* out, const void* in, int out_parity, bool dagger) {
@@ -126,8 +146,8 @@ void clover_mul(pfmp_op* op, int prec, void* out, const void* in, int parity) {
 
 template <int PREC>
 static void mhat_t(pfmp_op* op, void* out, const void* in, bool dagger, double* norm_out, CGScalars* scal) {
-  void* t = PREC == PFMP_F64 ? (void*)op->t64 : (void*)op->t32;
-  pfmp_ctx* s = op->ctx;
+  void* t = PREC == PFMP_F64 ? (void*)op->t64 : (PREC == PREC_DF ? (void*)op->tdf : (void*)op->t32);
+  pfmp_op* s = op;
   // t = A_oo^{-1} H_oe in
   auto a1 = params<PREC>(op, 1, t, in);
   a1.clov = clov_ptr<PREC>(op, 1);
@@ -189,6 +209,14 @@ void mhat(pfmp_op* op, int prec, void* out, const void* in, bool dagger, double*
     mhat_t<PFMP_F32>(op, out, in, dagger, norm_out, scal);
 }
 
+// K in double-float: in/out are df even fields ([12][Vh] float4), FP32-pipe arithmetic
+void kop_df(pfmp_op* op, void* out, const void* in) {
+  require_clover(op);
+  op->kapply += 1;
+  mhat_t<PREC_DF>(op, op->edf, in, false, nullptr, nullptr);
+  mhat_t<PREC_DF>(op, out, op->edf, true, nullptr, nullptr);
+}
+
 // out (odd) = A_oo^{-1} H_oe in (or the adjoint hop), FP64: the first half of M-hat,
 // used by the force terms
 void hop_clov_odd(pfmp_op* op, void* out, const void* in, bool dagger) {
@@ -196,9 +224,9 @@ void hop_clov_odd(pfmp_op* op, void* out, const void* in, bool dagger) {
   auto a = params<PFMP_F64>(op, 1, out, in);
   a.clov = clov_ptr<PFMP_F64>(op, 1);
   if (dagger)
-    launch<PFMP_F64, true, EPI_CLOV, false>(a, op->ctx);
+    launch<PFMP_F64, true, EPI_CLOV, false>(a, op);
   else
-    launch<PFMP_F64, false, EPI_CLOV, false>(a, op->ctx);
+    launch<PFMP_F64, false, EPI_CLOV, false>(a, op);
 }
 
 // out = K in; <in, K in> = ||M-hat in||^2 is reduced in the second kernel of M-hat

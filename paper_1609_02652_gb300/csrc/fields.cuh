@@ -172,4 +172,23 @@ __device__ __forceinline__ Spinor<T> clover_apply(const HermBlock<T> B[2], const
   return out;
 }
 
+// complex entries per storage chunk: 2 for FP32 (float4), 1 for FP64 and double-float
+template <int PREC>
+struct ChunkInfo {
+  static constexpr int per = PREC == PFMP_F32 ? 2 : 1;
+  static constexpr int n = 12 / per;
+};
+
+template <int PREC>
+__device__ __forceinline__ void store_chunk(typename Prec<PREC>::vec* f, int k, int cb, int Vh,
+                                            const cplx<typename Prec<PREC>::real>* v);
+template <>
+__device__ __forceinline__ void store_chunk<PFMP_F32>(float4* f, int k, int cb, int Vh, const cplx<float>* v) {
+  f[(size_t)k * Vh + cb] = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
+}
+template <>
+__device__ __forceinline__ void store_chunk<PFMP_F64>(double2* f, int k, int cb, int Vh, const cplx<double>* v) {
+  f[(size_t)k * Vh + cb] = make_double2(v[0].re, v[0].im);
+}
+
 }  // namespace pfmp

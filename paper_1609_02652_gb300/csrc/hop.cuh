@@ -108,6 +108,137 @@ __device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site(const HopP
   return out;
 }
 
+// ---------------------------------------------------------------- split-site kernel
+// NS threads per output site: thread t takes the hop terms t, t + NS, ... (term =
+// 2 mu + {0 forward, 1 backward}), the partial spinors are summed by a butterfly of
+// warp shuffles, and the first thread of the site applies the epilogue.  Measured on
+// GB300 this is slower than one thread per site at every lattice size from 8^3x16 to
+// 32^3x64, in FP32, FP64 and double-float; it is kept as an option (pfmp_op_set_split)
+// with parity tests, and the default is one thread per site.
+template <int PREC, int MU, int FWD, int SF>
+__device__ __forceinline__ void hop_term(Spinor<typename Prec<PREC>::real>& acc, const HopParams<PREC>& a,
+                                         const int x[4], int cb) {
+  using T = typename Prec<PREC>::real;
+  constexpr int LV = Prec<PREC>::link_vecs;
+  const Geom& g = a.g;
+  const int Vh = g.Vh;
+  const int n = nbr_cb(g, x, MU, FWD ? +1 : -1);
+  Spinor<T> psi;
+  load_spinor(psi, a.in, n, Vh);
+  Mat3<T> U;
+  if (FWD) {
+    Half<T> h = project<MU, SF>(psi);
+    load_link(U, a.gauge + (size_t)((a.p * 4 + MU) * LV) * Vh, cb, Vh);
+    Half<T> r = mul_half(U, h);
+    if (MU == 3 && x[3] == g.L[3] - 1) scale_half(r, (T)g.bc_t);
+    accumulate<MU, SF>(acc, r);
+  } else {
+    Half<T> h = project<MU, -SF>(psi);
+    load_link(U, a.gauge + (size_t)(((1 - a.p) * 4 + MU) * LV) * Vh, n, Vh);
+    Half<T> r = mul_half_dag(U, h);
+    if (MU == 3 && x[3] == 0) scale_half(r, (T)g.bc_t);
+    accumulate<MU, -SF>(acc, r);
+  }
+}
+
+template <int PREC, int SF>
+__device__ __forceinline__ void hop_term_rt(int term, Spinor<typename Prec<PREC>::real>& acc,
+                                            const HopParams<PREC>& a, const int x[4], int cb) {
+  switch (term) {
+    case 0: hop_term<PREC, 0, 1, SF>(acc, a, x, cb); break;
+    case 1: hop_term<PREC, 0, 0, SF>(acc, a, x, cb); break;
+    case 2: hop_term<PREC, 1, 1, SF>(acc, a, x, cb); break;
+    case 3: hop_term<PREC, 1, 0, SF>(acc, a, x, cb); break;
+    case 4: hop_term<PREC, 2, 1, SF>(acc, a, x, cb); break;
+    case 5: hop_term<PREC, 2, 0, SF>(acc, a, x, cb); break;
+    case 6: hop_term<PREC, 3, 1, SF>(acc, a, x, cb); break;
+    default: hop_term<PREC, 3, 0, SF>(acc, a, x, cb); break;
+  }
+}
+
+__device__ __forceinline__ float shfl_x(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ double shfl_x(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+template <typename T>
+__device__ __forceinline__ T shfl_x(T v, int m) {  // double-float and other pair types
+  return T(shfl_x(v.hi, m), shfl_x(v.lo, m));
+}
+
+template <int PREC, bool DAG, int EPI, bool REDUCE, int NS>
+__global__ void __launch_bounds__(128) k_hop_split(HopParams<PREC> a) {
+  using T = typename Prec<PREC>::real;
+  if (a.scal && a.scal->done) return;
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const int t = (int)(tid % NS);
+  const int cb0 = (int)(tid / NS);
+  const bool live = cb0 < a.g.Vh;
+  const int cb = live ? cb0 : a.g.Vh - 1;  // idle lanes still join the shuffles
+  int x[4];
+  cb_coords(a.g, cb, a.p, x);
+  Spinor<T> acc;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc.s[s][c] = mk<T>(0, 0);
+  constexpr int SF = DAG ? +1 : -1;
+#pragma unroll
+  for (int k = 0; k < 8 / NS; ++k) hop_term_rt<PREC, SF>(t + k * NS, acc, a, x, cb);
+#pragma unroll
+  for (int m = 1; m < NS; m <<= 1)
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc.s[s][c].re = acc.s[s][c].re + shfl_x(acc.s[s][c].re, m);
+        acc.s[s][c].im = acc.s[s][c].im + shfl_x(acc.s[s][c].im, m);
+      }
+  // the first thread of the site applies the epilogue to the summed hop, as in k_hop
+  const T cf = (T)a.coef;
+  double nrm[1] = {0.0};
+  if (t == 0 && live) {
+    Spinor<T> out;
+    if (EPI == EPI_PLAIN) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out.s[s][c] = cf * acc.s[s][c];
+    } else if (EPI == EPI_CLOV) {
+      HermBlock<T> B[2];
+      load_clover(B, a.clov, cb, a.g.Vh);
+      out = clover_apply(B, acc);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out.s[s][c] = cf * out.s[s][c];
+    } else {
+      HermBlock<T> B[2];
+      load_clover(B, a.clov, cb, a.g.Vh);
+      Spinor<T> xl;
+      load_spinor(xl, a.x, cb, a.g.Vh);
+      out = clover_apply(B, xl);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out.s[s][c] = out.s[s][c] + cf * acc.s[s][c];
+    }
+    store_spinor(a.out, out, cb, a.g.Vh);
+    if (REDUCE) {
+      double tt = 0;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tt += (double)norm2(out.s[s][c]);
+      nrm[0] = tt;
+    }
+  }
+  if (REDUCE) {
+    double tot[1];
+    if (grid_sum<1>(nrm, a.rb, tot)) {
+      *a.norm_out = tot[0];
+      if (a.scal) a.scal->alpha = a.scal->rr / tot[0];
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ double spinor_norm2(const Spinor<T>& v) {
   double t = 0;

@@ -868,15 +868,11 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
       const double rn = std::sqrt(rr);
       if (rn < delta * rn0 || rn * rn < 0.25 * tol * tol * bb) break;
     }
-    // outer FP64 correction
+    // outer correction in FP64 storage, true residual in double-float
     blas_add_lo(c, x, wk.e);
-    kop(op, PFMP_F64, Ax, x, nullptr, nullptr);
     *kapply += 1;
-    blas_xmy_norm(c, b, Ax, r64, c->d_sums);
-    PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    PFMP_CUDA(cudaStreamSynchronize(c->stream));
     *outer += 1;
-    res = std::sqrt(c->h_sums[0] / bb);
+    res = std::sqrt(true_residual_df(op, x, b, r64) / bb);
     PFMP_REQUIRE(std::isfinite(res), PFMP_E_NAN, "FGCR residual is not finite");
     if (res < tol) break;
     stall = res > 0.9 * prev ? stall + 1 : 0;
@@ -893,11 +889,7 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
       *fallback_iters = it;
       *kapply += kap;
       caxpby(c, 1.0, ec, 1.0, x);
-      kop(op, PFMP_F64, Ax, x, nullptr, nullptr);
-      blas_xmy_norm(c, b, Ax, r64, c->d_sums);
-      PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      PFMP_CUDA(cudaStreamSynchronize(c->stream));
-      res = std::sqrt(c->h_sums[0] / bb);
+      res = std::sqrt(true_residual_df(op, x, b, r64) / bb);
       break;
     }
   }

@@ -179,9 +179,9 @@ int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int c
       total += it;
       *kapply += it;
       PFMP_REQUIRE(std::isfinite(op->h_scal->rr), PFMP_E_NAN, "sloppy CG residual became NaN/Inf");
-      // reliable update
+      // reliable update: the true residual in double-float (FP64 accuracy on the FP32 pipe)
       blas_add_lo(c, x, xs32);
-      rr_true = true_residual(op, x, b, r, Ap);
+      rr_true = true_residual_df(op, x, b, r);
       *kapply += 1;
       *rel_updates += 1;
       if (std::sqrt(rr_true / bb) < tol) break;

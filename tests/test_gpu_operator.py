@@ -130,3 +130,30 @@ def test_blas(setup):
     x32 = g.buf(1)
     capi.pfmp_convert(g.ctx, x32, 1, x64, 0)
     assert rel_l2(lat.even * g.unpack(x32, 1, 0), lat.even * a) < 1e-7
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["f64", "f32"])
+@pytest.mark.parametrize("ns", [1, 2, 4, 8])
+def test_split_site_kernels(setup, prec, ns):
+    """Every threads-per-site variant of the stencil gives M-hat, M-hat^dag, K and the plain
+    hop to the parity bar."""
+    from oracle.dirac import WilsonClover, hop
+
+    lat, U, g, capi = setup
+    W = WilsonClover(lat, U, 0.125, 1.0)
+    op = g.op(0.125, 1.0)
+    capi.pfmp_op_set_split(op, prec, ns)
+    assert capi.pfmp_op_get_split(op, prec) == ns
+    bar = F64_BAR if prec == 0 else F32_BAR
+    psi = lat.even * spinor(lat, 9)
+    bi, bo = g.pack(psi, prec, 0), g.buf(prec)
+    for dagger, ref in [(0, W.mhat(psi)), (1, W.mhat_dag(psi))]:
+        capi.pfmp_mhat(op, prec, bo, bi, dagger)
+        assert rel_l2(lat.even * g.unpack(bo, prec, 0), ref) < bar
+    nrm = capi.pfmp_kop(op, prec, bo, bi, want_norm=True)
+    ref = W.K(psi)
+    assert rel_l2(lat.even * g.unpack(bo, prec, 0), ref) < bar
+    assert abs(nrm - (psi.conj() * ref).sum().real.item()) < bar * 10 * nrm
+    bo1 = g.buf(prec)
+    capi.pfmp_dslash(op, prec, bo1, bi, 1, 0)
+    assert rel_l2(lat.odd * g.unpack(bo1, prec, 1), lat.odd * hop(lat, U, psi)) < bar

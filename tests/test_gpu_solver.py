@@ -101,3 +101,38 @@ def test_fp64_cg_full_size_matches_oracle_iterations():
         capi.pfmp_op_destroy(op)
     finally:
         capi.pfmp_ctx_destroy(ctx)
+
+
+def test_double_float_true_residual():
+    """The double-float residual b - K x (FP32-pair arithmetic) agrees with the FP64 one and
+    with the oracle's, both for an O(1) residual and for a converged solution."""
+    from oracle.dirac import WilsonClover
+    from paper_1609_02652_gb300 import capi
+
+    dims = (6, 4, 4, 8)
+    lat, U = oracle_gauge(dims, 0.5, 7)
+    g = Gpu(lat, U)
+    try:
+        op = g.op(0.13, 1.0)
+        W = WilsonClover(lat, U, 0.13, 1.0)
+        b = lat.even * torch.tensor(pin.spinor(dims, 5)).reshape(*lat.shape, 4, 3)
+        x = lat.even * torch.tensor(pin.spinor(dims, 6)).reshape(*lat.shape, 4, 3)
+        bb, xx = g.pack(b, 0, 0), g.pack(x, 0, 0)
+        r64, rdf = g.buf(0), g.buf(0)
+        capi.pfmp_true_residual(op, capi.PFMP_F64, r64, xx, bb)
+        capi.pfmp_true_residual(op, capi.PFMP_DF, rdf, xx, bb)
+        ref = b - W.K(x)
+        scale = float(torch.linalg.vector_norm(W.K(x)))
+        assert float(torch.linalg.vector_norm(lat.even * g.unpack(rdf, 0, 0) - ref)) < 1e-12 * scale
+        assert float(torch.linalg.vector_norm(lat.even * g.unpack(r64, 0, 0) - ref)) < 1e-13 * scale
+        # converged x: the residual itself is ~1e-11 |b| and must still be resolved
+        prm = capi.SolverParams(method=0, tol=1e-11, max_iter=4000, delta=0.1, check_every=8)
+        capi.pfmp_solve(op, prm, xx, bb)
+        xs = lat.even * g.unpack(xx, 0, 0)
+        ref = b - W.K(xs)
+        rel_df = capi.pfmp_true_residual(op, capi.PFMP_DF, rdf, xx, bb)
+        rel_ref = float(torch.linalg.vector_norm(ref) / torch.linalg.vector_norm(b))
+        assert abs(rel_df - rel_ref) < 0.05 * rel_ref + 1e-13
+        assert float(torch.linalg.vector_norm(lat.even * g.unpack(rdf, 0, 0) - ref)) < 1e-13 * float(torch.linalg.vector_norm(b))
+    finally:
+        g.close()
