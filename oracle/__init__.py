@@ -19,9 +19,13 @@ Modules
   dirac       clover field, Wilson hop, full M, even-odd Schur complement M-hat, K, J
   solvers     CG, batched CG on normal equations for complex shifts, dense solves
   cheby       Chebyshev roots / normalisation / residues (App. A, App. C)
-  action      gauge action, PF-MP action terms, heatbath, forces (App. C)
+  action      gauge action, PF-MP action terms, heatbath, forces (App. C); the general
+              term list (filter, factorised filter, filter correction, Hasenbusch
+              ratio, inverse) and the paper's schemes 1PF, 2PF, 1MP, 2MP, PF-MP,
+              2PF-1MP, 1PF-2MP
   integrator  2MN / leapfrog step arrays, generalised multi-scale merge (App. B),
-              MD trajectory and Metropolis test (Sec. 2.1)
+              MD trajectory and Metropolis test (Sec. 2.1), for PF-MP and for a
+              general term list
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a closed
 form, an invariant, brute force or a value the paper prints, except the clover-term

@@ -198,3 +198,176 @@ class PFMP:
             return 2.0 * _vdot(chi, Wv.mhat_dag(phi3)).real - _vdot(chi, Mv.K(chi)).real
 
         return deriv(self.lat, U, f)
+
+
+# ====================================================================================
+# General filtered / mass-preconditioned actions (Sec. 2.2 eq. hasenbusch, Sec. 2.3 eqs.
+# 1poly and 2poly, Sec. 2.5 eq. pfmp_action, Sec. 3.6 (2PF-1MP and 1PF-2MP))
+# ====================================================================================
+#
+# A term list over a list of hopping parameters kappas[0..] (kappas[0] = the target
+# operator K; J_a = W_a^dag W_a with W_a = M-hat at kappas[a]; J_0 = K):
+#   gauge       S_G
+#   det         -2 sum_{x odd} log det A(x) at kappas[a]
+#   filter      phi^dag Q(J_a) phi,  Q = P_p2 / P_p1 (p1 = 0: P_p2)
+#   filtercorr  phi^dag [J_a P_p2(J_a)]^{-1} phi
+#   ratio       phi^dag W_a K_b^{-1} W_a^dag phi   (the paper's "J_a K_b^{-1}", see S_3 above)
+#   inv         phi^dag J_a^{-1} phi               (the first mass-preconditioning term)
+# Heatbath (derived so that every S_i(phi_i) = xi_i^dag xi_i):
+#   filter      phi = R_Q(J_a)^{-1} xi,  R_Q = sqrt(c) prod_{Im q_k < 0} (J_a - q_k)
+#   filtercorr  phi = R_p2(J_a)^dag W_a^dag xi
+#   ratio       phi = W_a J_a^{-1} M_b^dag xi  (M_b = M-hat at kappas[b])
+#   inv         phi = W_a^dag xi
+# Forces:
+#   filter      App. C eq. force_poly with the roots q_k and c in place of z_k and a_n
+#   filtercorr  App. C eq. force_polycorr at order p2
+#   ratio       2 Re chi^dag (dW_a^dag) phi - chi^dag dK_b chi,  chi = K_b^{-1} W_a^dag phi
+#   inv         -chi^dag dJ_a chi,  chi = J_a^{-1} phi
+
+FERMION_KINDS = ("filter", "filtercorr", "ratio", "inv")
+
+
+@dataclass
+class Term:
+    kind: str
+    a: int = 0
+    b: int = 0
+    p1: int = 0
+    p2: int = 0
+
+
+def scheme(name, p1=0, p2=0):
+    """Term lists of the actions the paper compares (Sec. 2, Sec. 3).  Hasenbusch kappas
+    are indexed from 1 upwards, lightest-first towards the target kappas[0]:
+      1PF      Sec. 2.3 eq. 1poly on K:            P_p2(K), [K P_p2(K)]^{-1}
+      2PF      Sec. 2.3 eq. 2poly on K:            P_p1(K), Q(K), [K P_p2(K)]^{-1}
+      1MP      Sec. 2.2 eq. hasenbusch:            J_1^{-1}, J_1 K^{-1}
+      2MP      two Hasenbusch masses:              J_1^{-1}, J_1 J_2^{-1}, J_2 K^{-1}
+      PF-MP    Sec. 2.5 eq. pfmp_action (1PF-1MP): P_p2(J_1), [J_1 P_p2(J_1)]^{-1}, J_1 K^{-1}
+      2PF-1MP  Sec. 3.6:  P_p1(J_1), Q(J_1), [J_1 P_p2(J_1)]^{-1}, J_1 K^{-1}
+      1PF-2MP  Sec. 3.6:  P_p2(J_1), [J_1 P_p2(J_1)]^{-1}, J_1 J_2^{-1}, J_2 K^{-1}
+    Every list starts with the gauge and clover-determinant terms."""
+    base = [Term("gauge"), Term("det", a=0)]
+    f = {
+        "1PF": [Term("filter", a=0, p2=p2), Term("filtercorr", a=0, p2=p2)],
+        "2PF": [Term("filter", a=0, p2=p1), Term("filter", a=0, p1=p1, p2=p2), Term("filtercorr", a=0, p2=p2)],
+        "1MP": [Term("inv", a=1), Term("ratio", a=1, b=0)],
+        "2MP": [Term("inv", a=1), Term("ratio", a=1, b=2), Term("ratio", a=2, b=0)],
+        "PF-MP": [Term("filter", a=1, p2=p2), Term("filtercorr", a=1, p2=p2), Term("ratio", a=1, b=0)],
+        "2PF-1MP": [Term("filter", a=1, p2=p1), Term("filter", a=1, p1=p1, p2=p2), Term("filtercorr", a=1, p2=p2),
+                    Term("ratio", a=1, b=0)],
+        "1PF-2MP": [Term("filter", a=1, p2=p2), Term("filtercorr", a=1, p2=p2), Term("ratio", a=1, b=2),
+                    Term("ratio", a=2, b=0)],
+    }[name]
+    return base + f
+
+
+class Action:
+    """A general action: ``terms`` over the hopping parameters ``kappas`` (same c_sw).
+    Pseudofermions belong to the fermion terms in list order."""
+
+    def __init__(self, lat: Lattice, beta, csw, kappas, terms, mu=1.2, nu=0.9, tol=1e-12):
+        self.lat, self.beta, self.csw = lat, beta, csw
+        self.kappas, self.terms = list(kappas), list(terms)
+        self.mu, self.nu, self.tol = mu, nu, tol
+        for t in self.terms:
+            if t.kind == "filter":
+                cheby.filter_roots(t.p1, t.p2, mu, nu)       # validates the orders
+            if t.kind == "filtercorr" and (t.p2 < 2 or t.p2 % 2):
+                raise ValueError("filter orders must be even")
+        self.pf = [i for i, t in enumerate(self.terms) if t.kind in FERMION_KINDS]
+
+    def op(self, U, a):
+        return WilsonClover(self.lat, U, self.kappas[a], self.csw)
+
+    # ---------------------------------------------------------------- heatbath
+    def heatbath(self, U, xis):
+        """One pseudofermion per fermion term, from the noise xis (same order)."""
+        phis = []
+        for i, xi in zip(self.pf, xis):
+            t = self.terms[i]
+            W = self.op(U, t.a)
+            if t.kind == "filter":
+                z, c = cheby.filter_roots(t.p1, t.p2, self.mu, self.nu)
+                zh, s = cheby.product_half(z)
+                xs, _ = multishift_cg(W.K, xi, -zh, tol=self.tol)
+                phis.append((s.reshape(-1, *([1] * xi.dim())) * xs).sum(0) / math.sqrt(c))
+            elif t.kind == "filtercorr":
+                phis.append(cheby.apply_R(W.K, W.mhat_dag(xi), t.p2, self.mu, self.nu, dagger=True))
+            elif t.kind == "ratio":
+                Mb = self.op(U, t.b)
+                y, _, _ = cg(W.K, Mb.mhat_dag(xi), tol=self.tol)
+                phis.append(W.mhat(y))
+            else:  # inv
+                phis.append(W.mhat_dag(xi))
+        return phis
+
+    # ---------------------------------------------------------------- actions
+    def S(self, U, i, phi=None):
+        t = self.terms[i]
+        if t.kind == "gauge":
+            return gauge_action(self.lat, U, self.beta)
+        if t.kind == "det":
+            return det_action(self.lat, U, self.kappas[t.a], self.csw) if self.csw != 0 else torch.zeros((), dtype=F64)
+        W = self.op(U, t.a)
+        if t.kind == "filter":
+            z, c = cheby.filter_roots(t.p1, t.p2, self.mu, self.nu)
+            return _vdot(phi, cheby.apply_product(W.K, phi, z, c)).real
+        if t.kind == "filtercorr":
+            shifts, r = cheby.residues(t.p2, self.mu, self.nu)
+            xs, _ = multishift_cg(W.K, phi, -shifts, tol=self.tol)
+            return sum(r[k] * _vdot(phi, xs[k]) for k in range(shifts.numel())).real
+        if t.kind == "ratio":
+            w = W.mhat_dag(phi)
+            x, _, _ = cg(self.op(U, t.b).K, w, tol=self.tol)
+            return _vdot(w, x).real
+        x, _, _ = cg(W.K, phi, tol=self.tol)            # inv
+        return _vdot(phi, x).real
+
+    # ---------------------------------------------------------------- forces
+    def F(self, U, i, phi=None):
+        t = self.terms[i]
+        lat, csw = self.lat, self.csw
+        ka = self.kappas[t.a]
+        Ja = lambda V: WilsonClover(lat, V, ka, csw).K
+        if t.kind == "gauge":
+            return deriv(lat, U, lambda V: gauge_action(lat, V, self.beta))
+        if t.kind == "det":
+            if csw == 0:
+                return torch.zeros(*lat.shape, 4, 8, dtype=F64)
+            return deriv(lat, U, lambda V: det_action(lat, V, ka, csw))
+        W = self.op(U, t.a)
+        J = W.K
+        if t.kind == "filter":
+            z, c = cheby.filter_roots(t.p1, t.p2, self.mu, self.nu)
+            m = z.numel()
+            chi = [None] * m
+            w = c * phi
+            chi[m - 1] = w
+            for k in range(m - 2, -1, -1):      # chi_k = c prod_{j>k} (J - q_j) phi
+                w = J(w) - z[k + 1] * w
+                chi[k] = w
+            eta = [phi]
+            for k in range(1, m):                # eta_k = prod_{j<k} (J - q_j^*) phi
+                eta.append(J(eta[-1]) - z[k - 1].conj() * eta[-1])
+            E, X = torch.stack(eta), torch.stack(chi)
+            return deriv(lat, U, lambda V: _vdot(E, Ja(V)(X)).real)
+        if t.kind == "filtercorr":
+            shifts, r = cheby.residues(t.p2, self.mu, self.nu)
+            xs, _ = multishift_cg(J, phi, -shifts, tol=self.tol)
+            conj_index = [int(torch.argmin((shifts - shifts[k].conj()).abs())) for k in range(shifts.numel())]
+            E = xs[conj_index]
+            X = r.reshape(-1, *([1] * phi.dim())) * xs
+            return deriv(lat, U, lambda V: -_vdot(E, Ja(V)(X)).real)
+        if t.kind == "ratio":
+            kb = self.kappas[t.b]
+            chi, _, _ = cg(self.op(U, t.b).K, W.mhat_dag(phi), tol=self.tol)
+
+            def f(V):
+                Wv = WilsonClover(lat, V, ka, csw)
+                Mv = WilsonClover(lat, V, kb, csw)
+                return 2.0 * _vdot(chi, Wv.mhat_dag(phi)).real - _vdot(chi, Mv.K(chi)).real
+
+            return deriv(lat, U, f)
+        chi, _, _ = cg(J, phi, tol=self.tol)             # inv
+        return deriv(lat, U, lambda V: -_vdot(chi, Ja(V)(chi)).real)

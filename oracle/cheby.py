@@ -17,6 +17,10 @@ Heatbath split (derived; the paper calls the heatbath negligible and gives no fo
 for even n the roots come in conjugate pairs and a_n > 0, so
   R(z) = sqrt(a_n) prod_{k: Im z_k < 0} (z - z_k),  P_n(z) = conj(R)(z) R(z) on the real axis,
 i.e. P(J) = R(J)^dag R(J) for Hermitian J.
+
+Factorised filters (App. A, Sec. 2.3 eq. 2poly): with (p1 + 1) | (p2 + 1) the ratio
+Q = P_p2 / P_p1 is the polynomial whose roots are those of P_p2 that P_p1 does not have,
+normalised by a_p2 / a_p1 (``filter_roots``); it splits as R_Q^dag R_Q the same way.
 """
 import math
 
@@ -90,3 +94,41 @@ def apply_R(J, v, n, mu, nu, dagger=False):
     for k in range(z.numel()):
         w = J(w) - z[k] * w
     return math.sqrt(norm(n, mu, nu)) * w
+
+
+def filter_roots(p1, p2, mu, nu):
+    """Roots q_k and normalisation c of the filter Q(z) = P_p2(z) / P_p1(z) = c prod_k (z - q_k).
+
+    App. A: two approximations with the same (mu, nu) factorise when (p1 + 1) divides
+    (p2 + 1); the roots of P_p1 (angles 2 pi j / (p1 + 1)) are then the roots of P_p2 with
+    index k = j (p2 + 1) / (p1 + 1), so Q keeps the other p2 - p1 roots of P_p2 and
+    c = a_p2 / a_p1.  p1 = 0 gives P_p2 itself (Q = P_p2, c = a_p2)."""
+    if p2 < 2 or p2 % 2 or p1 < 0 or p1 % 2:
+        raise ValueError("filter orders must be even (p1 >= 0, p2 >= 2)")
+    z = roots(p2, mu, nu)
+    if p1 == 0:
+        return z, norm(p2, mu, nu)
+    if p2 <= p1 or (p2 + 1) % (p1 + 1):
+        raise ValueError("P_p1 divides P_p2 only when (p1 + 1) divides (p2 + 1)")
+    m = (p2 + 1) // (p1 + 1)
+    keep = [k - 1 for k in range(1, p2 + 1) if k % m]
+    return z[keep], norm(p2, mu, nu) / norm(p1, mu, nu)
+
+
+def product_half(z):
+    """Half set of a conjugate-closed root list (Im < 0) and the residues s_k of
+    1 / prod_k (z - zh_k); the heatbath factor of c prod (z - z_k) is sqrt(c) prod (z - zh_k)."""
+    zh = z[z.imag < 0]
+    s = []
+    for i in range(zh.numel()):
+        others = torch.cat([zh[:i], zh[i + 1:]])
+        s.append(1.0 / torch.prod(zh[i] - others))
+    return zh, torch.stack(s)
+
+
+def apply_product(J, v, z, c):
+    """c prod_k (J - z_k) v, factors applied in list order."""
+    w = v
+    for k in range(z.numel()):
+        w = J(w) - z[k] * w
+    return c * w

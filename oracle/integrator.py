@@ -119,3 +119,36 @@ def trajectory(action, U0, p0, xis, u, levels, schedule):
         "H0": H0, "H1": H1, "dH": dH, "accepted": accepted, "S0": S0, "S1": S1,
         "U1": U, "p1": p, "U": U if accepted else U0, "phi": (phi1, phi2, phi3),
     }
+
+
+def trajectory_terms(action, U0, p0, xis, u, term_level, schedule):
+    """One trajectory of a general ``oracle.action.Action``: term i is integrated on
+    scheme ``term_level[i]`` of the merged schedule (-1: left out of H and of the MD)."""
+    phis = action.heatbath(U0, xis)
+    phi_of = {i: phis[k] for k, i in enumerate(action.pf)}
+    used = [i for i, l in enumerate(term_level) if l >= 0]
+
+    def total_S(U):
+        return {i: action.S(U, i, phi_of.get(i)).item() for i in used}
+
+    S0 = total_S(U0)
+    H0 = kinetic(p0) + sum(S0.values())
+    U, p = U0.clone(), p0.clone()
+    T, Slev = schedule
+    for k in range(len(T)):
+        if T[k] != 0.0:
+            U = link_update(U, p, T[k])
+        for j in range(len(Slev)):
+            eps = Slev[j][k]
+            if eps != 0.0:
+                for i in used:
+                    if term_level[i] == j:
+                        p = p - eps * action.F(U, i, phi_of.get(i))
+    S1 = total_S(U)
+    H1 = kinetic(p) + sum(S1.values())
+    dH = H1 - H0
+    accepted = bool(u < math.exp(-dH)) if dH > -700 else True
+    return {
+        "H0": H0, "H1": H1, "dH": dH, "accepted": accepted, "S0": S0, "S1": S1,
+        "U1": U, "p1": p, "U": U if accepted else U0, "phi": phis,
+    }
