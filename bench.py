@@ -492,6 +492,13 @@ def trajectory_4x4x4x4(capi, stream):
             "force_evals": int(info.force_evals), "steps": len(T)}
 
 
+def kernel_source():
+    """Bytes of the sources that define the FP32 stencil kernels (for the traffic record)."""
+    csrc = os.path.join(ROOT, "paper_1609_02652_gb300", "csrc")
+    return b"".join(open(os.path.join(csrc, f), "rb").read()
+                    for f in ("dslash.cu", "hop.cuh", "fields.cuh", "spin.cuh", "pfmp_internal.cuh"))
+
+
 def recorded_traffic():
     """DRAM bytes per launch of the FP32 stencil at 32^3x64 from the committed ncu summary,
     or None when the kernel source changed since those counters were taken."""
@@ -504,8 +511,7 @@ def recorded_traffic():
     txt = open(path).read()
     m = re.search(r"bytes_per_launch_32x32x32x64: (\d+)", txt)
     h = re.search(r"kernel_source_sha256: ([0-9a-f]+)", txt)
-    csrc = os.path.join(ROOT, "paper_1609_02652_gb300", "csrc")
-    src = open(os.path.join(csrc, "dslash.cu"), "rb").read() + open(os.path.join(csrc, "fields.cuh"), "rb").read()
+    src = kernel_source()
     if not m or not h or h.group(1) != hashlib.sha256(src).hexdigest():
         return None
     return int(m.group(1))
