@@ -23,6 +23,8 @@ Modules
               term list (filter, factorised filter, filter correction, Hasenbusch
               ratio, inverse) and the paper's schemes 1PF, 2PF, 1MP, 2MP, PF-MP,
               2PF-1MP, 1PF-2MP
+  spectrum    extreme eigenvalues of K (dense), Lanczos tridiagonal and its Ritz values
+              (App. A: the filter ellipse must enclose the spectrum)
   integrator  2MN / leapfrog step arrays, generalised multi-scale merge (App. B),
               MD trajectory and Metropolis test (Sec. 2.1), for PF-MP and for a
               general term list
