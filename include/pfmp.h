@@ -222,20 +222,73 @@ int pfmp_solve_multishift(pfmp_op* op, int nshift, const double* sigma_re, const
 int pfmp_poly_roots(int n, double mu, double nu, double* z_re, double* z_im, double* a_n);
 int pfmp_poly_apply(pfmp_op* op, int n, double mu, double nu, int which, void* out, const void* in);
 
-/* ---- PF-MP action, forces, trajectory (Sec. 2.1, 2.5, App. B, App. C) --------------
- * S = S_G + S_det + phi1^dag P(J) phi1 + phi2^dag [J P(J)]^{-1} phi2 + phi3^dag W K^{-1} W^dag phi3,
- * S_G = beta sum_{x,mu<nu} (1 - Re tr U_{mu nu} / 3), S_det = -2 sum_{x odd} log det A(x),
- * K at kappa, J = W^dag W with W = M-hat at kappa_h.  Pseudofermion heatbath from
- * Gaussian noise xi (density exp(-xi^dag xi)): phi1 = R(J)^{-1} xi1,
- * phi2 = R(J)^dag W^dag xi2, phi3 = W J^{-1} M-hat^dag xi3.  Forces are the algebra
- * coefficients dS/d omega_a for U -> exp(i omega_a T_a) U (App. C forms; F1 costs 2n - 2
- * J products, F2 one multi-shift solve with z_{n+1} = 0, F3 one CG on K).  All FP64.    */
+/* ---- spectral range (App. A) ----------------------------------------------------------
+ * The filter approximates K^{-1} only inside its ellipse (0 to 2 mu on the real axis),
+ * so (mu, nu) must enclose the spectrum of K.  pfmp_spectrum runs nsteps steps of the
+ * Lanczos recurrence on K (FP64, no reorthogonalisation) from the start vector v0 (FP64
+ * even device field, non-zero; not modified) and returns the extreme eigenvalues of the
+ * Lanczos tridiagonal T_k: lambda_min <= *lmin and *lmax <= lambda_max, converging to
+ * them (lmax within a few tens of steps, lmin more slowly, as sqrt of the condition
+ * number).  *steps = k, fewer than nsteps when the Krylov space closed.  alpha, beta
+ * (host arrays of nsteps, optional): the diagonal and off-diagonal of T_k.
+ * PFMP_E_INVALID for a zero start vector or nsteps < 1.  Synchronises.                 */
+int pfmp_spectrum(pfmp_op* op, int nsteps, const void* v0, double* lmin, double* lmax, double* alpha, double* beta,
+                  int* steps);
+
+/* ---- actions, forces, trajectory (Sec. 2.1-2.5, Sec. 3.6, App. A-C) ----------------
+ * An action is a list of terms over hopping parameters kappa[0..nkappa) that share c_sw.
+ * kappa[0] is the target operator K = M-hat^dag M-hat; J_a = W_a^dag W_a with
+ * W_a = M-hat at kappa[a] (J_0 = K).  Term kinds:
+ *   GAUGE       S_G = beta sum_{x,mu<nu} (1 - Re tr U_{mu nu} / 3)        (Table 3.1)
+ *   DET         S_det = -2 sum_{x odd} log det A(x) at kappa[a]            (even-odd clover)
+ *   FILTER      phi^dag Q(J_a) phi, Q = P_p2 / P_p1 (Sec. 2.3 eq. 2poly; p1 = 0: P_p2;
+ *               otherwise (p1 + 1) must divide (p2 + 1), App. A)
+ *   FILTERCORR  phi^dag [J_a P_p2(J_a)]^{-1} phi                          (eqs. 1poly, pfmp_action)
+ *   RATIO       phi^dag W_a K_b^{-1} W_a^dag phi: the paper's "J_a K_b^{-1}" (Sec. 2.2) in
+ *               its Hermitian form, K_b = J_b
+ *   INV         phi^dag J_a^{-1} phi                                       (eq. hasenbusch)
+ * Every fermion term (FILTER, FILTERCORR, RATIO, INV) owns one pseudofermion; they are
+ * numbered in term order.  Heatbath from Gaussian noise xi (density exp(-xi^dag xi)), so
+ * that each S_i(phi_i) = xi_i^dag xi_i:  FILTER phi = R_Q(J_a)^{-1} xi with
+ * R_Q = sqrt(c) prod_{Im q_k < 0} (J_a - q_k) (Q = c prod (z - q_k));  FILTERCORR
+ * phi = R_p2(J_a)^dag W_a^dag xi;  RATIO phi = W_a J_a^{-1} M_b^dag xi;  INV phi = W_a^dag xi.
+ * Forces are the algebra coefficients dS/d omega_a for U -> exp(i omega_a T_a) U:
+ * FILTER App. C eq. force_poly with the roots of Q (2q - 2 J products), FILTERCORR eq.
+ * force_polycorr (one multi-shift solve with z_{p2+1} = 0), RATIO
+ * 2 Re chi^dag dW_a^dag phi - chi^dag dK_b chi with chi = K_b^{-1} W_a^dag phi (one CG),
+ * INV -chi^dag dJ_a chi with chi = J_a^{-1} phi (one CG).  All FP64.
+ * The PF-MP action of Sec. 2.5 (pfmp_action_create) is the term list GAUGE, DET(0),
+ * FILTER(1, 0, n), FILTERCORR(1, n), RATIO(1, 0) over kappa = {kappa, kappa_h}.        */
+#define PFMP_KIND_GAUGE 0
+#define PFMP_KIND_DET 1
+#define PFMP_KIND_FILTER 2
+#define PFMP_KIND_FILTERCORR 3
+#define PFMP_KIND_RATIO 4
+#define PFMP_KIND_INV 5
+#define PFMP_MAX_TERMS 8
+#define PFMP_MAX_KAPPA 4
+/* term indices of the PF-MP action */
 #define PFMP_TERM_GAUGE 0
 #define PFMP_TERM_DET 1
 #define PFMP_TERM_POLY 2
 #define PFMP_TERM_POLYCORR 3
 #define PFMP_TERM_HASEN 4
 typedef struct pfmp_action pfmp_action;
+typedef struct {
+  int kind;        /* PFMP_KIND_*                                                       */
+  int a, b;        /* kappa indices: J_a / W_a, and K_b of RATIO                        */
+  int p1, p2;      /* filter orders (FILTER: Q = P_p2 / P_p1; FILTERCORR: order p2)     */
+} pfmp_term;
+typedef struct {
+  double beta, csw;
+  int nkappa;                         /* 1..PFMP_MAX_KAPPA                             */
+  double kappa[PFMP_MAX_KAPPA];       /* kappa[0]: the target operator                 */
+  int nterms;                         /* 1..PFMP_MAX_TERMS                             */
+  pfmp_term term[PFMP_MAX_TERMS];
+  double mu, nu;                      /* Chebyshev ellipse of every filter             */
+  double tol;                         /* relative residual of every solve              */
+  int max_iter;
+} pfmp_action_def;
 typedef struct {
   double beta, kappa, kappa_h, csw;  /* gauge coupling, target and Hasenbusch kappa, c_sw */
   int n;                             /* polynomial order (even)                          */
@@ -246,21 +299,47 @@ typedef struct {
 typedef struct {
   double H0, H1, dH;
   int accepted;
-  double S0[5], S1[5];   /* per term at the start and end (0 for terms not in the schedule) */
-  double plaquette;      /* after the accept/reject decision                               */
-  int64_t k_apply;       /* K and J applications outside CUDA-graph replays                */
-  int force_evals;
+  double S0[PFMP_MAX_TERMS], S1[PFMP_MAX_TERMS];  /* per term at start and end (0 if left out) */
+  double plaquette;        /* after the accept/reject decision                             */
+  int64_t k_apply;         /* K and J applications (every operator, solves included)       */
+  int force_evals;         /* term force evaluations                                        */
+  int64_t k_apply_term[PFMP_MAX_TERMS];  /* ... of them spent in each term's forces          */
+  int nforce[PFMP_MAX_TERMS];            /* force evaluations of each term                   */
+  double fmax[PFMP_MAX_TERMS];  /* max over the trajectory of max_links |F|, |F| = sqrt(sum_a f_a^2) */
+  double favg[PFMP_MAX_TERMS];  /* mean over the trajectory of the link average of |F|      */
 } pfmp_traj_info;
+/* Schemes compared in Sec. 3 (term lists; kappa[1], kappa[2] are the Hasenbusch kappas):
+ *   1PF      GAUGE, DET, FILTER(0; p2), FILTERCORR(0; p2)              (eq. 1poly on K)
+ *   2PF      GAUGE, DET, FILTER(0; p1), FILTER(0; p1, p2), FILTERCORR(0; p2)   (eq. 2poly)
+ *   1MP      GAUGE, DET, INV(1), RATIO(1, 0)                           (eq. hasenbusch)
+ *   2MP      GAUGE, DET, INV(1), RATIO(1, 2), RATIO(2, 0)
+ *   PF-MP    GAUGE, DET, FILTER(1; p2), FILTERCORR(1; p2), RATIO(1, 0) (eq. pfmp_action)
+ *   2PF-1MP  GAUGE, DET, FILTER(1; p1), FILTER(1; p1, p2), FILTERCORR(1; p2), RATIO(1, 0)
+ *   1PF-2MP  GAUGE, DET, FILTER(1; p2), FILTERCORR(1; p2), RATIO(1, 2), RATIO(2, 0)
+ * pfmp_action_scheme fills def->nterms and def->term and leaves the other fields.      */
+#define PFMP_SCHEME_1PF 0
+#define PFMP_SCHEME_2PF 1
+#define PFMP_SCHEME_1MP 2
+#define PFMP_SCHEME_2MP 3
+#define PFMP_SCHEME_PFMP 4
+#define PFMP_SCHEME_2PF1MP 5
+#define PFMP_SCHEME_1PF2MP 6
+int pfmp_action_scheme(int scheme, int p1, int p2, pfmp_action_def* def);
+/* PFMP_E_INVALID for out-of-range kinds, kappa indices or counts; PFMP_E_UNSUPPORTED for
+ * odd filter orders or orders that do not factorise.                                    */
+int pfmp_action_create_def(pfmp_ctx* ctx, const pfmp_action_def* def, pfmp_action** action);
 int pfmp_action_create(pfmp_ctx* ctx, const pfmp_action_params* prm, pfmp_action** action);
 int pfmp_action_destroy(pfmp_action* action);
+/* number of terms and of pseudofermions                                                 */
+int pfmp_action_counts(pfmp_action* action, int* nterms, int* npf);
 /* rebuild the clover blocks after pfmp_gauge_set                                      */
 int pfmp_action_refresh(pfmp_action* action);
-/* xi: three canonical spinors ([3][V][4][3] complex double; even sites used)          */
+/* xi: npf canonical spinors ([npf][V][4][3] complex double; even sites used)           */
 int pfmp_action_heatbath(pfmp_action* action, const double* xi, int where);
 int pfmp_action_get_phi(pfmp_action* action, int i, double* phi, int where);
 int pfmp_action_set_phi(pfmp_action* action, int i, const double* phi, int where);
-/* S[5] per term at the current gauge field (synchronises)                              */
-int pfmp_action_eval(pfmp_action* action, double S[5]);
+/* S[nterms] per term at the current gauge field (synchronises)                         */
+int pfmp_action_eval(pfmp_action* action, double* S);
 /* force of one term, canonical [V][4][8]                                               */
 int pfmp_action_force(pfmp_action* action, int term, double* F, int where);
 /* 2MN arrays of eq. 2MNSTS chained n times over tau: T and S of length 2n + 1          */
@@ -270,12 +349,13 @@ int pfmp_schedule_2mn(int n, double tau, double lambda, double* T, double* S);
  * S_out[nschemes][cap] and the merged length.                                          */
 int pfmp_schedule_merge(int nschemes, const int* len, const double* T, const double* S, int cap, double* T_out,
                         double* S_out, int* len_out);
-/* One trajectory: heatbath from xi, H0, the merged schedule (T[len], S[nlevels][len]),
- * each term t integrated on level term_level[t] (-1: term left out), H1, Metropolis
- * accept iff u < exp(-dH); a rejected trajectory restores the gauge field.  mom: initial
- * momenta, canonical [V][4][8].  Synchronises.                                          */
+/* One trajectory: heatbath from xi ([npf] canonical spinors), H0, the merged schedule
+ * (T[len], S[nlevels][len]), term t integrated on level term_level[t] (nterms entries;
+ * -1: term left out of H and of the MD), H1, Metropolis accept iff u < exp(-dH); a
+ * rejected trajectory restores the gauge field.  mom: initial momenta, canonical
+ * [V][4][8].  Synchronises.                                                             */
 int pfmp_trajectory(pfmp_action* action, int len, const double* T, int nlevels, const double* S,
-                    const int term_level[5], const double* mom, const double* xi, int where, double u,
+                    const int* term_level, const double* mom, const double* xi, int where, double u,
                     pfmp_traj_info* info);
 
 /* ---- batched solves ------------------------------------------------------------------

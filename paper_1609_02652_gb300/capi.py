@@ -54,13 +54,30 @@ class ActionParams(C.Structure):
                 ("n", C.c_int), ("mu", C.c_double), ("nu", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int)]
 
 
+PFMP_MAX_TERMS = 8
+PFMP_MAX_KAPPA = 4
+PFMP_KIND_GAUGE, PFMP_KIND_DET, PFMP_KIND_FILTER, PFMP_KIND_FILTERCORR, PFMP_KIND_RATIO, PFMP_KIND_INV = range(6)
+PFMP_TERM_GAUGE, PFMP_TERM_DET, PFMP_TERM_POLY, PFMP_TERM_POLYCORR, PFMP_TERM_HASEN = range(5)
+(PFMP_SCHEME_1PF, PFMP_SCHEME_2PF, PFMP_SCHEME_1MP, PFMP_SCHEME_2MP, PFMP_SCHEME_PFMP, PFMP_SCHEME_2PF1MP,
+ PFMP_SCHEME_1PF2MP) = range(7)
+
+
+class Term(C.Structure):
+    _fields_ = [("kind", C.c_int), ("a", C.c_int), ("b", C.c_int), ("p1", C.c_int), ("p2", C.c_int)]
+
+
+class ActionDef(C.Structure):
+    _fields_ = [("beta", C.c_double), ("csw", C.c_double), ("nkappa", C.c_int),
+                ("kappa", C.c_double * PFMP_MAX_KAPPA), ("nterms", C.c_int), ("term", Term * PFMP_MAX_TERMS),
+                ("mu", C.c_double), ("nu", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int)]
+
+
 class TrajInfo(C.Structure):
     _fields_ = [("H0", C.c_double), ("H1", C.c_double), ("dH", C.c_double), ("accepted", C.c_int),
-                ("S0", C.c_double * 5), ("S1", C.c_double * 5), ("plaquette", C.c_double),
-                ("k_apply", C.c_int64), ("force_evals", C.c_int)]
-
-
-PFMP_TERM_GAUGE, PFMP_TERM_DET, PFMP_TERM_POLY, PFMP_TERM_POLYCORR, PFMP_TERM_HASEN = range(5)
+                ("S0", C.c_double * PFMP_MAX_TERMS), ("S1", C.c_double * PFMP_MAX_TERMS),
+                ("plaquette", C.c_double), ("k_apply", C.c_int64), ("force_evals", C.c_int),
+                ("k_apply_term", C.c_int64 * PFMP_MAX_TERMS), ("nforce", C.c_int * PFMP_MAX_TERMS),
+                ("fmax", C.c_double * PFMP_MAX_TERMS), ("favg", C.c_double * PFMP_MAX_TERMS)]
 
 P = C.c_void_p
 I = C.c_int
@@ -107,6 +124,10 @@ SIGNATURES = {
     "pfmp_poly_roots": (I, [I, D, D, DP, DP, DP]),
     "pfmp_poly_apply": (I, [P, I, D, D, I, P, P]),
     "pfmp_action_create": (I, [P, C.POINTER(ActionParams), C.POINTER(P)]),
+    "pfmp_action_scheme": (I, [I, I, I, C.POINTER(ActionDef)]),
+    "pfmp_spectrum": (I, [P, I, P, DP, DP, DP, DP, C.POINTER(I)]),
+    "pfmp_action_create_def": (I, [P, C.POINTER(ActionDef), C.POINTER(P)]),
+    "pfmp_action_counts": (I, [P, C.POINTER(I), C.POINTER(I)]),
     "pfmp_action_destroy": (I, [P]),
     "pfmp_action_refresh": (I, [P]),
     "pfmp_action_heatbath": (I, [P, P, I]),
@@ -372,6 +393,33 @@ def pfmp_action_create(ctx, params):
     return h
 
 
+def pfmp_spectrum(op, nsteps, v0):
+    """Returns (lmin, lmax, alpha, beta) of nsteps Lanczos steps on K from v0."""
+    lo, hi, k = C.c_double(), C.c_double(), I()
+    a = np.zeros(nsteps)
+    b = np.zeros(nsteps)
+    check(lib().pfmp_spectrum(op, nsteps, _ptr(v0), C.byref(lo), C.byref(hi), a.ctypes.data_as(DP),
+                              b.ctypes.data_as(DP), C.byref(k)))
+    return lo.value, hi.value, a[:k.value].copy(), b[:k.value].copy()
+
+
+def pfmp_action_scheme(scheme, p1, p2, d):
+    check(lib().pfmp_action_scheme(scheme, p1, p2, C.byref(d)))
+    return d
+
+
+def pfmp_action_create_def(ctx, d):
+    h = P()
+    check(lib().pfmp_action_create_def(ctx, C.byref(d), C.byref(h)))
+    return h
+
+
+def pfmp_action_counts(a):
+    nt, npf = I(), I()
+    check(lib().pfmp_action_counts(a, C.byref(nt), C.byref(npf)))
+    return nt.value, npf.value
+
+
 def pfmp_action_destroy(a):
     check(lib().pfmp_action_destroy(a))
 
@@ -393,9 +441,9 @@ def pfmp_action_set_phi(a, i, phi, where=PFMP_HOST):
 
 
 def pfmp_action_eval(a):
-    S = (C.c_double * 5)()
+    S = (C.c_double * PFMP_MAX_TERMS)()
     check(lib().pfmp_action_eval(a, S))
-    return np.array(S[:])
+    return np.array(S[:pfmp_action_counts(a)[0]])
 
 
 def pfmp_action_force(a, term, out, where=PFMP_HOST):
@@ -424,7 +472,7 @@ def pfmp_schedule_merge(schemes, cap=4096):
 def pfmp_trajectory(a, T, S_levels, term_level, mom, xi, u, where=PFMP_HOST):
     T, pT = _dp(T)
     S, pS = _dp(np.asarray(S_levels).reshape(-1))
-    tl = (I * 5)(*term_level)
+    tl = (I * len(term_level))(*term_level)
     info = TrajInfo()
     check(lib().pfmp_trajectory(a, len(T), pT, np.asarray(S_levels).shape[0], pS, tl, _ptr(mom), _ptr(xi), where,
                                 float(u), C.byref(info)))

@@ -20,17 +20,21 @@ void spinor_pack_any(pfmp_ctx* c, void* dst, int prec, const double* src, int wh
 void spinor_unpack_any(pfmp_ctx* c, double* dst, int where, const void* src, int prec, int parity);
 void profile_begin(pfmp_ctx* c);
 pfmp_action* action_create(pfmp_ctx* c, const pfmp_action_params* prm);
+pfmp_action* action_create_def(pfmp_ctx* c, const pfmp_action_def* d);
+void action_scheme(int scheme, int p1, int p2, pfmp_action_def* d);
+int action_nterms(pfmp_action* A);
+int action_npf(pfmp_action* A);
 void action_destroy(pfmp_action* A);
-void action_heatbath(pfmp_action* A, const void* xi1, const void* xi2, const void* xi3);
-void action_eval(pfmp_action* A, double S[5]);
+void action_heatbath(pfmp_action* A, const void* const* xi);
+void action_eval(pfmp_action* A, double* S);
 void action_force_out(pfmp_action* A, int term, double* out, int where);
 void action_get_phi(pfmp_action* A, int i, double* out, int where);
 void action_set_phi(pfmp_action* A, int i, const double* in, int where);
 void action_refresh(pfmp_action* A);
 void schedule_2mn(int n, double tau, double lam, double* T, double* S);
 int schedule_merge(int ns, const int* len, const double* T, const double* S, int cap, double* Tout, double* Sout);
-void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int term_level[5],
-                const double* mom, int where, const void* const xi[3], double u, pfmp_traj_info* info);
+void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int* term_level,
+                const double* mom, int where, const void* const* xi, double u, pfmp_traj_info* info);
 pfmp_ctx* action_ctx(pfmp_action* A);
 pfmp_batch* batch_create(int nsys, pfmp_op* const* ops, const int* nrhs);
 void batch_destroy(pfmp_batch* B);
@@ -51,6 +55,8 @@ double nn_train(pfmp_nn* N, pfmp_op* op, int kind, int npairs, const void* const
 int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, double delta, void* x, const void* b,
                int* iters, int* outer, double* true_res, long* kapply, int* fallback_iters);
 void profile_end(pfmp_ctx* c, int cls, long* launches, double* ms, double* bytes);
+void spectrum(pfmp_op* op, int nsteps, const void* v0, double* lmin, double* lmax, double* alpha_out,
+              double* beta_out, int* steps);
 }  // namespace pfmp
 
 using namespace pfmp;
@@ -500,6 +506,29 @@ int pfmp_poly_apply(pfmp_op* op, int n, double mu, double nu, int which, void* o
   API_END
 }
 
+int pfmp_spectrum(pfmp_op* op, int nsteps, const void* v0, double* lmin, double* lmax, double* alpha, double* beta,
+                  int* steps) {
+  API_BEGIN
+  PFMP_REQUIRE(op && v0 && lmin && lmax && steps, PFMP_E_INVALID, "null argument");
+  PFMP_REQUIRE(nsteps >= 1 && nsteps <= 100000, PFMP_E_INVALID, "nsteps must be in [1, 100000]");
+  spectrum(op, nsteps, v0, lmin, lmax, alpha, beta, steps);
+  API_END
+}
+
+int pfmp_action_scheme(int scheme, int p1, int p2, pfmp_action_def* def) {
+  API_BEGIN
+  PFMP_REQUIRE(def, PFMP_E_INVALID, "null argument");
+  action_scheme(scheme, p1, p2, def);
+  API_END
+}
+
+int pfmp_action_create_def(pfmp_ctx* ctx, const pfmp_action_def* def, pfmp_action** out) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && def && out, PFMP_E_INVALID, "null argument");
+  *out = action_create_def(ctx, def);
+  API_END
+}
+
 int pfmp_action_create(pfmp_ctx* ctx, const pfmp_action_params* prm, pfmp_action** out) {
   API_BEGIN
   PFMP_REQUIRE(ctx && prm && out, PFMP_E_INVALID, "null argument");
@@ -513,6 +542,14 @@ int pfmp_action_destroy(pfmp_action* A) {
   API_END
 }
 
+int pfmp_action_counts(pfmp_action* A, int* nterms, int* npf) {
+  API_BEGIN
+  PFMP_REQUIRE(A && nterms && npf, PFMP_E_INVALID, "null argument");
+  *nterms = action_nterms(A);
+  *npf = action_npf(A);
+  API_END
+}
+
 int pfmp_action_refresh(pfmp_action* A) {
   API_BEGIN
   PFMP_REQUIRE(A, PFMP_E_INVALID, "null action");
@@ -520,25 +557,41 @@ int pfmp_action_refresh(pfmp_action* A) {
   API_END
 }
 
+namespace {
+// npf canonical host/device spinors -> temporary FP64 even device fields
+struct NoiseFields {
+  std::vector<double2*> d;
+  NoiseFields(pfmp_action* A, const double* xi, int where) {
+    pfmp_ctx* c = action_ctx(A);
+    const size_t n = (size_t)c->g.V * 24;
+    const int npf = action_npf(A);
+    try {
+      for (int i = 0; i < npf; ++i) {
+        d.push_back((double2*)dev_alloc(spinor_bytes(c->g, PFMP_F64)));
+        spinor_pack_any(c, d.back(), PFMP_F64, xi + i * n, where, 0);
+      }
+    } catch (...) {
+      release();
+      throw;
+    }
+  }
+  void release() {
+    for (auto p : d) dev_free(p);
+    d.clear();
+  }
+  ~NoiseFields() { release(); }
+  std::vector<const void*> ptrs() const { return std::vector<const void*>(d.begin(), d.end()); }
+};
+}  // namespace
+
 int pfmp_action_heatbath(pfmp_action* A, const double* xi, int where) {
   API_BEGIN
   PFMP_REQUIRE(A && xi, PFMP_E_INVALID, "null argument");
   check_where(where);
-  pfmp_ctx* c = action_ctx(A);
-  const size_t n = (size_t)c->g.V * 24;
-  std::vector<double2*> d(3, nullptr);
-  try {
-    for (int i = 0; i < 3; ++i) {
-      d[i] = (double2*)dev_alloc(spinor_bytes(c->g, PFMP_F64));
-      spinor_pack_any(c, d[i], PFMP_F64, xi + i * n, where, 0);
-    }
-    action_heatbath(A, d[0], d[1], d[2]);
-    PFMP_CUDA(cudaStreamSynchronize(c->stream));
-  } catch (...) {
-    for (auto p : d) dev_free(p);
-    throw;
-  }
-  for (auto p : d) dev_free(p);
+  NoiseFields nf(A, xi, where);
+  auto p = nf.ptrs();
+  action_heatbath(A, p.data());
+  PFMP_CUDA(cudaStreamSynchronize(action_ctx(A)->stream));
   API_END
 }
 
@@ -558,7 +611,7 @@ int pfmp_action_set_phi(pfmp_action* A, int i, const double* phi, int where) {
   API_END
 }
 
-int pfmp_action_eval(pfmp_action* A, double S[5]) {
+int pfmp_action_eval(pfmp_action* A, double* S) {
   API_BEGIN
   PFMP_REQUIRE(A && S, PFMP_E_INVALID, "null argument");
   action_eval(A, S);
@@ -567,7 +620,7 @@ int pfmp_action_eval(pfmp_action* A, double S[5]) {
 
 int pfmp_action_force(pfmp_action* A, int term, double* F, int where) {
   API_BEGIN
-  PFMP_REQUIRE(A && F && term >= 0 && term < 5, PFMP_E_INVALID, "bad argument");
+  PFMP_REQUIRE(A && F, PFMP_E_INVALID, "null argument");
   check_where(where);
   action_force_out(A, term, F, where);
   API_END
@@ -589,26 +642,14 @@ int pfmp_schedule_merge(int ns, const int* len, const double* T, const double* S
   API_END
 }
 
-int pfmp_trajectory(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int term_level[5],
+int pfmp_trajectory(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int* term_level,
                     const double* mom, const double* xi, int where, double u, pfmp_traj_info* info) {
   API_BEGIN
   PFMP_REQUIRE(A && T && S && term_level && mom && xi && info, PFMP_E_INVALID, "null argument");
   check_where(where);
-  pfmp_ctx* c = action_ctx(A);
-  const size_t n = (size_t)c->g.V * 24;
-  std::vector<double2*> d(3, nullptr);
-  try {
-    for (int i = 0; i < 3; ++i) {
-      d[i] = (double2*)dev_alloc(spinor_bytes(c->g, PFMP_F64));
-      spinor_pack_any(c, d[i], PFMP_F64, xi + i * n, where, 0);
-    }
-    const void* xs[3] = {d[0], d[1], d[2]};
-    trajectory(A, len, T, nlev, S, term_level, mom, where, xs, u, info);
-  } catch (...) {
-    for (auto p : d) dev_free(p);
-    throw;
-  }
-  for (auto p : d) dev_free(p);
+  NoiseFields nf(A, xi, where);
+  auto p = nf.ptrs();
+  trajectory(A, len, T, nlev, S, term_level, mom, where, p.data(), u, info);
   API_END
 }
 

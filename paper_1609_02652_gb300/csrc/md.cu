@@ -1,23 +1,30 @@
-// PF-MP action, heatbath, forces and the molecular-dynamics trajectory.
+// Actions, heatbath, forces and the molecular-dynamics trajectory.
 //
-// Action (Sec. 2.5 eq. pfmp_action, with the Wilson gauge action and the even-odd clover
-// determinant):
-//   S = S_G + S_det + phi1^dag P(J) phi1 + phi2^dag [J P(J)]^{-1} phi2 + phi3^dag W K^{-1} W^dag phi3
-//   S_G = beta sum_{x, mu<nu} (1 - Re tr U_{mu nu}/3),  S_det = -2 sum_{x odd} log det A(x),
-//   K = M-hat^dag M-hat at kappa, J = W^dag W with W = M-hat at kappa' (same c_sw).
-// Heatbath from Gaussian xi_i (density exp(-xi^dag xi)), so that S_i(phi_i) = xi_i^dag xi_i:
-//   phi1 = R(J)^{-1} xi1,  phi2 = R(J)^dag W^dag xi2,  phi3 = W J^{-1} M-hat^dag xi3,
-//   R(J) = sqrt(a_n) prod_{Im z_k<0} (J - z_k)  (P = R^dag R).
+// An action is a list of terms over hopping parameters kappa[0..] sharing c_sw (Sec. 2.2
+// eq. hasenbusch, Sec. 2.3 eqs. 1poly/2poly, Sec. 2.5 eq. pfmp_action, Sec. 3.6):
+//   GAUGE       S_G = beta sum_{x, mu<nu} (1 - Re tr U_{mu nu}/3)
+//   DET         S_det = -2 sum_{x odd} log det A(x) at kappa[a]
+//   FILTER      phi^dag Q(J_a) phi, Q = P_p2 / P_p1 = c prod_k (J_a - q_k)  (App. A factorisation)
+//   FILTERCORR  phi^dag [J_a P_p2(J_a)]^{-1} phi = sum_i r_i phi^dag (J_a - z_i)^{-1} phi, z_{p2+1} = 0
+//   RATIO       phi^dag W_a K_b^{-1} W_a^dag phi    (the Hermitian form of "J_a K_b^{-1}")
+//   INV         phi^dag J_a^{-1} phi
+// with K_b = M_b^dag M_b, J_a = W_a^dag W_a, M_b and W_a the even-odd M-hat at kappa[b], kappa[a].
+// Heatbath from Gaussian xi (density exp(-xi^dag xi)), so that S_i(phi_i) = xi_i^dag xi_i:
+//   FILTER phi = c^{-1/2} sum_k s_k (J_a - qh_k)^{-1} xi  (qh: roots with Im < 0, s_k the
+//   residues of 1/prod(z - qh_k)),  FILTERCORR phi = R_p2(J_a)^dag W_a^dag xi,
+//   RATIO phi = W_a J_a^{-1} M_b^dag xi,  INV phi = W_a^dag xi.
 // Forces (App. C), as dS/d omega_a:
-//   poly      F1 = sum_i Re eta_i^dag dJ chi_i, chi_i = a_n prod_{j>i}(J - z_j) phi1,
-//             eta_i = prod_{j<i}(J - z_j^*) phi1  (eq. force_poly; 2n - 2 J products)
-//   polycorr  F2 = -sum_{i<=n+1} Re eta-bar_i^dag dJ chi-bar_i, chi-bar_i = r_i (J - z_i)^{-1} phi2,
-//             eta-bar_i = (J - z_i^*)^{-1} phi2, z_{n+1} = 0  (eq. force_polycorr, one multi-shift solve)
-//   hasen     F3 = 2 Re chi^dag dW^dag phi3 - chi^dag dK chi, chi = K^{-1} W^dag phi3
-//   det       dS_det = 2 kappa c_sw sum_x sum_{mu<nu} tr(dF_{mu nu} G), G = sum sigma A^{-1}
-//   gauge     (beta/3) Im tr(T_a U S)
+//   FILTER      sum_i Re eta_i^dag dJ chi_i, chi_i = c prod_{j>i}(J - q_j) phi,
+//               eta_i = prod_{j<i}(J - q_j^*) phi  (eq. force_poly; 2q - 2 J products)
+//   FILTERCORR  -sum_i Re eta-bar_i^dag dJ chi-bar_i, chi-bar_i = r_i (J - z_i)^{-1} phi,
+//               eta-bar_i = (J - z_i^*)^{-1} phi  (eq. force_polycorr, one multi-shift solve)
+//   RATIO       2 Re chi^dag dW_a^dag phi - chi^dag dK_b chi, chi = K_b^{-1} W_a^dag phi
+//   INV         -chi^dag dJ_a chi, chi = J_a^{-1} phi
+//   DET         2 kappa c_sw sum_x sum_{mu<nu} tr(dF_{mu nu} G), G = sum sigma A^{-1}
+//   GAUGE       (beta/3) Im tr(T_a U S)
 // Trajectory (Sec. 2.1, App. B): for each step of the merged schedule T-hat then the S-hat
 // of every level with a non-zero step; Metropolis accept iff u < exp(-dH).
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -91,22 +98,61 @@ static int grid_for(long n) {
   return (int)(b < 152 * 8 ? b : 152 * 8);
 }
 
+// per-link force norm |F_mu(x)| = sqrt(sum_a f_a^2) (F: [2][4][8][Vh]): out[0] = sum over
+// links (deterministic grid sum), *maxbits = max over links (the bit patterns of
+// non-negative doubles order like the values, so an integer atomicMax is exact and
+// independent of scheduling); *maxbits must be zero on entry
+__global__ void k_force_norm(const double* __restrict__ F, int Vh, ReduceBuf rb, double* out,
+                             unsigned long long* maxbits) {
+  double v[1] = {0.0};
+  double mx = 0.0;
+  const long nl = 8L * Vh;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nl; i += (long)gridDim.x * blockDim.x) {
+    const long pm = i / Vh, cb = i - pm * Vh;
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const double f = F[(size_t)(pm * 8 + a) * Vh + cb];
+      s += f * f;
+    }
+    const double n = sqrt(s);
+    v[0] += n;
+    mx = fmax(mx, n);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxbits, (unsigned long long)__double_as_longlong(mx));
+  double t[1];
+  if (grid_sum<1>(v, rb, t)) out[0] = t[0];
+}
+
 }  // namespace pfmp
 
 using namespace pfmp;
 
+namespace {
+struct Term {
+  pfmp_term d{};
+  int pf = -1;                   // pseudofermion index (fermion terms)
+  std::vector<cd> q;             // FILTER: roots of Q, Q = c prod (z - q_k)
+  double c = 0;
+  std::vector<cd> qh, sh;        // FILTER: roots with Im < 0, residues of 1/prod(z - qh_k)
+  std::vector<cd> sig, r;        // FILTERCORR: shifts -z_i (z_{p+1} = 0), residues of 1/(z P(z))
+  std::vector<int> conj_of;      // FILTERCORR: index of the conjugate shift
+  std::vector<cd> zh;            // FILTERCORR: roots of P_p with Im < 0 (heatbath R)
+  double a_p = 0;
+};
+bool is_fermion(int kind) {
+  return kind == PFMP_KIND_FILTER || kind == PFMP_KIND_FILTERCORR || kind == PFMP_KIND_RATIO || kind == PFMP_KIND_INV;
+}
+}  // namespace
+
 struct pfmp_action {
   pfmp_ctx* ctx = nullptr;
-  pfmp_action_params prm{};
-  pfmp_op* M = nullptr;  // kappa
-  pfmp_op* W = nullptr;  // kappa'
-  std::vector<cd> z;     // roots z_1..z_n
-  double a_n = 0;
-  std::vector<cd> sig;   // multi-shift shifts -z_i, i = 1..n+1 (z_{n+1} = 0)
-  std::vector<cd> r;     // residues of 1/(z P(z))
-  std::vector<int> conj_of;
-  std::vector<cd> zh, sh;  // half roots (Im < 0) and residues of 1/prod(z - zh)
-  double2* phi[3] = {nullptr, nullptr, nullptr};
+  pfmp_action_def def{};
+  std::vector<pfmp_op*> ops;  // one per kappa
+  std::vector<Term> t;
+  std::vector<double2*> phi;  // one per fermion term
   double* F = nullptr;    // [2][4][8][Vh]
   double* Hc = nullptr;   // [2][6][8][Vh]
   double* mom = nullptr;  // [2][4][8][Vh]
@@ -114,7 +160,6 @@ struct pfmp_action {
   std::vector<double2*> ev;  // even FP64 temporaries
   std::vector<double2*> xs;  // multi-shift solutions
   double2* od[2] = {nullptr, nullptr};  // odd FP64 temporaries
-  long long kapply0 = 0;
   int force_evals = 0;
 };
 
@@ -140,7 +185,7 @@ void cg64(pfmp_action* A, pfmp_op* op, void* x, const void* b) {
   int it, rel;
   double res;
   long kap;
-  int st = solve(op, PFMP_SOLVER_CG64, A->prm.tol, A->prm.max_iter, 0.1, 8, x, b, &it, &rel, &res, &kap);
+  int st = solve(op, PFMP_SOLVER_CG64, A->def.tol, A->def.max_iter, 0.1, 8, x, b, &it, &rel, &res, &kap);
   PFMP_REQUIRE(st == PFMP_OK, st, "CG inside the action did not converge");
 }
 
@@ -151,7 +196,7 @@ void multishift(pfmp_action* A, pfmp_op* op, const std::vector<cd>& sig, const v
   int it;
   double res;
   long kap;
-  int st = solve_multishift(op, (int)sig.size(), sig.data(), x.data(), b, A->prm.tol, A->prm.max_iter, 8, &it, &res,
+  int st = solve_multishift(op, (int)sig.size(), sig.data(), x.data(), b, A->def.tol, A->def.max_iter, 8, &it, &res,
                             &kap, false);
   PFMP_REQUIRE(st == PFMP_OK, st, "multi-shift CG inside the action did not converge");
 }
@@ -167,8 +212,74 @@ void deriv_K(pfmp_action* A, pfmp_op* op, const void* eta, const void* chi, doub
 }
 
 void refresh_ops(pfmp_action* A) {
-  clover_build(A->M);
-  clover_build(A->W);
+  for (auto op : A->ops) clover_build(op);
+}
+
+long long kapply_total(pfmp_action* A) {
+  long long k = 0;
+  for (auto op : A->ops) k += op->kapply;
+  return k;
+}
+
+// residues of 1 / prod_k (z - w_k) over the list w
+std::vector<cd> product_residues(const std::vector<cd>& w) {
+  std::vector<cd> s;
+  for (size_t i = 0; i < w.size(); ++i) {
+    cd prod = 1.0;
+    for (size_t j = 0; j < w.size(); ++j)
+      if (j != i) prod *= (w[i] - w[j]);
+    s.push_back(1.0 / prod);
+  }
+  return s;
+}
+
+// roots and normalisation of Q = P_p2 / P_p1 (App. A: with (p1 + 1) | (p2 + 1) the roots
+// of P_p1 are those of P_p2 with index k = j (p2 + 1)/(p1 + 1); Q keeps the others and
+// c = a_p2 / a_p1).  p1 = 0: Q = P_p2.
+void filter_roots(int p1, int p2, double mu, double nu, std::vector<cd>& q, double& c) {
+  PFMP_REQUIRE(p2 >= 2 && p2 % 2 == 0 && p1 >= 0 && p1 % 2 == 0, PFMP_E_UNSUPPORTED, "filter orders must be even");
+  std::vector<cd> z = cheb_roots(p2, mu, nu);
+  q.clear();
+  if (p1 == 0) {
+    q = z;
+    c = cheb_norm(p2, mu, nu);
+    return;
+  }
+  PFMP_REQUIRE(p2 > p1 && (p2 + 1) % (p1 + 1) == 0, PFMP_E_UNSUPPORTED,
+               "P_p1 divides P_p2 only when (p1 + 1) divides (p2 + 1)");
+  const int m = (p2 + 1) / (p1 + 1);
+  for (int k = 1; k <= p2; ++k)
+    if (k % m) q.push_back(z[k - 1]);
+  c = cheb_norm(p2, mu, nu) / cheb_norm(p1, mu, nu);
+}
+
+void setup_term(Term& T, const pfmp_action_def& d) {
+  const pfmp_term& x = T.d;
+  if (x.kind == PFMP_KIND_FILTER) {
+    filter_roots(x.p1, x.p2, d.mu, d.nu, T.q, T.c);
+    for (auto qk : T.q)
+      if (qk.imag() < 0) T.qh.push_back(qk);
+    T.sh = product_residues(T.qh);
+  } else if (x.kind == PFMP_KIND_FILTERCORR) {
+    PFMP_REQUIRE(x.p2 >= 2 && x.p2 % 2 == 0, PFMP_E_UNSUPPORTED, "filter orders must be even");
+    std::vector<cd> z = cheb_roots(x.p2, d.mu, d.nu);
+    T.a_p = cheb_norm(x.p2, d.mu, d.nu);
+    for (auto zk : z)
+      if (zk.imag() < 0) T.zh.push_back(zk);
+    z.push_back(0.0);
+    const int n = x.p2;
+    for (int i = 0; i <= n; ++i) {
+      cd prod = T.a_p;
+      for (int j = 0; j <= n; ++j)
+        if (j != i) prod *= (z[i] - z[j]);
+      T.r.push_back(1.0 / prod);
+      T.sig.push_back(-z[i]);
+      int best = 0;
+      for (int j = 0; j <= n; ++j)
+        if (std::abs(z[j] - std::conj(z[i])) < std::abs(z[best] - std::conj(z[i]))) best = j;
+      T.conj_of.push_back(best);
+    }
+  }
 }
 
 }  // namespace
@@ -186,45 +297,81 @@ void action_destroy(pfmp_action* A) {
   for (auto p : A->ev) dev_free(p);
   for (auto p : A->xs) dev_free(p);
   for (auto p : A->od) dev_free(p);
-  op_delete(A->M);
-  op_delete(A->W);
+  for (auto op : A->ops) op_delete(op);
   delete A;
 }
 
-pfmp_action* action_create(pfmp_ctx* c, const pfmp_action_params* prm) {
-  PFMP_REQUIRE(prm->n >= 2 && prm->n % 2 == 0, PFMP_E_UNSUPPORTED, "polynomial order must be even and >= 2");
-  PFMP_REQUIRE(prm->mu >= prm->nu && prm->nu > 0, PFMP_E_INVALID, "need mu >= nu > 0");
-  PFMP_REQUIRE(prm->tol > 0 && prm->max_iter > 0, PFMP_E_INVALID, "bad solver tolerance / iteration cap");
+void action_scheme(int scheme, int p1, int p2, pfmp_action_def* d) {
+  auto T = [](int kind, int a, int b, int q1, int q2) { return pfmp_term{kind, a, b, q1, q2}; };
+  std::vector<pfmp_term> v = {T(PFMP_KIND_GAUGE, 0, 0, 0, 0), T(PFMP_KIND_DET, 0, 0, 0, 0)};
+  switch (scheme) {
+    case PFMP_SCHEME_1PF:
+      v.push_back(T(PFMP_KIND_FILTER, 0, 0, 0, p2));
+      v.push_back(T(PFMP_KIND_FILTERCORR, 0, 0, 0, p2));
+      break;
+    case PFMP_SCHEME_2PF:
+      v.push_back(T(PFMP_KIND_FILTER, 0, 0, 0, p1));
+      v.push_back(T(PFMP_KIND_FILTER, 0, 0, p1, p2));
+      v.push_back(T(PFMP_KIND_FILTERCORR, 0, 0, 0, p2));
+      break;
+    case PFMP_SCHEME_1MP:
+      v.push_back(T(PFMP_KIND_INV, 1, 0, 0, 0));
+      v.push_back(T(PFMP_KIND_RATIO, 1, 0, 0, 0));
+      break;
+    case PFMP_SCHEME_2MP:
+      v.push_back(T(PFMP_KIND_INV, 1, 0, 0, 0));
+      v.push_back(T(PFMP_KIND_RATIO, 1, 2, 0, 0));
+      v.push_back(T(PFMP_KIND_RATIO, 2, 0, 0, 0));
+      break;
+    case PFMP_SCHEME_PFMP:
+      v.push_back(T(PFMP_KIND_FILTER, 1, 0, 0, p2));
+      v.push_back(T(PFMP_KIND_FILTERCORR, 1, 0, 0, p2));
+      v.push_back(T(PFMP_KIND_RATIO, 1, 0, 0, 0));
+      break;
+    case PFMP_SCHEME_2PF1MP:
+      v.push_back(T(PFMP_KIND_FILTER, 1, 0, 0, p1));
+      v.push_back(T(PFMP_KIND_FILTER, 1, 0, p1, p2));
+      v.push_back(T(PFMP_KIND_FILTERCORR, 1, 0, 0, p2));
+      v.push_back(T(PFMP_KIND_RATIO, 1, 0, 0, 0));
+      break;
+    case PFMP_SCHEME_1PF2MP:
+      v.push_back(T(PFMP_KIND_FILTER, 1, 0, 0, p2));
+      v.push_back(T(PFMP_KIND_FILTERCORR, 1, 0, 0, p2));
+      v.push_back(T(PFMP_KIND_RATIO, 1, 2, 0, 0));
+      v.push_back(T(PFMP_KIND_RATIO, 2, 0, 0, 0));
+      break;
+    default:
+      PFMP_REQUIRE(false, PFMP_E_INVALID, "unknown scheme");
+  }
+  d->nterms = (int)v.size();
+  for (size_t i = 0; i < v.size(); ++i) d->term[i] = v[i];
+}
+
+pfmp_action* action_create_def(pfmp_ctx* c, const pfmp_action_def* d) {
+  PFMP_REQUIRE(d->nkappa >= 1 && d->nkappa <= PFMP_MAX_KAPPA, PFMP_E_INVALID, "nkappa out of range");
+  PFMP_REQUIRE(d->nterms >= 1 && d->nterms <= PFMP_MAX_TERMS, PFMP_E_INVALID, "nterms out of range");
+  PFMP_REQUIRE(d->mu >= d->nu && d->nu > 0, PFMP_E_INVALID, "need mu >= nu > 0");
+  PFMP_REQUIRE(d->tol > 0 && d->max_iter > 0, PFMP_E_INVALID, "bad solver tolerance / iteration cap");
+  for (int i = 0; i < d->nkappa; ++i) PFMP_REQUIRE(d->kappa[i] > 0, PFMP_E_INVALID, "kappa must be positive");
+  for (int i = 0; i < d->nterms; ++i) {
+    const pfmp_term& x = d->term[i];
+    PFMP_REQUIRE(x.kind >= PFMP_KIND_GAUGE && x.kind <= PFMP_KIND_INV, PFMP_E_INVALID, "unknown term kind");
+    PFMP_REQUIRE(x.a >= 0 && x.a < d->nkappa, PFMP_E_INVALID, "term kappa index a out of range");
+    PFMP_REQUIRE(x.kind != PFMP_KIND_RATIO || (x.b >= 0 && x.b < d->nkappa), PFMP_E_INVALID,
+                 "term kappa index b out of range");
+  }
   pfmp_action* A = new pfmp_action();
   A->ctx = c;
-  A->prm = *prm;
+  A->def = *d;
   try {
-    A->M = op_new(c, prm->kappa, prm->csw);
-    A->W = op_new(c, prm->kappa_h, prm->csw);
-    const int n = prm->n;
-    A->z = cheb_roots(n, prm->mu, prm->nu);
-    A->a_n = cheb_norm(n, prm->mu, prm->nu);
-    std::vector<cd> zz = A->z;
-    zz.push_back(0.0);
-    for (int i = 0; i <= n; ++i) {
-      cd prod = A->a_n;
-      for (int j = 0; j <= n; ++j)
-        if (j != i) prod *= (zz[i] - zz[j]);
-      A->r.push_back(1.0 / prod);
-      A->sig.push_back(-zz[i]);
-      int best = 0;
-      for (int j = 0; j <= n; ++j)
-        if (std::abs(zz[j] - std::conj(zz[i])) < std::abs(zz[best] - std::conj(zz[i]))) best = j;
-      A->conj_of.push_back(best);
+    for (int i = 0; i < d->nterms; ++i) {
+      Term T;
+      T.d = d->term[i];
+      setup_term(T, *d);
+      if (is_fermion(T.d.kind)) T.pf = (int)A->phi.size(), A->phi.push_back(nullptr);
+      A->t.push_back(T);
     }
-    for (auto zk : A->z)
-      if (zk.imag() < 0) A->zh.push_back(zk);
-    for (size_t i = 0; i < A->zh.size(); ++i) {
-      cd prod = 1.0;
-      for (size_t j = 0; j < A->zh.size(); ++j)
-        if (j != i) prod *= (A->zh[i] - A->zh[j]);
-      A->sh.push_back(1.0 / prod);
-    }
+    for (int i = 0; i < d->nkappa; ++i) A->ops.push_back(op_new(c, d->kappa[i], d->csw));
     const Geom& g = c->g;
     for (auto& p : A->phi) p = (double2*)dev_alloc(spb(A));
     A->F = (double*)dev_alloc((size_t)g.Vh * 64 * sizeof(double));
@@ -240,94 +387,148 @@ pfmp_action* action_create(pfmp_ctx* c, const pfmp_action_params* prm) {
   return A;
 }
 
-// phi_i from the noise xi_i (even FP64 device fields)
-void action_heatbath(pfmp_action* A, const void* xi1, const void* xi2, const void* xi3) {
-  pfmp_ctx* c = A->ctx;
-  // phi1 = a_n^{-1/2} sum_k s_k (J - zh_k)^{-1} xi1
-  std::vector<cd> sig;
-  for (auto zk : A->zh) sig.push_back(-zk);
-  multishift(A, A->W, sig, xi1);
-  blas_zero(c, PFMP_F64, A->phi[0]);
-  for (size_t k = 0; k < A->zh.size(); ++k) caxpby(c, A->sh[k] / std::sqrt(A->a_n), A->xs[k], 1.0, A->phi[0]);
-  // phi2 = R(J)^dag W^dag xi2
-  mhat(A->W, PFMP_F64, E(A, 0), xi2, true, nullptr, nullptr);
-  std::vector<cd> zc;
-  for (auto zk : A->zh) zc.push_back(std::conj(zk));
-  poly_product(A->W, zc, std::sqrt(A->a_n), A->phi[1], E(A, 0));
-  // phi3 = W J^{-1} M-hat^dag xi3
-  mhat(A->M, PFMP_F64, E(A, 0), xi3, true, nullptr, nullptr);
-  cg64(A, A->W, E(A, 1), E(A, 0));
-  mhat(A->W, PFMP_F64, A->phi[2], E(A, 1), false, nullptr, nullptr);
+pfmp_action* action_create(pfmp_ctx* c, const pfmp_action_params* prm) {
+  PFMP_REQUIRE(prm->n >= 2 && prm->n % 2 == 0, PFMP_E_UNSUPPORTED, "polynomial order must be even and >= 2");
+  pfmp_action_def d{};
+  d.beta = prm->beta;
+  d.csw = prm->csw;
+  d.nkappa = 2;
+  d.kappa[0] = prm->kappa;
+  d.kappa[1] = prm->kappa_h;
+  d.mu = prm->mu;
+  d.nu = prm->nu;
+  d.tol = prm->tol;
+  d.max_iter = prm->max_iter;
+  action_scheme(PFMP_SCHEME_PFMP, 0, prm->n, &d);
+  return action_create_def(c, &d);
 }
 
-void action_eval(pfmp_action* A, double S[5]) {
+int action_nterms(pfmp_action* A) { return (int)A->t.size(); }
+int action_npf(pfmp_action* A) { return (int)A->phi.size(); }
+
+// phi_i from the noise xi_i (even FP64 device fields, one per fermion term)
+void action_heatbath(pfmp_action* A, const void* const* xi) {
   pfmp_ctx* c = A->ctx;
-  S[PFMP_TERM_GAUGE] = A->prm.beta * 6.0 * c->g.V * (1.0 - plaquette(c));
-  S[PFMP_TERM_DET] = A->prm.csw != 0.0 ? -2.0 * A->M->logdet_oo : 0.0;
-  // S1 = phi1^dag P(J) phi1
-  poly_product(A->W, A->z, A->a_n, E(A, 0), A->phi[0]);
-  S[PFMP_TERM_POLY] = cdot(c, A->phi[0], E(A, 0)).real();
-  // S2 = sum_i r_i phi2^dag (J - z_i)^{-1} phi2
-  multishift(A, A->W, A->sig, A->phi[1]);
-  cd s2 = 0.0;
-  for (size_t i = 0; i < A->sig.size(); ++i) s2 += A->r[i] * cdot(c, A->phi[1], A->xs[i]);
-  S[PFMP_TERM_POLYCORR] = s2.real();
-  // S3 = w^dag K^{-1} w, w = W^dag phi3
-  mhat(A->W, PFMP_F64, E(A, 0), A->phi[2], true, nullptr, nullptr);
-  cg64(A, A->M, E(A, 1), E(A, 0));
-  S[PFMP_TERM_HASEN] = cdot(c, E(A, 0), E(A, 1)).real();
+  for (auto& T : A->t) {
+    if (T.pf < 0) continue;
+    pfmp_op* W = A->ops[T.d.a];
+    void* phi = A->phi[T.pf];
+    const void* x = xi[T.pf];
+    if (T.d.kind == PFMP_KIND_FILTER) {
+      // phi = c^{-1/2} sum_k s_k (J - qh_k)^{-1} xi
+      std::vector<cd> sig;
+      for (auto qk : T.qh) sig.push_back(-qk);
+      multishift(A, W, sig, x);
+      blas_zero(c, PFMP_F64, phi);
+      for (size_t k = 0; k < T.qh.size(); ++k) caxpby(c, T.sh[k] / std::sqrt(T.c), A->xs[k], 1.0, phi);
+    } else if (T.d.kind == PFMP_KIND_FILTERCORR) {
+      // phi = R(J)^dag W^dag xi
+      mhat(W, PFMP_F64, E(A, 0), x, true, nullptr, nullptr);
+      std::vector<cd> zc;
+      for (auto zk : T.zh) zc.push_back(std::conj(zk));
+      poly_product(W, zc, std::sqrt(T.a_p), phi, E(A, 0));
+    } else if (T.d.kind == PFMP_KIND_RATIO) {
+      // phi = W_a J_a^{-1} M_b^dag xi
+      mhat(A->ops[T.d.b], PFMP_F64, E(A, 0), x, true, nullptr, nullptr);
+      cg64(A, W, E(A, 1), E(A, 0));
+      mhat(W, PFMP_F64, phi, E(A, 1), false, nullptr, nullptr);
+    } else {  // INV: phi = W^dag xi
+      mhat(W, PFMP_F64, phi, x, true, nullptr, nullptr);
+    }
+  }
 }
 
-// F += dS_term/d omega (F must be zeroed by the caller for a fresh force)
-void action_force(pfmp_action* A, int term) {
+double action_term(pfmp_action* A, int i) {
+  pfmp_ctx* c = A->ctx;
+  Term& T = A->t[i];
+  pfmp_op* W = A->ops[T.d.a];
+  switch (T.d.kind) {
+    case PFMP_KIND_GAUGE:
+      return A->def.beta * 6.0 * c->g.V * (1.0 - plaquette(c));
+    case PFMP_KIND_DET:
+      return A->def.csw != 0.0 ? -2.0 * W->logdet_oo : 0.0;
+    case PFMP_KIND_FILTER: {
+      poly_product(W, T.q, T.c, E(A, 0), A->phi[T.pf]);
+      return cdot(c, A->phi[T.pf], E(A, 0)).real();
+    }
+    case PFMP_KIND_FILTERCORR: {
+      multishift(A, W, T.sig, A->phi[T.pf]);
+      cd s = 0.0;
+      for (size_t k = 0; k < T.sig.size(); ++k) s += T.r[k] * cdot(c, A->phi[T.pf], A->xs[k]);
+      return s.real();
+    }
+    case PFMP_KIND_RATIO: {
+      mhat(W, PFMP_F64, E(A, 0), A->phi[T.pf], true, nullptr, nullptr);
+      cg64(A, A->ops[T.d.b], E(A, 1), E(A, 0));
+      return cdot(c, E(A, 0), E(A, 1)).real();
+    }
+    default: {  // INV
+      cg64(A, W, E(A, 1), A->phi[T.pf]);
+      return cdot(c, A->phi[T.pf], E(A, 1)).real();
+    }
+  }
+}
+
+void action_eval(pfmp_action* A, double* S) {
+  for (int i = 0; i < (int)A->t.size(); ++i) S[i] = action_term(A, i);
+}
+
+// F += dS_i/d omega (F must be zeroed by the caller for a fresh force)
+void action_force(pfmp_action* A, int i) {
   pfmp_ctx* c = A->ctx;
   const Geom& g = c->g;
+  Term& T = A->t[i];
+  pfmp_op* W = A->ops[T.d.a];
   A->force_evals++;
-  if (term == PFMP_TERM_GAUGE) {
-    gauge_force(c, A->F, A->prm.beta);
+  if (T.d.kind == PFMP_KIND_GAUGE) {
+    gauge_force(c, A->F, A->def.beta);
     return;
   }
+  const bool clover = A->def.csw != 0.0;
+  if (T.d.kind == PFMP_KIND_DET && !clover) return;
   PFMP_CUDA(cudaMemsetAsync(A->Hc, 0, (size_t)g.Vh * 96 * sizeof(double), c->stream));
-  bool clover = A->prm.csw != 0.0;
-  if (term == PFMP_TERM_DET) {
-    if (!clover) return;
-    clover_insert_det(A->M, A->Hc, 2.0 * A->M->kappa * A->M->csw);
-  } else if (term == PFMP_TERM_POLY) {
-    const int n = A->prm.n;
-    // chi_i, i = n-1 .. 0 (0-based): chi[n-1] = a_n phi1, chi[i] = (J - z_{i+1}) chi[i+1]
-    while ((int)A->xs.size() < n) A->xs.push_back((double2*)dev_alloc(spb(A)));
-    caxpby(c, A->a_n, A->phi[0], 0.0, A->xs[n - 1]);
-    for (int i = n - 2; i >= 0; --i) {
-      kop(A->W, PFMP_F64, A->xs[i], A->xs[i + 1], nullptr, nullptr);
-      caxpby(c, -A->z[i + 1], A->xs[i + 1], 1.0, A->xs[i]);
+  void* phi = T.pf >= 0 ? A->phi[T.pf] : nullptr;
+  if (T.d.kind == PFMP_KIND_DET) {
+    clover_insert_det(W, A->Hc, 2.0 * W->kappa * W->csw);
+  } else if (T.d.kind == PFMP_KIND_FILTER) {
+    const int m = (int)T.q.size();
+    // chi_i, i = m-1 .. 0 (0-based): chi[m-1] = c phi, chi[i] = (J - q_{i+1}) chi[i+1]
+    while ((int)A->xs.size() < m) A->xs.push_back((double2*)dev_alloc(spb(A)));
+    caxpby(c, T.c, phi, 0.0, A->xs[m - 1]);
+    for (int k = m - 2; k >= 0; --k) {
+      kop(W, PFMP_F64, A->xs[k], A->xs[k + 1], nullptr, nullptr);
+      caxpby(c, -T.q[k + 1], A->xs[k + 1], 1.0, A->xs[k]);
     }
-    // eta_0 = phi1, eta_i = (J - z_{i-1}^*) eta_{i-1}
+    // eta_0 = phi, eta_i = (J - q_{i-1}^*) eta_{i-1}
     void* eta = E(A, 2);
     void* tmp = E(A, 3);
-    PFMP_CUDA(cudaMemcpyAsync(eta, A->phi[0], spb(A), cudaMemcpyDeviceToDevice, c->stream));
-    for (int i = 0; i < n; ++i) {
-      if (i > 0) {
-        kop(A->W, PFMP_F64, tmp, eta, nullptr, nullptr);
-        caxpby(c, 1.0, tmp, -std::conj(A->z[i - 1]), eta);
+    PFMP_CUDA(cudaMemcpyAsync(eta, phi, spb(A), cudaMemcpyDeviceToDevice, c->stream));
+    for (int k = 0; k < m; ++k) {
+      if (k > 0) {
+        kop(W, PFMP_F64, tmp, eta, nullptr, nullptr);
+        caxpby(c, 1.0, tmp, -std::conj(T.q[k - 1]), eta);
       }
-      deriv_K(A, A->W, eta, A->xs[i], 1.0);
+      deriv_K(A, W, eta, A->xs[k], 1.0);
     }
-  } else if (term == PFMP_TERM_POLYCORR) {
-    multishift(A, A->W, A->sig, A->phi[1]);
+  } else if (T.d.kind == PFMP_KIND_FILTERCORR) {
+    multishift(A, W, T.sig, phi);
     void* chib = E(A, 2);
-    for (size_t i = 0; i < A->sig.size(); ++i) {
-      caxpby(c, A->r[i], A->xs[i], 0.0, chib);
-      deriv_K(A, A->W, A->xs[A->conj_of[i]], chib, -1.0);
+    for (size_t k = 0; k < T.sig.size(); ++k) {
+      caxpby(c, T.r[k], A->xs[k], 0.0, chib);
+      deriv_K(A, W, A->xs[T.conj_of[k]], chib, -1.0);
     }
-  } else if (term == PFMP_TERM_HASEN) {
-    mhat(A->W, PFMP_F64, E(A, 0), A->phi[2], true, nullptr, nullptr);
+  } else if (T.d.kind == PFMP_KIND_RATIO) {
+    pfmp_op* Mb = A->ops[T.d.b];
+    mhat(W, PFMP_F64, E(A, 0), phi, true, nullptr, nullptr);
     void* chi = E(A, 1);
-    cg64(A, A->M, chi, E(A, 0));
-    // 2 Re chi^dag dW^dag phi3 = 2 Re phi3^dag dW chi
-    deriv_mhat(A->W, A->F, A->Hc, A->phi[2], chi, 2.0, A->od[0], A->od[1]);
-    deriv_K(A, A->M, chi, chi, -1.0);
-  } else {
-    PFMP_REQUIRE(false, PFMP_E_INVALID, "unknown action term");
+    cg64(A, Mb, chi, E(A, 0));
+    // 2 Re chi^dag dW^dag phi = 2 Re phi^dag dW chi
+    deriv_mhat(W, A->F, A->Hc, phi, chi, 2.0, A->od[0], A->od[1]);
+    deriv_K(A, Mb, chi, chi, -1.0);
+  } else {  // INV
+    void* chi = E(A, 1);
+    cg64(A, W, chi, phi);
+    deriv_K(A, W, chi, chi, -1.0);
   }
   if (clover) clover_force(c, A->F, A->Hc);
 }
@@ -371,6 +572,7 @@ void alg_unpack(pfmp_ctx* c, double* dst, int where, const double* src_dev) {
 }
 
 void action_force_out(pfmp_action* A, int term, double* out, int where) {
+  PFMP_REQUIRE(term >= 0 && term < (int)A->t.size(), PFMP_E_INVALID, "term index out of range");
   action_zero_force(A);
   action_force(A, term);
   alg_unpack(A->ctx, out, where, A->F);
@@ -402,39 +604,66 @@ void mom_update(pfmp_action* A, double eps) {
   PFMP_CHECK_LAUNCH();
 }
 
-void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int term_level[5],
-                const double* mom, int where, const void* const xi[3], double u, pfmp_traj_info* info) {
+// link sum and maximum of |F_mu(x)| over the current force buffer (synchronises)
+void force_norms(pfmp_action* A, double* sum, double* mx) {
+  pfmp_ctx* c = A->ctx;
+  PFMP_CUDA(cudaMemsetAsync(c->d_sums, 0, 2 * sizeof(double), c->stream));
+  const long nl = 8L * c->g.Vh;
+  k_force_norm<<<grid_for(nl), kBlock, 0, c->stream>>>(A->F, c->g.Vh, c->rb, c->d_sums,
+                                                       (unsigned long long*)(c->d_sums + 1));
+  PFMP_CHECK_LAUNCH();
+  double v[2];
+  sync_read(c, v, 2);
+  *sum = v[0];
+  *mx = v[1];
+}
+
+void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int* term_level,
+                const double* mom, int where, const void* const* xi, double u, pfmp_traj_info* info) {
   pfmp_ctx* c = A->ctx;
   const Geom& g = c->g;
+  const int nt = (int)A->t.size();
   PFMP_REQUIRE(len >= 1 && nlev >= 1, PFMP_E_INVALID, "empty schedule");
-  for (int t = 0; t < 5; ++t)
+  for (int t = 0; t < nt; ++t)
     PFMP_REQUIRE(term_level[t] >= -1 && term_level[t] < nlev, PFMP_E_INVALID, "term level out of range");
-  const long long k0 = A->M->kapply + A->W->kapply;
+  *info = pfmp_traj_info{};
+  const long long k0 = kapply_total(A);
   A->force_evals = 0;
   PFMP_CUDA(cudaMemcpyAsync(A->U0, c->U64, (size_t)g.Vh * 72 * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-  if (A->M->built_version != c->gauge_version || A->W->built_version != c->gauge_version) refresh_ops(A);
+  bool stale = false;
+  for (auto op : A->ops) stale = stale || op->built_version != c->gauge_version;
+  if (stale) refresh_ops(A);
   alg_pack(c, A->mom, mom, where);
-  action_heatbath(A, xi[0], xi[1], xi[2]);
-  double S0[5], S1[5];
-  action_eval(A, S0);
+  action_heatbath(A, xi);
+  std::vector<double> S0(nt, 0.0), S1(nt, 0.0);
   double H0 = kinetic(A);
-  for (int t = 0; t < 5; ++t)
-    if (term_level[t] >= 0) H0 += S0[t];
+  for (int t = 0; t < nt; ++t)
+    if (term_level[t] >= 0) H0 += (S0[t] = action_term(A, t));
+  // per term: P -= eps F_t, one term at a time so that each term's force is measured
+  const double nlinks = 4.0 * g.V;
   for (int i = 0; i < len; ++i) {
     if (T[i] != 0.0) link_update(A, T[i]);
     for (int l = 0; l < nlev; ++l) {
       const double eps = S[(size_t)l * len + i];
       if (eps == 0.0) continue;
-      action_zero_force(A);
-      for (int t = 0; t < 5; ++t)
-        if (term_level[t] == l) action_force(A, t);
-      mom_update(A, eps);
+      for (int t = 0; t < nt; ++t) {
+        if (term_level[t] != l) continue;
+        const long long kt = kapply_total(A);
+        action_zero_force(A);
+        action_force(A, t);
+        mom_update(A, eps);
+        info->k_apply_term[t] += kapply_total(A) - kt;
+        double fs, fm;
+        force_norms(A, &fs, &fm);
+        info->nforce[t] += 1;
+        info->fmax[t] = std::max(info->fmax[t], fm);
+        info->favg[t] += fs / nlinks;
+      }
     }
   }
-  action_eval(A, S1);
   double H1 = kinetic(A);
-  for (int t = 0; t < 5; ++t)
-    if (term_level[t] >= 0) H1 += S1[t];
+  for (int t = 0; t < nt; ++t)
+    if (term_level[t] >= 0) H1 += (S1[t] = action_term(A, t));
   const double dH = H1 - H0;
   PFMP_REQUIRE(std::isfinite(dH), PFMP_E_NAN, "dH is not finite");
   const bool acc = u < std::exp(-dH);
@@ -442,11 +671,12 @@ void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double
   info->H1 = H1;
   info->dH = dH;
   info->accepted = acc ? 1 : 0;
-  for (int t = 0; t < 5; ++t) {
-    info->S0[t] = term_level[t] >= 0 ? S0[t] : 0.0;
-    info->S1[t] = term_level[t] >= 0 ? S1[t] : 0.0;
+  for (int t = 0; t < nt; ++t) {
+    info->S0[t] = S0[t];
+    info->S1[t] = S1[t];
+    if (info->nforce[t] > 0) info->favg[t] /= info->nforce[t];
   }
-  info->k_apply = A->M->kapply + A->W->kapply - k0;
+  info->k_apply = kapply_total(A) - k0;
   info->force_evals = A->force_evals;
   if (!acc) {
     PFMP_CUDA(cudaMemcpyAsync(c->U64, A->U0, (size_t)g.Vh * 72 * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
@@ -512,12 +742,12 @@ int schedule_merge(int ns, const int* len, const double* T, const double* S, int
 }
 
 void action_get_phi(pfmp_action* A, int i, double* out, int where) {
-  PFMP_REQUIRE(i >= 0 && i < 3, PFMP_E_INVALID, "pseudofermion index must be 0, 1 or 2");
+  PFMP_REQUIRE(i >= 0 && i < (int)A->phi.size(), PFMP_E_INVALID, "pseudofermion index out of range");
   spinor_unpack_any(A->ctx, out, where, A->phi[i], PFMP_F64, 0);
 }
 
 void action_set_phi(pfmp_action* A, int i, const double* in, int where) {
-  PFMP_REQUIRE(i >= 0 && i < 3, PFMP_E_INVALID, "pseudofermion index must be 0, 1 or 2");
+  PFMP_REQUIRE(i >= 0 && i < (int)A->phi.size(), PFMP_E_INVALID, "pseudofermion index out of range");
   spinor_pack_any(A->ctx, A->phi[i], PFMP_F64, in, where, 0);
 }
 

@@ -232,6 +232,7 @@ int solve_multishift(pfmp_op* op, int ns, const std::complex<double>* sigma, voi
   h->stop_rr = tol * tol * bb;
   PFMP_CUDA(cudaMemcpyAsync(op->scal, h, sizeof(CGScalars), cudaMemcpyHostToDevice, c->stream));
   int done = 0;
+  const long long kapply0 = op->kapply;  // queued iterations after convergence do no work
   while (done < max_iter) {
     const int chunk = check < max_iter - done ? check : max_iter - done;
     for (int k = 0; k < chunk; ++k) {
@@ -255,6 +256,7 @@ int solve_multishift(pfmp_op* op, int ns, const std::complex<double>* sigma, voi
   }
   *iters = done;
   *kapply = done;
+  op->kapply = kapply0 + done;
   if (want_true_res) {
     // || b - (K + sigma) x || / ||b|| for every shift, FP64
     for (int k = 0; k < ns; ++k) {

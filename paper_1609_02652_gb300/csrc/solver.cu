@@ -61,10 +61,15 @@ static void launch_chunk(pfmp_op* op, int prec, void* x, void* r, void* p, void*
 // One chunk of CG iterations.  Without kernel profiling the chunk is captured once into
 // a CUDA graph (6 kernels per iteration, all parameters fixed: the scalars live on the
 // device) and replayed on the context's stream, which removes the per-launch host cost.
+// K applications are counted by run_cg from the iterations the device actually ran (the
+// queued kernels of a converged chunk return at once), so the count kop keeps while the
+// chunk is launched or captured is put back afterwards.
 static void run_chunk(pfmp_op* op, int prec, void* x, void* r, void* p, void* Ap, int chunk) {
   pfmp_ctx* c = op->ctx;
+  const long long kapply0 = op->kapply;
   if (c->prof.on) {
     launch_chunk(op, prec, x, r, p, Ap, chunk);
+    op->kapply = kapply0;
     return;
   }
   pfmp_op::Graph& G = op->graph[prec];
@@ -91,6 +96,7 @@ static void run_chunk(pfmp_op* op, int prec, void* x, void* r, void* p, void* Ap
       throw;
     }
     c->stream = keep;
+    op->kapply = kapply0;
     G.kernels = launch_count() - n0;
     count_launches(-G.kernels);  // captured, not launched
     PFMP_CUDA(cudaStreamEndCapture(op->cap, &graph));
@@ -112,6 +118,7 @@ static int run_cg(pfmp_op* op, int prec, void* x, void* r, void* p, void* Ap, in
     if (chunk <= 0) break;
     run_chunk(op, prec, x, r, p, Ap, chunk);
     get_scalars(op);
+    op->kapply += op->h_scal->iter - done_iters;
     done_iters = op->h_scal->iter;
     if (op->h_scal->done) break;
   }
