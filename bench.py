@@ -400,10 +400,12 @@ def batched_96(capi, stream, l2_flush, args):
 
 
 def learned(capi, stream, l2_flush, args, ctx, op, b, x):
-    """Mixed + learned: a [1,4,4,1] network trained (residual loss, Adam, the project's
-    kernels) on (b, K^{-1} b) pairs from the mixed solver on a held-out 8^3x16 gauge field
-    (eps = 0.5, seed 2, same kappa and c_sw), then used as the FGCR preconditioner on the
-    16^3x32 benchmark system; GCR (no network) alongside."""
+    """Mixed + learned: a [1,8,8,8,1] network (4 layers, 8 hidden channels) trained
+    (residual loss, Adam, the project's FP32 kernels) on (b, K^{-1} b) pairs from the
+    mixed solver on a held-out 8^3x16 gauge field (eps = 0.5, seed 2, same kappa and c_sw),
+    then used as the FGCR preconditioner on the 16^3x32 benchmark system with its 8 -> 8
+    layers on the tensor cores; the same network on the FP32 kernels and GCR (no network)
+    alongside, and the time of one network application each way."""
     import torch
 
     import pfmp_inputs as pin
@@ -427,7 +429,7 @@ def learned(capi, stream, l2_flush, args, ctx, op, b, x):
         bs.append(bb)
         xs.append(xx)
     t_pairs = time.perf_counter() - t0
-    ch = [1, 4, 4, 1]
+    ch = [1, 8, 8, 8, 1]
     net = capi.pfmp_nn_create(tctx, ch, capi.PFMP_F32)
     capi.pfmp_nn_set_weights(net, pin.nn_weights(ch, 5))
     t0 = time.perf_counter()
@@ -445,7 +447,9 @@ def learned(capi, stream, l2_flush, args, ctx, op, b, x):
     prm = capi.SolverParams(method=0, tol=TOL, max_iter=20000, delta=1e-3, check_every=8, restart=16)
     out = {"train_lattice": "8x8x8x16 (held-out field, seed 2)", "pairs": 16, "pairs_s": t_pairs,
            "train_steps": args.nn_steps, "train_s": t_train, "final_train_loss": loss, "network": ch}
-    for name, n in (("fgcr_nn", net), ("gcr", None)):
+    for name, n, tc in (("fgcr_nn", net, 1), ("fgcr_nn_fp32_layers", net, 0), ("gcr", None, 0)):
+        if n is not None:
+            capi.pfmp_nn_set_tensor_cores(n, tc)
         capi.pfmp_solve_fgcr(op, n, prm, x, b)  # warm
         l2_flush()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -455,6 +459,22 @@ def learned(capi, stream, l2_flush, args, ctx, op, b, x):
         e1.synchronize()
         out[name] = {"ms": e0.elapsed_time(e1), "iterations": info.iters, "cg_fallback_iterations": info.reliable_updates,
                      "true_rel_res": info.true_rel_res}
+    # one network application on an FP32 even field, tensor-core and FP32 layers
+    n32 = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F32) // 4
+    vin = torch.randn(n32, dtype=torch.float32, device="cuda")
+    vout = torch.zeros_like(vin)
+    for tc in (1, 0):
+        capi.pfmp_nn_set_tensor_cores(net, tc)
+        capi.pfmp_nn_apply(net, capi.PFMP_F32, vout, vin)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            capi.pfmp_nn_apply(net, capi.PFMP_F32, vout, vin)
+        e1.record(stream)
+        e1.synchronize()
+        out["apply_ms_tensor_cores" if tc else "apply_ms_fp32_layers"] = e0.elapsed_time(e1) / 10
+    capi.pfmp_nn_set_tensor_cores(net, 1)
     capi.pfmp_nn_destroy(net)
     return out
 

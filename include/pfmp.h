@@ -397,8 +397,17 @@ int pfmp_nn_destroy(pfmp_nn* nn);
 int64_t pfmp_nn_num_weights(const pfmp_nn* nn);
 int pfmp_nn_set_weights(pfmp_nn* nn, const double* w);
 int pfmp_nn_get_weights(pfmp_nn* nn, double* w);
-/* out = N(in), even fields of precision prec in the library layout                     */
+/* out = N(in), even fields of precision prec in the library layout (synchronises)      */
 int pfmp_nn_apply(pfmp_nn* nn, int prec, void* out, const void* in);
+/* Tensor-core inference (default on for FP32 networks with 1 -> 8, 8 -> 8 or 8 -> 1
+ * layers): those layers of pfmp_nn_apply (FP32 io) and of FGCR run as tcgen05 MMAs on
+ * FP16 operands
+ * (inputs scaled by 1 / rms of the network input, weights packed as [[Re, -Im], [Im,
+ * Re]]) with FP32 accumulation; training always uses the FP32 kernels.  on = 0 selects
+ * the FP32 kernels everywhere.  PFMP_E_UNSUPPORTED if the network has no such layer;
+ * PFMP_E_TIMEOUT from pfmp_nn_apply / pfmp_solve_fgcr if a tensor-core kernel gave up
+ * waiting for its MMAs (bounded waits; the context stays usable).                       */
+int pfmp_nn_set_tensor_cores(pfmp_nn* nn, int on);
 /* loss of one pair and its gradient dL/dRe W + i dL/dIm W (grad: host, may be NULL)     */
 int pfmp_nn_loss_grad(pfmp_nn* nn, pfmp_op* op, int kind, const void* b, const void* x, double* loss, double* grad);
 int pfmp_nn_train(pfmp_nn* nn, pfmp_op* op, int kind, int npairs, const void* const* b, const void* const* x, int steps,

@@ -148,6 +148,7 @@ SIGNATURES = {
     "pfmp_nn_set_weights": (I, [P, DP]),
     "pfmp_nn_get_weights": (I, [P, DP]),
     "pfmp_nn_apply": (I, [P, I, P, P]),
+    "pfmp_nn_set_tensor_cores": (I, [P, I]),
     "pfmp_nn_loss_grad": (I, [P, P, I, P, P, DP, DP]),
     "pfmp_nn_train": (I, [P, P, I, I, C.POINTER(P), C.POINTER(P), I, I, D, DP]),
     "pfmp_solve_fgcr": (I, [P, P, C.POINTER(SolverParams), P, P, C.POINTER(SolveInfo)]),
@@ -548,6 +549,10 @@ def pfmp_nn_get_weights(nn, shapes):
 
 def pfmp_nn_apply(nn, prec, out, inp):
     check(lib().pfmp_nn_apply(nn, prec, _ptr(out), _ptr(inp)))
+
+
+def pfmp_nn_set_tensor_cores(nn, on):
+    check(lib().pfmp_nn_set_tensor_cores(nn, int(on)))
 
 
 PFMP_NN_LOSS_SOLUTION = 0

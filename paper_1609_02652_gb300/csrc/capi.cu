@@ -48,6 +48,8 @@ void nn_set_weights(pfmp_nn* N, const double* w);
 void nn_get_weights(pfmp_nn* N, double* w);
 void nn_get_grads(pfmp_nn* N, double* w);
 void nn_apply(pfmp_nn* N, void* out, const void* in, int prec_io);
+void nn_set_tc(pfmp_nn* N, bool on);
+void nn_check(pfmp_nn* N);
 void nn_zero_grad(pfmp_nn* N);
 double nn_loss_grad(pfmp_nn* N, pfmp_op* op, int kind, const void* b, const void* x, double scale);
 double nn_train(pfmp_nn* N, pfmp_op* op, int kind, int npairs, const void* const* b, const void* const* x, int steps,
@@ -109,6 +111,7 @@ void pfmp::op_delete(pfmp_op* op) {
   dev_free(op->scal);
   if (op->h_scal) cudaFreeHost(op->h_scal);
   ms_work_free(op);
+  if (op->fgcr && op->fgcr_free) op->fgcr_free(op->fgcr);
   for (auto& G : op->graph)
     if (G.exec) cudaGraphExecDestroy(G.exec);
   if (op->cap) cudaStreamDestroy(op->cap);
@@ -720,6 +723,14 @@ int pfmp_nn_apply(pfmp_nn* nn, int prec, void* out, const void* in) {
   PFMP_REQUIRE(nn && out && in && out != in, PFMP_E_INVALID, "bad argument");
   check_prec(prec);
   nn_apply(nn, out, in, prec);
+  nn_check(nn);
+  API_END
+}
+
+int pfmp_nn_set_tensor_cores(pfmp_nn* nn, int on) {
+  API_BEGIN
+  PFMP_REQUIRE(nn, PFMP_E_INVALID, "null network");
+  nn_set_tc(nn, on != 0);
   API_END
 }
 

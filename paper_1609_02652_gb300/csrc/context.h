@@ -89,6 +89,8 @@ struct pfmp_op {
   } graph[2];
   cudaStream_t cap = nullptr;
   pfmp::MSWork* ms = nullptr;  // multi-shift workspace (grown on demand)
+  void* fgcr = nullptr;         // FGCR workspace (kept between solves), freed by fgcr_free
+  void (*fgcr_free)(void*) = nullptr;
   long long kapply = 0;         // K applications done (CUDA-graph replays included)
   int nsplit[3] = {1, 1, 1};    // threads per site of the stencil kernels: FP64, FP32, double-float
   int hop_block = 128;          // threads per block of the stencil kernels (32..128)

@@ -457,16 +457,33 @@ struct pfmp_nn {
   double last_norm = 1;
   int maxc = 1;
   long step = 0;
+  // tensor-core inference of the C -> C layers (nn_tc.cu)
+  bool tc = false;               // use it in nn_apply
+  bool packed = false;           // Bp holds the current weights
+  std::vector<void*> Bp;         // packed FP16 operand per layer
+  std::vector<void*> act16;      // FP16 scaled inputs of each layer
+  float* sigma = nullptr;        // device scalar: 1 / rms of the network input
+  int* err = nullptr;            // device error flag of the tensor-core kernel
 };
 
 namespace pfmp {
 
 static size_t csz(const pfmp_nn* N) { return N->prec == PFMP_F64 ? sizeof(double2) : sizeof(float2); }
 
+bool nn_tc_supported(int cin, int cout);
+size_t nn_tc_packed_bytes(int cin, int cout);
+void nn_tc_pack(pfmp_ctx* c, int cin, int cout, const void* W, void* Bp);
+void nn_tc_scale(pfmp_ctx* c, const void* in_even_f32, float* sigma_dev);
+void nn_tc_layer(pfmp_ctx* c, int cin, int cout, bool last, const void* Bp, const void* in, void* out,
+                 const float* sigma, int* err);
+void nn_tc_embed(pfmp_ctx* c, const void* in_even_f32, const float* sigma, void* act16);
+
 void nn_destroy(pfmp_nn* N) {
   if (!N) return;
-  for (auto* vec : {&N->W, &N->gW, &N->m, &N->v, &N->act})
+  for (auto* vec : {&N->W, &N->gW, &N->m, &N->v, &N->act, &N->Bp, &N->act16})
     for (auto p : *vec) dev_free(p);
+  dev_free(N->sigma);
+  dev_free(N->err);
   dev_free(N->gbuf[0]);
   dev_free(N->gbuf[1]);
   dev_free(N->target);
@@ -500,6 +517,18 @@ pfmp_nn* nn_create(pfmp_ctx* c, int nl, const int* ch, int prec) {
     for (auto& p : N->gbuf) p = dev_alloc((size_t)N->maxc * 12 * c->g.V * csz(N));
     N->target = dev_alloc((size_t)12 * c->g.V * csz(N));
     for (auto& p : N->ev) p = dev_alloc(spinor_bytes(c->g, prec));
+    bool all = prec == PFMP_F32 && nl >= 2;
+    for (int l = 0; l < nl; ++l) all = all && nn_tc_supported(ch[l], ch[l + 1]);
+    if (all) {  // every layer on the tensor cores (1 -> 8, 8 -> 8 ..., 8 -> 1)
+      for (int l = 0; l < nl; ++l) {
+        N->Bp.push_back(dev_alloc(nn_tc_packed_bytes(ch[l], ch[l + 1])));
+        N->act16.push_back(dev_alloc((size_t)ch[l] * 12 * c->g.V * 4));
+      }
+      N->tc = true;
+      N->sigma = (float*)dev_alloc(sizeof(float));
+      N->err = (int*)dev_alloc(sizeof(int));
+      PFMP_CUDA(cudaMemset(N->err, 0, sizeof(int)));
+    }
   } catch (...) {
     nn_destroy(N);
     throw;
@@ -529,6 +558,7 @@ void nn_set_weights(pfmp_nn* N, const double* w) {
     off += n;
   }
   N->step = 0;
+  N->packed = false;
 }
 
 static void copy_out(pfmp_nn* N, const std::vector<void*>& src, double* w) {
@@ -547,6 +577,25 @@ static void copy_out(pfmp_nn* N, const std::vector<void*>& src, double* w) {
   }
 }
 void nn_get_weights(pfmp_nn* N, double* w) { copy_out(N, N->W, w); }
+
+// tensor-core inference on / off (only FP32 networks with C -> C layers have it)
+void nn_set_tc(pfmp_nn* N, bool on) {
+  PFMP_REQUIRE(!on || !N->Bp.empty(), PFMP_E_UNSUPPORTED,
+               "tensor-core inference needs an FP32 network 1 -> 8 -> ... -> 8 -> 1");
+  N->tc = on;
+}
+
+// raises PFMP_E_TIMEOUT if a tensor-core kernel gave up waiting (synchronises)
+void nn_check(pfmp_nn* N) {
+  if (!N->err) return;
+  int e = 0;
+  PFMP_CUDA(cudaMemcpyAsync(&e, N->err, sizeof(int), cudaMemcpyDeviceToHost, N->ctx->stream));
+  PFMP_CUDA(cudaStreamSynchronize(N->ctx->stream));
+  if (e) {
+    PFMP_CUDA(cudaMemsetAsync(N->err, 0, sizeof(int), N->ctx->stream));
+    PFMP_REQUIRE(false, PFMP_E_TIMEOUT, "tensor-core network layer timed out waiting for its MMAs");
+  }
+}
 void nn_get_grads(pfmp_nn* N, double* w) { copy_out(N, N->gW, w); }
 
 template <typename T, int CO>
@@ -558,6 +607,23 @@ static bool layer_site(pfmp_ctx* c, const void* W, int cin, const void* in, void
                                                                       (C*)out);
   PFMP_CHECK_LAUNCH();
   return true;
+}
+
+// tensor-core forward pass: in (even FP32) -> act[L] (FP32), through FP16 activations
+static void forward_tc(pfmp_nn* N, const void* in) {
+  pfmp_ctx* c = N->ctx;
+  const int L = (int)N->W.size();
+  if (!N->packed) {
+    for (int l = 0; l < L; ++l) nn_tc_pack(c, N->ch[l], N->ch[l + 1], N->W[l], N->Bp[l]);
+    N->packed = true;
+  }
+  nn_tc_scale(c, in, N->sigma);
+  nn_tc_embed(c, in, N->sigma, N->act16[0]);
+  for (int l = 0; l < L; ++l) {
+    const bool last = l == L - 1;
+    nn_tc_layer(c, N->ch[l], N->ch[l + 1], last, N->Bp[l], N->act16[l], last ? N->act[L] : N->act16[l + 1],
+                N->sigma, N->err);
+  }
 }
 
 template <typename T>
@@ -595,12 +661,16 @@ void nn_apply(pfmp_nn* N, void* out, const void* in, int prec_io) {
     else
       k_nn_extract<double, PFMP_F32><<<nblocks(g.Vh), kBlock, 0, c->stream>>>(g, (const double2*)N->act[L], (float4*)out);
   } else {
-    if (prec_io == PFMP_F64)
-      k_nn_embed<float, PFMP_F64><<<nblocks(g.V), kBlock, 0, c->stream>>>(g, (const double2*)in, (float2*)N->act[0]);
-    else
-      k_nn_embed<float, PFMP_F32><<<nblocks(g.V), kBlock, 0, c->stream>>>(g, (const float4*)in, (float2*)N->act[0]);
-    PFMP_CHECK_LAUNCH();
-    forward_t<float>(N);
+    if (N->tc && prec_io == PFMP_F32) {
+      forward_tc(N, in);
+    } else {
+      if (prec_io == PFMP_F64)
+        k_nn_embed<float, PFMP_F64><<<nblocks(g.V), kBlock, 0, c->stream>>>(g, (const double2*)in, (float2*)N->act[0]);
+      else
+        k_nn_embed<float, PFMP_F32><<<nblocks(g.V), kBlock, 0, c->stream>>>(g, (const float4*)in, (float2*)N->act[0]);
+      PFMP_CHECK_LAUNCH();
+      forward_t<float>(N);
+    }
     if (prec_io == PFMP_F64)
       k_nn_extract<float, PFMP_F64><<<nblocks(g.Vh), kBlock, 0, c->stream>>>(g, (const float2*)N->act[L], (double2*)out);
     else
@@ -721,6 +791,7 @@ double nn_loss_grad(pfmp_nn* N, pfmp_op* op, int kind, const void* b, const void
 void nn_adam(pfmp_nn* N, double lr) {
   pfmp_ctx* c = N->ctx;
   N->step += 1;
+  N->packed = false;
   const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
   const double c1 = 1 - std::pow(b1, (double)N->step), c2 = 1 - std::pow(b2, (double)N->step);
   for (size_t l = 0; l < N->W.size(); ++l) {
@@ -764,6 +835,7 @@ static std::complex<double> cdot_sync(pfmp_ctx* c, int prec, const void* x, cons
 }
 
 struct FgcrWork {
+  int restart = 0, grid = 0;
   std::vector<float4*> Z, W;
   float4 *r = nullptr, *e = nullptr, *z = nullptr, *w = nullptr;
   float4** dW = nullptr;
@@ -796,22 +868,38 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
   if (!(delta > 0 && delta < 1)) delta = 1e-3;
   const size_t b32 = spinor_bytes(g, PFMP_F32), b64 = spinor_bytes(g, PFMP_F64);
   const long n32 = 6L * g.Vh;
-  FgcrWork wk;
-  for (int k = 0; k < restart; ++k) {
-    wk.Z.push_back((float4*)dev_alloc(b32));
-    wk.W.push_back((float4*)dev_alloc(b32));
-  }
-  wk.r = (float4*)dev_alloc(b32);
-  wk.e = (float4*)dev_alloc(b32);
   const int fgrid = (int)std::min<long>(nblocks(n32), 152 * 2);
-  wk.dW = (float4**)dev_alloc(restart * sizeof(float4*));
-  wk.dZ = (float4**)dev_alloc(restart * sizeof(float4*));
-  PFMP_CUDA(cudaMemcpy(wk.dW, wk.W.data(), restart * sizeof(float4*), cudaMemcpyHostToDevice));
-  PFMP_CUDA(cudaMemcpy(wk.dZ, wk.Z.data(), restart * sizeof(float4*), cudaMemcpyHostToDevice));
-  wk.part = (double*)dev_alloc((size_t)fgrid * 34 * sizeof(double));
-  wk.ticket = (unsigned*)dev_alloc(sizeof(unsigned));
-  PFMP_CUDA(cudaMemset(wk.ticket, 0, sizeof(unsigned)));
-  wk.out = (double*)dev_alloc(34 * sizeof(double));
+  // workspace kept on the operator between solves (allocation is not per solve)
+  FgcrWork* wp = (FgcrWork*)op->fgcr;
+  if (!wp || wp->restart < restart) {
+    if (wp) op->fgcr_free(wp);
+    op->fgcr = nullptr;
+    wp = new FgcrWork();
+    try {
+      for (int k = 0; k < restart; ++k) {
+        wp->Z.push_back((float4*)dev_alloc(b32));
+        wp->W.push_back((float4*)dev_alloc(b32));
+      }
+      wp->r = (float4*)dev_alloc(b32);
+      wp->e = (float4*)dev_alloc(b32);
+      wp->dW = (float4**)dev_alloc(restart * sizeof(float4*));
+      wp->dZ = (float4**)dev_alloc(restart * sizeof(float4*));
+      PFMP_CUDA(cudaMemcpy(wp->dW, wp->W.data(), restart * sizeof(float4*), cudaMemcpyHostToDevice));
+      PFMP_CUDA(cudaMemcpy(wp->dZ, wp->Z.data(), restart * sizeof(float4*), cudaMemcpyHostToDevice));
+      wp->part = (double*)dev_alloc((size_t)fgrid * 34 * sizeof(double));
+      wp->ticket = (unsigned*)dev_alloc(sizeof(unsigned));
+      PFMP_CUDA(cudaMemset(wp->ticket, 0, sizeof(unsigned)));
+      wp->out = (double*)dev_alloc(34 * sizeof(double));
+    } catch (...) {
+      delete wp;
+      throw;
+    }
+    wp->restart = restart;
+    wp->grid = fgrid;
+    op->fgcr = wp;
+    op->fgcr_free = [](void* p) { delete (FgcrWork*)p; };
+  }
+  FgcrWork& wk = *wp;
   *iters = *outer = *fallback_iters = 0;
   *kapply = 0;
   blas_norm2(c, PFMP_F64, b, c->d_sums);
@@ -893,6 +981,7 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
       break;
     }
   }
+  if (nn) nn_check(nn);
   *true_res = res;
   return res < tol ? PFMP_OK : PFMP_E_NOT_CONVERGED;
 }

@@ -111,3 +111,65 @@ def test_training_and_fgcr_gain(world):
         assert its["nn"] < its["gcr"], its
     finally:
         capi.pfmp_nn_destroy(net)
+
+
+CH8 = [1, 8, 8, 8, 1]
+# Tensor-core layers take FP16 operands (unit roundoff u = 2^-11) with FP32 accumulation:
+# each product carries a relative error of at most 2u, so a layer's output (sums of up
+# to 576 such terms that do not cancel) is within about 2u of its norm, and the four
+# layers of [1, 8, 8, 8, 1] within 8u = 3.9e-3 of the FP64 network.
+TC_BAR = 4e-3
+
+
+@pytest.mark.parametrize("dims", [(6, 4, 4, 6), (4, 4, 4, 8)], ids=["6x4x4x6_ragged", "4x4x4x8"])
+def test_tensor_core_forward(dims):
+    """[1, 8, 8, 8, 1]: all four layers on tcgen05 (V = 576 sites is 4.5 tiles of 128: a
+    ragged tail) against the oracle's FP64 network; the FP32 kernels alongside;
+    a residual 1e-9 times smaller keeps the same relative accuracy (the input is scaled
+    by its rms before the FP16 conversion)."""
+    from oracle import nn
+    from paper_1609_02652_gb300 import capi
+
+    lat, U = oracle_gauge(dims, 0.4, 61)
+    g = Gpu(lat, U)
+    net = capi.pfmp_nn_create(g.ctx, CH8, capi.PFMP_F32)
+    try:
+        ws = nn.init_weights(CH8, 7)
+        capi.pfmp_nn_set_weights(net, [w.numpy() for w in ws])
+        b = lat.even * torch.tensor(pin.spinor(lat.dims, 81)).reshape(*lat.shape, 4, 3)
+        ref = nn.network_apply(lat, U, ws, b)
+        out = g.buf(1)
+        capi.pfmp_nn_apply(net, 1, out, g.pack(b, 1, 0))
+        err = rel_l2(lat.even * g.unpack(out, 1, 0), ref)
+        assert err < TC_BAR, err
+        capi.pfmp_nn_apply(net, 1, out, g.pack(1e-9 * b, 1, 0))
+        err_small = rel_l2(lat.even * g.unpack(out, 1, 0), 1e-9 * ref)
+        assert err_small < TC_BAR, err_small
+        capi.pfmp_nn_set_tensor_cores(net, 0)
+        capi.pfmp_nn_apply(net, 1, out, g.pack(b, 1, 0))
+        assert rel_l2(lat.even * g.unpack(out, 1, 0), ref) < 1e-5
+        print("tensor-core network error", err, err_small)
+    finally:
+        capi.pfmp_nn_destroy(net)
+        g.close()
+
+
+def test_tensor_core_fgcr_converges(world):
+    """FGCR with the tensor-core network reaches the 1e-10 true residual (oracle K)."""
+    from oracle.dirac import WilsonClover
+
+    lat, U, g, capi = world
+    op = g.op(0.125, 1.0)
+    W = WilsonClover(lat, U, 0.125, 1.0)
+    net = capi.pfmp_nn_create(g.ctx, CH8, capi.PFMP_F32)
+    try:
+        capi.pfmp_nn_set_weights(net, pin.nn_weights(CH8, 9))
+        prm = capi.SolverParams(method=0, tol=1e-10, max_iter=4000, delta=1e-3, check_every=8, restart=16)
+        b = lat.even * torch.tensor(pin.spinor(lat.dims, 998)).reshape(*lat.shape, 4, 3)
+        x = g.buf(0)
+        capi.pfmp_solve_fgcr(op, net, prm, x, g.pack(b, 0, 0))
+        xo = lat.even * g.unpack(x, 0, 0)
+        res = float(torch.linalg.vector_norm(b - W.K(xo)) / torch.linalg.vector_norm(b))
+        assert res < 1e-10, res
+    finally:
+        capi.pfmp_nn_destroy(net)
