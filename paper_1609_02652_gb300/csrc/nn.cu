@@ -368,9 +368,16 @@ __device__ bool grid_sum_n(double* v, int nv, double* partials, unsigned* ticket
   return threadIdx.x == 0;
 }
 
+// The inner FGCR iteration runs without host round trips: the Gram-Schmidt coefficients,
+// |w|^2, the step alpha and the residual norm stay in device memory, and the solver
+// scalars' `done` flag (set by the step kernel's last block once |r| has fallen by delta)
+// makes every later kernel of the cycle return at once.
+
 // h_j = <W_j, w> (j < k) and <w, r>: out[2j], out[2j+1], out[2k], out[2k+1]
 __global__ void k_fgcr_dots(float4* const* __restrict__ Wp, int k, const float4* __restrict__ w,
-                            const float4* __restrict__ r, long n, double* partials, unsigned* ticket, double* out) {
+                            const float4* __restrict__ r, long n, double* partials, unsigned* ticket, double* out,
+                            const CGScalars* __restrict__ s) {
+  if (s->done) return;
   double v[34];
   for (int j = 0; j < 2 * k + 2; ++j) v[j] = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -387,15 +394,19 @@ __global__ void k_fgcr_dots(float4* const* __restrict__ Wp, int k, const float4*
   grid_sum_n(v, 2 * k + 2, partials, ticket, out);
 }
 
-// w -= sum_j h_j W_j, z -= sum_j h_j Z_j, out[0] = |w|^2
-__global__ void k_fgcr_orth(float4* const* __restrict__ Wp, float4* const* __restrict__ Zp, int k, CoefList h,
-                            float4* __restrict__ w, float4* __restrict__ z, long n, double* partials, unsigned* ticket,
-                            double* out) {
+// w -= sum_j h_j W_j, z -= sum_j h_j Z_j with h from the dots; *n2 = |w|^2
+__global__ void k_fgcr_orth(float4* const* __restrict__ Wp, float4* const* __restrict__ Zp, int k,
+                            const double* __restrict__ hd, float4* __restrict__ w, float4* __restrict__ z, long n,
+                            double* partials, unsigned* ticket, double* n2, const CGScalars* __restrict__ s) {
+  if (s->done) return;
+  __shared__ float2 h[16];
+  if (threadIdx.x < k) h[threadIdx.x] = make_float2((float)hd[2 * threadIdx.x], (float)hd[2 * threadIdx.x + 1]);
+  __syncthreads();
   double v[1] = {0.0};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     float4 a = w[i], b = z[i];
     for (int j = 0; j < k; ++j) {
-      const float2 c = h.h[j];
+      const float2 c = h[j];
       const float4 q = Wp[j][i], p = Zp[j][i];
       a.x -= c.x * q.x - c.y * q.y;
       a.y -= c.x * q.y + c.y * q.x;
@@ -410,27 +421,68 @@ __global__ void k_fgcr_orth(float4* const* __restrict__ Wp, float4* const* __res
     z[i] = b;
     v[0] += (double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z + (double)a.w * a.w;
   }
-  grid_sum_n(v, 1, partials, ticket, out);
+  grid_sum_n(v, 1, partials, ticket, n2);
 }
 
-// r -= alpha w, e += alpha z, then w, z scaled by s (to unit |w|)
+// alpha = <w, r> / |w|^2: r -= alpha w, e += alpha z, then w, z scaled to unit |w|; the
+// last block updates |r|^2 = |r|^2 - |<w, r>|^2 / |w|^2 (r is orthogonal to the earlier
+// directions), counts the iteration and raises `done` below stop_rr (or when w vanished)
 __global__ void k_fgcr_step(float4* __restrict__ w, float4* __restrict__ z, float4* __restrict__ r,
-                            float4* __restrict__ e, float2 al, float s, long n) {
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    float4 a = w[i], b = z[i], rr = r[i], ee = e[i];
-    rr.x -= al.x * a.x - al.y * a.y;
-    rr.y -= al.x * a.y + al.y * a.x;
-    rr.z -= al.x * a.z - al.y * a.w;
-    rr.w -= al.x * a.w + al.y * a.z;
-    ee.x += al.x * b.x - al.y * b.y;
-    ee.y += al.x * b.y + al.y * b.x;
-    ee.z += al.x * b.z - al.y * b.w;
-    ee.w += al.x * b.w + al.y * b.z;
-    r[i] = rr;
-    e[i] = ee;
-    w[i] = make_float4(s * a.x, s * a.y, s * a.z, s * a.w);
-    z[i] = make_float4(s * b.x, s * b.y, s * b.z, s * b.w);
+                            float4* __restrict__ e, const double* __restrict__ dots, int k,
+                            const double* __restrict__ n2p, long n, CGScalars* s, unsigned* ticket) {
+  if (s->done) return;
+  const double n2 = *n2p;
+  const double wr_re = dots[2 * k], wr_im = dots[2 * k + 1];
+  const bool ok = n2 > 0;
+  if (ok) {
+    const float2 al = make_float2((float)(wr_re / n2), (float)(wr_im / n2));
+    const float sc = (float)(1.0 / sqrt(n2));
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+      float4 a = w[i], b = z[i], rr = r[i], ee = e[i];
+      rr.x -= al.x * a.x - al.y * a.y;
+      rr.y -= al.x * a.y + al.y * a.x;
+      rr.z -= al.x * a.z - al.y * a.w;
+      rr.w -= al.x * a.w + al.y * a.z;
+      ee.x += al.x * b.x - al.y * b.y;
+      ee.y += al.x * b.y + al.y * b.x;
+      ee.z += al.x * b.z - al.y * b.w;
+      ee.w += al.x * b.w + al.y * b.z;
+      r[i] = rr;
+      e[i] = ee;
+      w[i] = make_float4(sc * a.x, sc * a.y, sc * a.z, sc * a.w);
+      z[i] = make_float4(sc * b.x, sc * b.y, sc * b.z, sc * b.w);
+    }
   }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    *ticket = 0u;
+    if (ok) {
+      double rr = s->rr - (wr_re * wr_re + wr_im * wr_im) / n2;
+      s->rr = rr > 0 ? rr : 0.0;
+      s->iter += 1;
+    }
+    if (!ok || s->rr < s->stop_rr) s->done = 1;
+  }
+}
+
+// z = r (GCR: no preconditioner) unless done
+__global__ void k_fgcr_copy(float4* __restrict__ z, const float4* __restrict__ r, long n, const CGScalars* s) {
+  if (s->done) return;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) z[i] = r[i];
+}
+
+// start of a cycle: rr = |r|^2 (already in s->rr), stop = max(delta^2 rr, floor)
+__global__ void k_fgcr_start(CGScalars* s, double delta2, double floor_rr) {
+  const double st = delta2 * s->rr;
+  s->stop_rr = st > floor_rr ? st : floor_rr;
+  s->done = 0;
+  s->iter = 0;
 }
 
 __global__ void k_scale32(float4* x, float a, long n) {
@@ -464,6 +516,7 @@ struct pfmp_nn {
   std::vector<void*> act16;      // FP16 scaled inputs of each layer
   float* sigma = nullptr;        // device scalar: 1 / rms of the network input
   int* err = nullptr;            // device error flag of the tensor-core kernel
+  long long id = 0;              // unique per network (keys the FGCR cycle graphs)
 };
 
 namespace pfmp {
@@ -473,10 +526,12 @@ static size_t csz(const pfmp_nn* N) { return N->prec == PFMP_F64 ? sizeof(double
 bool nn_tc_supported(int cin, int cout);
 size_t nn_tc_packed_bytes(int cin, int cout);
 void nn_tc_pack(pfmp_ctx* c, int cin, int cout, const void* W, void* Bp);
-void nn_tc_scale(pfmp_ctx* c, const void* in_even_f32, float* sigma_dev);
+void nn_tc_scale(pfmp_ctx* c, const void* in_even_f32, float* sigma_dev, const int* skip);
 void nn_tc_layer(pfmp_ctx* c, int cin, int cout, bool last, const void* Bp, const void* in, void* out,
-                 const float* sigma, int* err);
-void nn_tc_embed(pfmp_ctx* c, const void* in_even_f32, const float* sigma, void* act16);
+                 const float* sigma, int* err, const int* skip);
+void nn_tc_embed(pfmp_ctx* c, const void* in_even_f32, const float* sigma, void* act16, const int* skip);
+void nn_tc_extract(pfmp_ctx* c, const void* act32, void* out_even_f32, const int* skip);
+void nn_tc_init();
 
 void nn_destroy(pfmp_nn* N) {
   if (!N) return;
@@ -495,9 +550,11 @@ pfmp_nn* nn_create(pfmp_ctx* c, int nl, const int* ch, int prec) {
   PFMP_REQUIRE(nl >= 1 && nl <= 16 && ch, PFMP_E_INVALID, "need 1..16 layers");
   PFMP_REQUIRE(ch[0] == 1 && ch[nl] == 1, PFMP_E_INVALID, "the network maps one spinor to one spinor");
   PFMP_REQUIRE(prec == PFMP_F32 || prec == PFMP_F64, PFMP_E_INVALID, "bad precision");
+  static long long next_id = 0;
   pfmp_nn* N = new pfmp_nn();
   N->ctx = c;
   N->prec = prec;
+  N->id = ++next_id;
   try {
     for (int l = 0; l <= nl; ++l) {
       PFMP_REQUIRE(ch[l] >= 1 && ch[l] <= 64, PFMP_E_INVALID, "channels must be in 1..64");
@@ -609,21 +666,28 @@ static bool layer_site(pfmp_ctx* c, const void* W, int cin, const void* in, void
   return true;
 }
 
-// tensor-core forward pass: in (even FP32) -> act[L] (FP32), through FP16 activations
-static void forward_tc(pfmp_nn* N, const void* in) {
-  pfmp_ctx* c = N->ctx;
-  const int L = (int)N->W.size();
+// packed FP16 weights up to date and kernel attributes set (outside any stream capture)
+static void tc_prepare(pfmp_nn* N) {
   if (!N->packed) {
-    for (int l = 0; l < L; ++l) nn_tc_pack(c, N->ch[l], N->ch[l + 1], N->W[l], N->Bp[l]);
+    for (size_t l = 0; l < N->W.size(); ++l) nn_tc_pack(N->ctx, N->ch[l], N->ch[l + 1], N->W[l], N->Bp[l]);
     N->packed = true;
   }
-  nn_tc_scale(c, in, N->sigma);
-  nn_tc_embed(c, in, N->sigma, N->act16[0]);
+  nn_tc_init();
+}
+
+// tensor-core forward pass: in (even FP32) -> out (even FP32) through FP16 activations;
+// every kernel returns at once while *skip is set (FGCR after convergence)
+static void forward_tc(pfmp_nn* N, void* out, const void* in, const int* skip) {
+  pfmp_ctx* c = N->ctx;
+  const int L = (int)N->W.size();
+  nn_tc_scale(c, in, N->sigma, skip);
+  nn_tc_embed(c, in, N->sigma, N->act16[0], skip);
   for (int l = 0; l < L; ++l) {
     const bool last = l == L - 1;
     nn_tc_layer(c, N->ch[l], N->ch[l + 1], last, N->Bp[l], N->act16[l], last ? N->act[L] : N->act16[l + 1],
-                N->sigma, N->err);
+                N->sigma, N->err, skip);
   }
+  nn_tc_extract(c, N->act[L], out, skip);
 }
 
 template <typename T>
@@ -644,8 +708,9 @@ static void forward_t(pfmp_nn* N) {
   }
 }
 
-// out_even = N(in_even); io precision prec_io (device layout of the library)
-void nn_apply(pfmp_nn* N, void* out, const void* in, int prec_io) {
+// out_even = N(in_even); io precision prec_io (device layout of the library); skip: see
+// forward_tc (tensor-core path only)
+static void nn_apply_skip(pfmp_nn* N, void* out, const void* in, int prec_io, const int* skip) {
   pfmp_ctx* c = N->ctx;
   const Geom& g = c->g;
   const int L = (int)N->W.size();
@@ -662,15 +727,16 @@ void nn_apply(pfmp_nn* N, void* out, const void* in, int prec_io) {
       k_nn_extract<double, PFMP_F32><<<nblocks(g.Vh), kBlock, 0, c->stream>>>(g, (const double2*)N->act[L], (float4*)out);
   } else {
     if (N->tc && prec_io == PFMP_F32) {
-      forward_tc(N, in);
-    } else {
-      if (prec_io == PFMP_F64)
-        k_nn_embed<float, PFMP_F64><<<nblocks(g.V), kBlock, 0, c->stream>>>(g, (const double2*)in, (float2*)N->act[0]);
-      else
-        k_nn_embed<float, PFMP_F32><<<nblocks(g.V), kBlock, 0, c->stream>>>(g, (const float4*)in, (float2*)N->act[0]);
-      PFMP_CHECK_LAUNCH();
-      forward_t<float>(N);
+      tc_prepare(N);
+      forward_tc(N, out, in, skip);
+      return;
     }
+    if (prec_io == PFMP_F64)
+      k_nn_embed<float, PFMP_F64><<<nblocks(g.V), kBlock, 0, c->stream>>>(g, (const double2*)in, (float2*)N->act[0]);
+    else
+      k_nn_embed<float, PFMP_F32><<<nblocks(g.V), kBlock, 0, c->stream>>>(g, (const float4*)in, (float2*)N->act[0]);
+    PFMP_CHECK_LAUNCH();
+    forward_t<float>(N);
     if (prec_io == PFMP_F64)
       k_nn_extract<float, PFMP_F64><<<nblocks(g.Vh), kBlock, 0, c->stream>>>(g, (const float2*)N->act[L], (double2*)out);
     else
@@ -678,6 +744,8 @@ void nn_apply(pfmp_nn* N, void* out, const void* in, int prec_io) {
   }
   PFMP_CHECK_LAUNCH();
 }
+
+void nn_apply(pfmp_nn* N, void* out, const void* in, int prec_io) { nn_apply_skip(N, out, in, prec_io, nullptr); }
 
 // residual loss on even device fields of the network precision:
 // r = K y - b, L = |r|^2 / |b|^2, dL/dy = 2 K r / |b|^2 (K Hermitian)
@@ -827,15 +895,15 @@ double nn_train(pfmp_nn* N, pfmp_op* op, int kind, int npairs, const void* const
 }
 
 // ------------------------------------------------------------------ FGCR
-static std::complex<double> cdot_sync(pfmp_ctx* c, int prec, const void* x, const void* y) {
-  blas_cdot(c, prec, x, y, c->d_sums);
-  PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  PFMP_CUDA(cudaStreamSynchronize(c->stream));
-  return {c->h_sums[0], c->h_sums[1]};
-}
-
 struct FgcrWork {
   int restart = 0, grid = 0;
+  CGScalars* scal = nullptr;   // device: rr, stop_rr, done, iter of the current cycle
+  CGScalars* h_scal = nullptr; // pinned host mirror
+  cudaGraphExec_t exec = nullptr;  // one cycle of `glen` iterations, keyed by the network
+  long long gkey = -1;
+  int glen = 0;
+  long long gkernels = 0;
+  cudaStream_t cap = nullptr;
   std::vector<float4*> Z, W;
   float4 *r = nullptr, *e = nullptr, *z = nullptr, *w = nullptr;
   float4** dW = nullptr;
@@ -844,6 +912,10 @@ struct FgcrWork {
   unsigned* ticket = nullptr;
   double* out = nullptr;
   ~FgcrWork() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+    dev_free(scal);
+    if (h_scal) cudaFreeHost(h_scal);
     for (auto p : Z) dev_free(p);
     for (auto p : W) dev_free(p);
     dev_free(r);
@@ -889,7 +961,9 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
       wp->part = (double*)dev_alloc((size_t)fgrid * 34 * sizeof(double));
       wp->ticket = (unsigned*)dev_alloc(sizeof(unsigned));
       PFMP_CUDA(cudaMemset(wp->ticket, 0, sizeof(unsigned)));
-      wp->out = (double*)dev_alloc(34 * sizeof(double));
+      wp->out = (double*)dev_alloc(40 * sizeof(double));
+      wp->scal = (CGScalars*)dev_alloc(sizeof(CGScalars));
+      PFMP_CUDA(cudaMallocHost(&wp->h_scal, sizeof(CGScalars)));
     } catch (...) {
       delete wp;
       throw;
@@ -910,52 +984,86 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
   *true_res = 0;
   if (bb == 0) return PFMP_OK;
   void* r64 = op->cg64[0];
-  void* Ax = op->cg64[2];
   PFMP_CUDA(cudaMemcpyAsync(r64, b, b64, cudaMemcpyDeviceToDevice, c->stream));
   double res = 1.0, prev = 1.0;
   int stall = 0;
+  const bool use_graph = !c->prof.on;
+  if (nn && nn->tc) tc_prepare(nn);
   while (*iters < max_iter) {
-    // inner FGCR(restart) in FP32 on K e = r
+    // inner FGCR(restart) in FP32 on K e = r, one device-driven cycle: the launches of
+    // `len` iterations go out without a host round trip (as one CUDA graph when the
+    // cycle has the full length) and the host reads the scalars once at the end
     blas_copy(c, wk.r, PFMP_F32, r64, PFMP_F64);
     blas_zero(c, PFMP_F32, wk.e);
-    const double rn0 = std::sqrt(std::max(cdot_sync(c, PFMP_F32, wk.r, wk.r).real(), 0.0));
-    double rr = rn0 * rn0;
-    for (int k = 0; k < restart && *iters < max_iter; ++k) {
-      float4* z = wk.Z[k];
-      float4* w = wk.W[k];
-      if (nn)
-        nn_apply(nn, z, wk.r, PFMP_F32);
-      else
-        PFMP_CUDA(cudaMemcpyAsync(z, wk.r, b32, cudaMemcpyDeviceToDevice, c->stream));
-      kop(op, PFMP_F32, w, z, nullptr, nullptr);
-      *kapply += 1;
-      // classical Gram-Schmidt against the orthonormal W_j: all <W_j, w> and <w, r> in
-      // one pass (r is orthogonal to every W_j, so <w', r> = <w, r>)
-      k_fgcr_dots<<<fgrid, kBlock, 0, c->stream>>>(wk.dW, k, w, wk.r, n32, wk.part, wk.ticket, wk.out);
-      PFMP_CHECK_LAUNCH();
-      double hv[34];
-      PFMP_CUDA(cudaMemcpyAsync(c->h_sums, wk.out, (2 * k + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      PFMP_CUDA(cudaStreamSynchronize(c->stream));
-      for (int j = 0; j < 2 * k + 2; ++j) hv[j] = c->h_sums[j];
-      CoefList cl;
-      for (int j = 0; j < k; ++j) cl.h[j] = make_float2((float)hv[2 * j], (float)hv[2 * j + 1]);
-      const std::complex<double> wr(hv[2 * k], hv[2 * k + 1]);
-      k_fgcr_orth<<<fgrid, kBlock, 0, c->stream>>>(wk.dW, wk.dZ, k, cl, w, z, n32, wk.part, wk.ticket, wk.out);
-      PFMP_CHECK_LAUNCH();
-      PFMP_CUDA(cudaMemcpyAsync(c->h_sums, wk.out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      PFMP_CUDA(cudaStreamSynchronize(c->stream));
-      const double n2 = c->h_sums[0];
-      PFMP_REQUIRE(std::isfinite(n2), PFMP_E_NAN, "FGCR direction is not finite");
-      if (!(n2 > 0)) break;
-      const std::complex<double> al = wr / n2;
-      k_fgcr_step<<<fgrid, kBlock, 0, c->stream>>>(w, z, wk.r, wk.e, make_float2((float)al.real(), (float)al.imag()),
-                                                   (float)(1.0 / std::sqrt(n2)), n32);
-      PFMP_CHECK_LAUNCH();
-      *iters += 1;
-      rr = std::max(rr - std::norm(wr) / n2, 0.0);  // |r - <w^,r> w^|^2
-      const double rn = std::sqrt(rr);
-      if (rn < delta * rn0 || rn * rn < 0.25 * tol * tol * bb) break;
+    blas_norm2(c, PFMP_F32, wk.r, &wk.scal->rr);
+    k_fgcr_start<<<1, 1, 0, c->stream>>>(wk.scal, delta * delta, 0.25 * tol * tol * bb);
+    PFMP_CHECK_LAUNCH();
+    const int len = std::min(restart, max_iter - *iters);
+    auto launch_cycle = [&](int n_it) {
+      for (int k = 0; k < n_it; ++k) {
+        float4* z = wk.Z[k];
+        float4* w = wk.W[k];
+        if (nn) {
+          nn_apply_skip(nn, z, wk.r, PFMP_F32, &wk.scal->done);
+        } else {
+          k_fgcr_copy<<<fgrid, kBlock, 0, c->stream>>>(z, wk.r, n32, wk.scal);
+          PFMP_CHECK_LAUNCH();
+        }
+        kop(op, PFMP_F32, w, z, nullptr, wk.scal);
+        k_fgcr_dots<<<fgrid, kBlock, 0, c->stream>>>(wk.dW, k, w, wk.r, n32, wk.part, wk.ticket, wk.out, wk.scal);
+        PFMP_CHECK_LAUNCH();
+        k_fgcr_orth<<<fgrid, kBlock, 0, c->stream>>>(wk.dW, wk.dZ, k, wk.out, w, z, n32, wk.part, wk.ticket,
+                                                     wk.out + 36, wk.scal);
+        PFMP_CHECK_LAUNCH();
+        k_fgcr_step<<<fgrid, kBlock, 0, c->stream>>>(w, z, wk.r, wk.e, wk.out, k, wk.out + 36, n32, wk.scal,
+                                                     wk.ticket);
+        PFMP_CHECK_LAUNCH();
+      }
+    };
+    const long long key = nn ? nn->id * 2 + (nn->tc ? 1 : 0) : 0;
+    const long long kap0 = op->kapply;
+    if (use_graph && len == restart) {
+      if (!wk.exec || wk.gkey != key || wk.glen != len) {
+        if (wk.exec) {
+          cudaGraphExecDestroy(wk.exec);
+          wk.exec = nullptr;
+        }
+        if (!wk.cap) PFMP_CUDA(cudaStreamCreateWithFlags(&wk.cap, cudaStreamNonBlocking));
+        cudaStream_t keep = c->stream;
+        cudaGraph_t graph = nullptr;
+        PFMP_CUDA(cudaStreamBeginCapture(wk.cap, cudaStreamCaptureModeThreadLocal));
+        c->stream = wk.cap;
+        const long long n0 = launch_count();
+        try {
+          launch_cycle(len);
+        } catch (...) {
+          c->stream = keep;
+          cudaStreamEndCapture(wk.cap, &graph);
+          if (graph) cudaGraphDestroy(graph);
+          throw;
+        }
+        c->stream = keep;
+        wk.gkernels = launch_count() - n0;
+        count_launches(-wk.gkernels);  // captured, not launched
+        PFMP_CUDA(cudaStreamEndCapture(wk.cap, &graph));
+        cudaError_t e = cudaGraphInstantiate(&wk.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        PFMP_CUDA(e);
+        wk.gkey = key;
+        wk.glen = len;
+      }
+      PFMP_CUDA(cudaGraphLaunch(wk.exec, c->stream));
+      count_launches(wk.gkernels);
+    } else {
+      launch_cycle(len);
     }
+    PFMP_CUDA(cudaMemcpyAsync(wk.h_scal, wk.scal, sizeof(CGScalars), cudaMemcpyDeviceToHost, c->stream));
+    PFMP_CUDA(cudaStreamSynchronize(c->stream));
+    PFMP_REQUIRE(std::isfinite(wk.h_scal->rr), PFMP_E_NAN, "FGCR residual is not finite");
+    const int done_it = wk.h_scal->iter;
+    op->kapply = kap0 + done_it;  // K applications the device actually did
+    *iters += done_it;
+    *kapply += done_it;
     // outer correction in FP64 storage, true residual in double-float
     blas_add_lo(c, x, wk.e);
     *kapply += 1;

@@ -142,7 +142,9 @@ __global__ void k_pack_b(const float2* __restrict__ W, __half* __restrict__ B) {
 }
 
 // sigma = sqrt(n) / |in| (1 for a zero input) of an even FP32 field
-__global__ void k_rms_scale(const float4* __restrict__ in, int Vh, ReduceBuf rb, float* sigma) {
+__global__ void k_rms_scale(const float4* __restrict__ in, int Vh, ReduceBuf rb, float* sigma,
+                            const int* __restrict__ skip) {
+  if (skip && *skip) return;
   double s[1] = {0.0};
   const long n = 6L * Vh;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -265,7 +267,8 @@ __device__ __forceinline__ void gather_stage(const Geom& g, const float4* __rest
 // network input: sigma * (even FP32 field [6][Vh] float4) on even sites, 0 on odd sites,
 // as FP16 complex [12][V] (lexicographic sites)
 __global__ void k_embed16(Geom g, const float4* __restrict__ src, const float* __restrict__ sigma_p,
-                          __half2* __restrict__ dst) {
+                          __half2* __restrict__ dst, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int r = s, x[4];
@@ -286,12 +289,30 @@ __global__ void k_embed16(Geom g, const float4* __restrict__ src, const float* _
   }
 }
 
+// network output: even sites of the FP32 activation [12][V] -> even FP32 field [6][Vh]
+__global__ void k_extract32(Geom g, const float2* __restrict__ src, float4* __restrict__ dst,
+                            const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.Vh) return;
+  int x[4];
+  cb_coords(g, cb, 0, x);
+  const size_t s = (size_t)lex_index(g, x);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float2 a = src[(size_t)(2 * k) * g.V + s], b = src[(size_t)(2 * k + 1) * g.V + s];
+    dst[(size_t)k * g.Vh + cb] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
 // OUT16: FP16 scaled output for the next layer; otherwise FP32 output divided by sigma
 template <int CIN, int COUT, bool OUT16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_nn_layer_tc(Geom g, const float4* __restrict__ U32, const __half* __restrict__ Bg, const __half2* __restrict__ in,
-                  void* __restrict__ out, const float* __restrict__ sigma_p, int* __restrict__ err) {
+                  void* __restrict__ out, const float* __restrict__ sigma_p, int* __restrict__ err,
+                  const int* __restrict__ skip) {
   using S = Shape<CIN, COUT>;
+  if (skip && *skip) return;  // block-uniform: nothing allocated yet
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tmem_slot;
   __shared__ __align__(8) uint64_t bar_w, bar_a[2];
@@ -469,16 +490,22 @@ void nn_tc_pack(pfmp_ctx* c, int cin, int cout, const void* W, void* Bp) {
     pack_t<8, 8>(c, W, Bp);
 }
 
-void nn_tc_scale(pfmp_ctx* c, const void* in_even_f32, float* sigma_dev) {
+void nn_tc_scale(pfmp_ctx* c, const void* in_even_f32, float* sigma_dev, const int* skip) {
   const long n = 6L * c->g.Vh;
   long b = (n + kBlock - 1) / kBlock;
   const int grid = (int)(b < 152 * 4 ? b : 152 * 4);
-  tc::k_rms_scale<<<grid, kBlock, 0, c->stream>>>((const float4*)in_even_f32, c->g.Vh, c->rb, sigma_dev);
+  tc::k_rms_scale<<<grid, kBlock, 0, c->stream>>>((const float4*)in_even_f32, c->g.Vh, c->rb, sigma_dev, skip);
+  PFMP_CHECK_LAUNCH();
+}
+
+void nn_tc_extract(pfmp_ctx* c, const void* act32, void* out_even_f32, const int* skip) {
+  tc::k_extract32<<<nblocks(c->g.Vh, 256), 256, 0, c->stream>>>(c->g, (const float2*)act32, (float4*)out_even_f32,
+                                                                 skip);
   PFMP_CHECK_LAUNCH();
 }
 
 template <int CIN, int COUT, bool OUT16>
-static void layer_t(pfmp_ctx* c, const void* Bp, const void* in, void* out, const float* sigma, int* err) {
+static int layer_init() {
   using S = tc::Shape<CIN, COUT>;
   static int sms = 0;
   if (!sms) {
@@ -488,28 +515,43 @@ static void layer_t(pfmp_ctx* c, const void* Bp, const void* in, void* out, cons
     PFMP_CUDA(cudaGetDevice(&dev));
     PFMP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
+  return sms;
+}
+
+// kernel attributes set outside any stream capture
+void nn_tc_init() {
+  layer_init<1, 8, true>();
+  layer_init<8, 8, true>();
+  layer_init<8, 1, false>();
+}
+
+template <int CIN, int COUT, bool OUT16>
+static void layer_t(pfmp_ctx* c, const void* Bp, const void* in, void* out, const float* sigma, int* err,
+                    const int* skip) {
+  using S = tc::Shape<CIN, COUT>;
+  const int sms = layer_init<CIN, COUT, OUT16>();
   const int ntiles = (c->g.V + tc::kM - 1) / tc::kM;
   const int grid = ntiles < sms ? ntiles : sms;
   tc::k_nn_layer_tc<CIN, COUT, OUT16><<<grid, tc::kThreads, S::SMEM, c->stream>>>(
-      c->g, c->U32, (const __half*)Bp, (const __half2*)in, out, sigma, err);
+      c->g, c->U32, (const __half*)Bp, (const __half2*)in, out, sigma, err, skip);
   PFMP_CHECK_LAUNCH();
 }
 
 // in: FP16 scaled activations; out: FP16 scaled (last = false) or FP32 / sigma (last)
 void nn_tc_layer(pfmp_ctx* c, int cin, int cout, bool last, const void* Bp, const void* in, void* out,
-                 const float* sigma, int* err) {
+                 const float* sigma, int* err, const int* skip) {
   PFMP_REQUIRE(!(last && cout == 8) && !(!last && cout == 1), PFMP_E_INVALID, "tensor-core layer sequence");
   if (cin == 1)
-    layer_t<1, 8, true>(c, Bp, in, out, sigma, err);
+    layer_t<1, 8, true>(c, Bp, in, out, sigma, err, skip);
   else if (cout == 1)
-    layer_t<8, 1, false>(c, Bp, in, out, sigma, err);
+    layer_t<8, 1, false>(c, Bp, in, out, sigma, err, skip);
   else
-    layer_t<8, 8, true>(c, Bp, in, out, sigma, err);
+    layer_t<8, 8, true>(c, Bp, in, out, sigma, err, skip);
 }
 
-void nn_tc_embed(pfmp_ctx* c, const void* in_even_f32, const float* sigma, void* act16) {
+void nn_tc_embed(pfmp_ctx* c, const void* in_even_f32, const float* sigma, void* act16, const int* skip) {
   tc::k_embed16<<<nblocks(c->g.V, 256), 256, 0, c->stream>>>(c->g, (const float4*)in_even_f32, sigma,
-                                                             (__half2*)act16);
+                                                             (__half2*)act16, skip);
   PFMP_CHECK_LAUNCH();
 }
 
