@@ -248,50 +248,78 @@ __device__ __forceinline__ int plane_index(int mu, int nu) {
   return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
 
-// F[p] += (1/8) Re tr(T_a [U X_above - Y_below U^dag]) summed over the three planes
+// F[p] += (1/8) Re tr(T_a [U X_above - Y_below U^dag]) summed over the three planes,
+// one thread per (site, mu).  With V1 = U_nu(z+mu), V2 = U_mu(z+nu)^dag, V3 = U_nu(z)^dag,
+// W1 = U_nu(z-nu)^dag, W2 = U_mu(z-nu), W3 = U_nu(z-nu+mu) and H_y the clover insertion
+// at site y:
+//   U X = U H_{z+mu} V1 V2 V3 + U V1 H_{z+mu+nu} V2 V3 + U V1 V2 H_{z+nu} V3 + U V1 V2 V3 H_z
+//   Y U^dag = H_z W1 W2 W3 U^dag + W1 H_{z-nu} W2 W3 U^dag + W1 W2 H_{z-nu+mu} W3 U^dag
+//             + W1 W2 W3 H_{z+mu} U^dag
+// both summed Horner-fashion (U X from the left with the running prefix U V1 .. Vk,
+// Y U^dag from the right with the running suffix Wk .. W3 U^dag), which keeps three
+// 3x3 matrices live instead of a dozen.
 __global__ void k_clover_force(double* F, const double2* U64, const double* Hc, Geom g, int p) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mu = blockIdx.y;
   if (cb >= g.Vh) return;
   int z[4];
   cb_coords(g, cb, p, z);
-  for (int mu = 0; mu < 4; ++mu) {
-    const Mat3<double> U = mlink(U64, g, z, mu);
-    Mat3<double> Zs = mat_zero<double>();
-    for (int nu = 0; nu < 4; ++nu) {
-      if (nu == mu) continue;
-      const int pl = plane_index(mu, nu);
-      const double sg = mu < nu ? 1.0 : -1.0;
-      int zpm[4], zpmpn[4], zpn[4], zmn[4], zmnpm[4];
-      shift(g, z, mu, 1, zpm);
-      shift(g, zpm, nu, 1, zpmpn);
-      shift(g, z, nu, 1, zpn);
-      shift(g, z, nu, -1, zmn);
-      shift(g, zmn, mu, 1, zmnpm);
+  const Mat3<double> U = mlink(U64, g, z, mu);
+  Mat3<double> Zs = mat_zero<double>();
+#pragma unroll 1
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    const int pl = plane_index(mu, nu);
+    const double sg = mu < nu ? 1.0 : -1.0;
+    int zpm[4], zpmpn[4], zpn[4], zmn[4], zmnpm[4];
+    shift(g, z, mu, 1, zpm);
+    shift(g, zpm, nu, 1, zpmpn);
+    shift(g, z, nu, 1, zpn);
+    shift(g, z, nu, -1, zmn);
+    shift(g, zmn, mu, 1, zmnpm);
+    // upper: R = sum over the four leaves, L = running prefix U V1 .. Vk
+    Mat3<double> L = U;
+    Mat3<double> R = matmul(L, load_H(Hc, g, zpm, pl, sg));
+    {
       const Mat3<double> V1 = mlink(U64, g, zpm, nu);
-      const Mat3<double> V2 = dagger(mlink(U64, g, zpn, mu));
-      const Mat3<double> V3 = dagger(mlink(U64, g, z, nu));
-      const Mat3<double> W1 = dagger(mlink(U64, g, zmn, nu));
-      const Mat3<double> W2 = mlink(U64, g, zmn, mu);
-      const Mat3<double> W3 = mlink(U64, g, zmnpm, nu);
-      const Mat3<double> V12 = matmul(V1, V2), V23 = matmul(V2, V3), V123 = matmul(V12, V3);
-      const Mat3<double> W12 = matmul(W1, W2), W23 = matmul(W2, W3), W123 = matmul(W12, W3);
-      Mat3<double> X = matmul(load_H(Hc, g, zpm, pl, sg), V123);
-      X = mat_add(X, matmul(matmul(V1, load_H(Hc, g, zpmpn, pl, sg)), V23));
-      X = mat_add(X, matmul(matmul(V12, load_H(Hc, g, zpn, pl, sg)), V3));
-      X = mat_add(X, matmul(V123, load_H(Hc, g, z, pl, sg)));
-      Mat3<double> Y = matmul(load_H(Hc, g, z, pl, sg), W123);
-      Y = mat_add(Y, matmul(matmul(W1, load_H(Hc, g, zmn, pl, sg)), W23));
-      Y = mat_add(Y, matmul(matmul(W12, load_H(Hc, g, zmnpm, pl, sg)), W3));
-      Y = mat_add(Y, matmul(W123, load_H(Hc, g, zpm, pl, sg)));
-      const Mat3<double> A = matmul(U, X), B = matmul_nd(Y, U);
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) Zs.m[i][j] = Zs.m[i][j] + A.m[i][j] - B.m[i][j];
+      L = matmul(L, V1);
+      R = mat_add(matmul(R, V1), matmul(L, load_H(Hc, g, zpmpn, pl, sg)));
     }
-    cplx<double> t[8];
-    tr_lambda(Zs, t);
-    // (1/8) Re tr(T_a Z) = (1/16) Re tr(lambda_a Z)
-    for (int a = 0; a < 8; ++a) fptr(F, g, p, mu, a)[cb] += 0.0625 * t[a].re;
+    {
+      const Mat3<double> V2 = dagger(mlink(U64, g, zpn, mu));
+      L = matmul(L, V2);
+      R = mat_add(matmul(R, V2), matmul(L, load_H(Hc, g, zpn, pl, sg)));
+    }
+    {
+      const Mat3<double> V3 = dagger(mlink(U64, g, z, nu));
+      L = matmul(L, V3);
+      R = mat_add(matmul(R, V3), matmul(L, load_H(Hc, g, z, pl, sg)));
+    }
+    // lower: Q = sum over the four leaves, M = running suffix Wk .. W3 U^dag
+    Mat3<double> M = dagger(U);
+    Mat3<double> Q = matmul(load_H(Hc, g, zpm, pl, sg), M);
+    {
+      const Mat3<double> W3 = mlink(U64, g, zmnpm, nu);
+      M = matmul(W3, M);
+      Q = mat_add(matmul(W3, Q), matmul(load_H(Hc, g, zmnpm, pl, sg), M));
+    }
+    {
+      const Mat3<double> W2 = mlink(U64, g, zmn, mu);
+      M = matmul(W2, M);
+      Q = mat_add(matmul(W2, Q), matmul(load_H(Hc, g, zmn, pl, sg), M));
+    }
+    {
+      const Mat3<double> W1 = dagger(mlink(U64, g, zmn, nu));
+      M = matmul(W1, M);
+      Q = mat_add(matmul(W1, Q), matmul(load_H(Hc, g, z, pl, sg), M));
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Zs.m[i][j] = Zs.m[i][j] + R.m[i][j] - Q.m[i][j];
   }
+  cplx<double> t[8];
+  tr_lambda(Zs, t);
+  // (1/8) Re tr(T_a Z) = (1/16) Re tr(lambda_a Z)
+  for (int a = 0; a < 8; ++a) fptr(F, g, p, mu, a)[cb] += 0.0625 * t[a].re;
 }
 
 // F += (beta/3) Im tr(T_a U S) = (beta/6) Im tr(lambda_a U S)
@@ -342,7 +370,8 @@ void clover_insert_det(pfmp_op* op, double* Hc, double coef) {
 }
 void clover_force(pfmp_ctx* c, double* F, const double* Hc) {
   for (int p = 0; p < 2; ++p) {
-    k_clover_force<<<nblocks(c->g.Vh, 64), 64, 0, c->stream>>>(F, c->U64, Hc, c->g, p);
+    dim3 grid(nblocks(c->g.Vh, 64), 4);
+    k_clover_force<<<grid, 64, 0, c->stream>>>(F, c->U64, Hc, c->g, p);
     PFMP_CHECK_LAUNCH();
   }
 }
