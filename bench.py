@@ -282,6 +282,8 @@ def run_ours(args, rank, world):
     e2e_ms = allmax(statistics.mean(e2e), world) / world
     learn = None if args.no_learned else learned(capi, stream, l2_flush, args, ctx, op, b, x)
     traj = trajectory_4x4x4x4(capi, stream)
+    traj_big = None if args.no_big_trajectory else guarded(trajectory_16x16x16x32, capi, stream)
+    tuning = None if args.no_tuning else guarded(tuning_4x4x4x4, capi, stream)
     capi.pfmp_op_destroy(op)
     capi.pfmp_ctx_destroy(ctx)
 
@@ -306,6 +308,8 @@ def run_ours(args, rank, world):
         "roofline": roof,
         "learned": learn,
         "trajectory_4x4x4x4": traj,
+        "trajectory_16x16x16x32": traj_big,
+        "tuning_4x4x4x4": tuning,
         "batched": batched,
         "hop_in_solve": {"launches": n_hop, "avg_us": hop_ms * 1e3 / max(n_hop, 1), "algorithmic_gbs": hop_gbs_l2,
                          "note": "16^3x32 FP32 working set (~75 MB) is L2-resident inside a solve"},
@@ -479,6 +483,106 @@ def learned(capi, stream, l2_flush, args, ctx, op, b, x):
     return out
 
 
+def guarded(fn, *a):
+    """A secondary measurement that must not take the headline line down with it."""
+    try:
+        return fn(*a)
+    except Exception as e:  # reported in the JSON line instead
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
+def trajectory_16x16x16x32(capi, stream):
+    """One PF-MP trajectory on the paper's lattice size, 16^3x32 (synthetic field eps 0.3,
+    seed 1; beta 5.5, c_sw 1, kappa 0.125, kappa' 0.110, order-8 filter, (mu, nu) = (1.2,
+    0.9)), the action's CG in mixed precision and the multi-shift in FP64, all solves to
+    1e-10; 2-level 2MN, 2 coarse (correction + Hasenbusch ratio) x 4 fine (gauge, clover
+    determinant, filter) steps over tau = 0.1.  Wall time of the whole trajectory
+    (heatbath, both Hamiltonians, MD, accept/reject) with per-term K counts and forces."""
+    import torch
+
+    import pfmp_inputs as pin
+
+    dims = (16, 16, 16, 32)
+    V = 16 * 16 * 16 * 32
+    ctx = capi.pfmp_ctx_create(dims, -1, stream.cuda_stream)
+    h = torch.tensor(np.ascontiguousarray(pin.gauge_algebra(dims, 1)).reshape(-1), device="cuda")
+    torch.cuda.synchronize()
+    capi.pfmp_gauge_from_algebra(ctx, h, 0.3, capi.PFMP_DEVICE)
+    d = capi.ActionDef()
+    d.beta, d.csw, d.nkappa = 5.5, 1.0, 2
+    d.kappa[0], d.kappa[1] = 0.125, 0.110
+    d.mu, d.nu, d.tol, d.max_iter = 1.2, 0.9, 1e-10, 20000
+    d.solver = capi.PFMP_SOLVER_CG_MIXED
+    capi.pfmp_action_scheme(capi.PFMP_SCHEME_PFMP, 0, 8, d)
+    A = capi.pfmp_action_create_def(ctx, d)
+    lam = 0.1931833275037836
+    T, S = capi.pfmp_schedule_merge([capi.pfmp_schedule_2mn(2, 0.1, lam), capi.pfmp_schedule_2mn(4, 0.1, lam)])
+    xi = np.concatenate([np.ascontiguousarray(pin.spinor(dims, 10 + i)).view(np.float64).reshape(-1) for i in range(3)])
+    mom = np.ascontiguousarray(pin.momenta(dims, 5)).reshape(-1)
+    levels = [1, 1, 1, 0, 0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = capi.pfmp_trajectory(A, T, S, levels, mom, xi, float(pin.uniform(6)[0]))
+    ms = (time.perf_counter() - t0) * 1e3
+    names = ["gauge", "det", "filter", "filtercorr", "ratio"]
+    out = {"ms": ms, "dH": info.dH, "accepted": bool(info.accepted), "k_apply": int(info.k_apply),
+           "force_evals": int(info.force_evals), "steps": len(T), "sites": V,
+           "per_term": {n: {"k_apply": int(info.k_apply_term[t]), "forces": int(info.nforce[t]),
+                            "fmax": info.fmax[t], "favg": info.favg[t]} for t, n in enumerate(names)}}
+    capi.pfmp_action_destroy(A)
+    capi.pfmp_ctx_destroy(ctx)
+    return out
+
+
+def tuning_4x4x4x4(capi, stream, ntraj=6):
+    """The paper's step-size method (Sec. 2.4, Sec. 3.1) on the 4^4 parity configuration:
+    one PF-MP trajectory (2MN 4 x 8 steps, tau 0.5) measures the maximal force of each
+    level, F_l h_l = const gives the step counts (4 on the level with the smaller force),
+    then ntraj trajectories from the same field with fresh momenta and noise give P_acc,
+    N_mat and C = N_mat / P_acc with the autocorrelation-corrected errors (tau_int 12.5)."""
+    import pfmp_inputs as pin
+
+    dims = (4, 4, 4, 4)
+    V = 256
+    ctx = capi.pfmp_ctx_create(dims, -1, stream.cuda_stream)
+    capi.pfmp_gauge_from_algebra(ctx, np.ascontiguousarray(pin.gauge_algebra(dims, 1)).reshape(-1), 0.3, capi.PFMP_HOST)
+    U0 = np.zeros(V * 72)
+    capi.pfmp_gauge_get(ctx, U0, capi.PFMP_HOST)
+    d = capi.ActionDef()
+    d.beta, d.csw, d.nkappa = 5.5, 1.0, 2
+    d.kappa[0], d.kappa[1] = 0.120, 0.110
+    d.mu, d.nu, d.tol, d.max_iter = 1.2, 0.9, 1e-12, 5000
+    capi.pfmp_action_scheme(capi.PFMP_SCHEME_PFMP, 0, 8, d)
+    A = capi.pfmp_action_create_def(ctx, d)
+    lam = 0.1931833275037836
+    levels = [1, 1, 1, 0, 0]
+    noise = lambda s: np.concatenate([np.ascontiguousarray(pin.spinor(dims, s + i)).view(np.float64).reshape(-1)
+                                      for i in range(3)])
+    T, S = capi.pfmp_schedule_merge([capi.pfmp_schedule_2mn(n, 0.5, lam) for n in (4, 8)])
+    info = capi.pfmp_trajectory(A, T, S, levels, np.ascontiguousarray(pin.momenta(dims, 500)).reshape(-1),
+                                noise(510), 2.0)
+    fl = [max(info.fmax[t] for t in range(5) if levels[t] == lv) for lv in (0, 1)]
+    n = capi.pfmp_balance_steps(fl, 4)
+    T, S = capi.pfmp_schedule_merge([capi.pfmp_schedule_2mn(k, 0.5, lam) for k in n])
+    acc, nmat, dh = [], [], []
+    t0 = time.perf_counter()
+    for k in range(ntraj):
+        capi.pfmp_gauge_set(ctx, U0, capi.PFMP_HOST)
+        capi.pfmp_action_refresh(A)
+        r = capi.pfmp_trajectory(A, T, S, levels, np.ascontiguousarray(pin.momenta(dims, 520 + k)).reshape(-1),
+                                 noise(530 + 3 * k), float(pin.uniform(560 + k)[0]))
+        acc.append(r.accepted)
+        nmat.append(r.k_apply)
+        dh.append(r.dH)
+    s = time.perf_counter() - t0
+    c = capi.pfmp_cost(acc, nmat, dh, 12.5)
+    capi.pfmp_action_destroy(A)
+    capi.pfmp_ctx_destroy(ctx)
+    return {"level_fmax": fl, "steps": n, "trajectories": ntraj, "s_per_trajectory": s / ntraj,
+            "p_acc": [c.p_acc, c.p_acc_err], "n_mat": [c.nmat, c.nmat_err], "cost": [c.cost, c.cost_err],
+            "exp_minus_dH": [c.exp_mdh, c.exp_mdh_err], "dH": dh}
+
+
 def trajectory_4x4x4x4(capi, stream):
     """One PF-MP trajectory of the 4^4 parity configuration (eps 0.3, beta 5.5, c_sw 1,
     kappa 0.120, kappa' 0.110, order-8 filter, 2MN 8 x 16 steps, tau 0.5, FP64, CG 1e-12)."""
@@ -604,6 +708,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-big-trajectory", action="store_true")
+    ap.add_argument("--no-tuning", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 96-system batched-solve measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner measurement")
     ap.add_argument("--nn-steps", type=int, default=300, help="training steps of the learned preconditioner")

@@ -288,6 +288,9 @@ typedef struct {
   double mu, nu;                      /* Chebyshev ellipse of every filter             */
   double tol;                         /* relative residual of every solve              */
   int max_iter;
+  int solver;                         /* CG of the action: PFMP_SOLVER_CG64 (default 0) or
+                                         PFMP_SOLVER_CG_MIXED (FP32 iterations, FP64-
+                                         accurate true residual); multi-shift stays FP64 */
 } pfmp_action_def;
 typedef struct {
   double beta, kappa, kappa_h, csw;  /* gauge coupling, target and Hasenbusch kappa, c_sw */
@@ -357,6 +360,23 @@ int pfmp_schedule_merge(int nschemes, const int* len, const double* T, const dou
 int pfmp_trajectory(pfmp_action* action, int len, const double* T, int nlevels, const double* S,
                     const int* term_level, const double* mom, const double* xi, int where, double u,
                     pfmp_traj_info* info);
+
+/* ---- step-size balancing and cost (Sec. 2.4 eq. force_tune, Sec. 3.1 eqs. cost_func,
+ * error_corrected) ---------------------------------------------------------------------
+ * pfmp_balance_steps: step counts over tau for nlev levels from each level's maximal
+ * force fmax[l] (e.g. the largest pfmp_traj_info.fmax of the terms on it) so that
+ * F_l h_l = constant (h = tau / n): anchored at the level with the smallest force, which
+ * keeps n_coarse steps; n[l] = max(1, round(n_coarse fmax[l] / fmax_min)).
+ * pfmp_cost: over ntraj trajectories, P_acc = mean(accepted), N_mat = mean(nmat),
+ * C = N_mat / P_acc, <exp(-dH)>, each with sigma = sqrt(2 tau_int) sigma_p / sqrt(N)
+ * (sigma_p the sample standard deviation); the error of C by linear propagation.
+ * PFMP_E_INVALID for ntraj < 2, a non-positive force or n_coarse < 1.  Host only.      */
+typedef struct {
+  double p_acc, p_acc_err, nmat, nmat_err, cost, cost_err, exp_mdh, exp_mdh_err;
+} pfmp_cost_info;
+int pfmp_balance_steps(int nlev, const double* fmax, int n_coarse, int* n);
+int pfmp_cost(int ntraj, const int* accepted, const double* nmat, const double* dH, double tau_int,
+              pfmp_cost_info* info);
 
 /* ---- batched solves ------------------------------------------------------------------
  * Many independent systems K_s x = b (each operator on its own context: lattice, gauge

@@ -69,7 +69,13 @@ class Term(C.Structure):
 class ActionDef(C.Structure):
     _fields_ = [("beta", C.c_double), ("csw", C.c_double), ("nkappa", C.c_int),
                 ("kappa", C.c_double * PFMP_MAX_KAPPA), ("nterms", C.c_int), ("term", Term * PFMP_MAX_TERMS),
-                ("mu", C.c_double), ("nu", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int)]
+                ("mu", C.c_double), ("nu", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int),
+                ("solver", C.c_int)]
+
+
+class CostInfo(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("p_acc", "p_acc_err", "nmat", "nmat_err", "cost", "cost_err", "exp_mdh",
+                                          "exp_mdh_err")]
 
 
 class TrajInfo(C.Structure):
@@ -126,6 +132,8 @@ SIGNATURES = {
     "pfmp_action_create": (I, [P, C.POINTER(ActionParams), C.POINTER(P)]),
     "pfmp_action_scheme": (I, [I, I, I, C.POINTER(ActionDef)]),
     "pfmp_spectrum": (I, [P, I, P, DP, DP, DP, DP, C.POINTER(I)]),
+    "pfmp_balance_steps": (I, [I, DP, I, C.POINTER(I)]),
+    "pfmp_cost": (I, [I, C.POINTER(I), DP, DP, D, C.POINTER(CostInfo)]),
     "pfmp_action_create_def": (I, [P, C.POINTER(ActionDef), C.POINTER(P)]),
     "pfmp_action_counts": (I, [P, C.POINTER(I), C.POINTER(I)]),
     "pfmp_action_destroy": (I, [P]),
@@ -402,6 +410,22 @@ def pfmp_spectrum(op, nsteps, v0):
     check(lib().pfmp_spectrum(op, nsteps, _ptr(v0), C.byref(lo), C.byref(hi), a.ctypes.data_as(DP),
                               b.ctypes.data_as(DP), C.byref(k)))
     return lo.value, hi.value, a[:k.value].copy(), b[:k.value].copy()
+
+
+def pfmp_balance_steps(fmax, n_coarse):
+    f, pf = _dp(np.asarray(fmax, dtype=np.float64))
+    n = (I * len(f))()
+    check(lib().pfmp_balance_steps(len(f), pf, n_coarse, n))
+    return list(n)
+
+
+def pfmp_cost(accepted, nmat, dH, tau_int=12.5):
+    acc = (I * len(accepted))(*[int(bool(a)) for a in accepted])
+    nm, pn = _dp(np.asarray(nmat, dtype=np.float64))
+    dh, pd = _dp(np.asarray(dH, dtype=np.float64))
+    info = CostInfo()
+    check(lib().pfmp_cost(len(acc), acc, pn, pd, float(tau_int), C.byref(info)))
+    return info
 
 
 def pfmp_action_scheme(scheme, p1, p2, d):

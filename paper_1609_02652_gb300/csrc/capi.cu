@@ -518,6 +518,49 @@ int pfmp_spectrum(pfmp_op* op, int nsteps, const void* v0, double* lmin, double*
   API_END
 }
 
+int pfmp_balance_steps(int nlev, const double* fmax, int n_coarse, int* n) {
+  API_BEGIN
+  PFMP_REQUIRE(nlev >= 1 && fmax && n && n_coarse >= 1, PFMP_E_INVALID, "bad argument");
+  int c = 0;
+  for (int l = 0; l < nlev; ++l) {
+    PFMP_REQUIRE(fmax[l] > 0 && std::isfinite(fmax[l]), PFMP_E_INVALID, "forces must be positive and finite");
+    if (fmax[l] < fmax[c]) c = l;
+  }
+  for (int l = 0; l < nlev; ++l) {
+    const double v = std::floor(n_coarse * fmax[l] / fmax[c] + 0.5);
+    PFMP_REQUIRE(v < 1e9, PFMP_E_INVALID, "force ratio too large");
+    n[l] = v < 1 ? 1 : (int)v;
+  }
+  API_END
+}
+
+int pfmp_cost(int ntraj, const int* accepted, const double* nmat, const double* dH, double tau_int,
+              pfmp_cost_info* info) {
+  API_BEGIN
+  PFMP_REQUIRE(ntraj >= 2 && accepted && nmat && dH && info && tau_int > 0, PFMP_E_INVALID, "bad argument");
+  auto mean_err = [&](auto f, double& m, double& e) {
+    double s = 0;
+    for (int i = 0; i < ntraj; ++i) s += f(i);
+    m = s / ntraj;
+    double v = 0;
+    for (int i = 0; i < ntraj; ++i) v += (f(i) - m) * (f(i) - m);
+    e = std::sqrt(2.0 * tau_int) * std::sqrt(v / (ntraj - 1)) / std::sqrt((double)ntraj);
+  };
+  pfmp_cost_info r{};
+  mean_err([&](int i) { return accepted[i] ? 1.0 : 0.0; }, r.p_acc, r.p_acc_err);
+  mean_err([&](int i) { return nmat[i]; }, r.nmat, r.nmat_err);
+  mean_err([&](int i) { return std::exp(-dH[i]); }, r.exp_mdh, r.exp_mdh_err);
+  if (r.p_acc > 0) {
+    r.cost = r.nmat / r.p_acc;
+    r.cost_err = r.cost * std::sqrt((r.nmat_err / r.nmat) * (r.nmat_err / r.nmat) +
+                                    (r.p_acc_err / r.p_acc) * (r.p_acc_err / r.p_acc));
+  } else {
+    r.cost = r.cost_err = HUGE_VAL;
+  }
+  *info = r;
+  API_END
+}
+
 int pfmp_action_scheme(int scheme, int p1, int p2, pfmp_action_def* def) {
   API_BEGIN
   PFMP_REQUIRE(def, PFMP_E_INVALID, "null argument");

@@ -181,11 +181,15 @@ cd cdot(pfmp_ctx* c, const void* x, const void* y) {
   return cd(v[0], v[1]);
 }
 
+// the action's CG: FP64, or mixed (FP32 iterations with reliable updates, FP64-accurate
+// true residual) when the action was created with PFMP_SOLVER_CG_MIXED
 void cg64(pfmp_action* A, pfmp_op* op, void* x, const void* b) {
   int it, rel;
   double res;
   long kap;
-  int st = solve(op, PFMP_SOLVER_CG64, A->def.tol, A->def.max_iter, 0.1, 8, x, b, &it, &rel, &res, &kap);
+  const bool mixed = A->def.solver == PFMP_SOLVER_CG_MIXED;
+  int st = solve(op, mixed ? PFMP_SOLVER_CG_MIXED : PFMP_SOLVER_CG64, A->def.tol, A->def.max_iter, mixed ? 1e-4 : 0.1,
+                 8, x, b, &it, &rel, &res, &kap);
   PFMP_REQUIRE(st == PFMP_OK, st, "CG inside the action did not converge");
 }
 
@@ -352,6 +356,8 @@ pfmp_action* action_create_def(pfmp_ctx* c, const pfmp_action_def* d) {
   PFMP_REQUIRE(d->nterms >= 1 && d->nterms <= PFMP_MAX_TERMS, PFMP_E_INVALID, "nterms out of range");
   PFMP_REQUIRE(d->mu >= d->nu && d->nu > 0, PFMP_E_INVALID, "need mu >= nu > 0");
   PFMP_REQUIRE(d->tol > 0 && d->max_iter > 0, PFMP_E_INVALID, "bad solver tolerance / iteration cap");
+  PFMP_REQUIRE(d->solver == PFMP_SOLVER_CG64 || d->solver == PFMP_SOLVER_CG_MIXED, PFMP_E_INVALID,
+               "action solver must be CG64 or CG_MIXED");
   for (int i = 0; i < d->nkappa; ++i) PFMP_REQUIRE(d->kappa[i] > 0, PFMP_E_INVALID, "kappa must be positive");
   for (int i = 0; i < d->nterms; ++i) {
     const pfmp_term& x = d->term[i];

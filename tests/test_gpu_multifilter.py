@@ -151,3 +151,70 @@ def test_trajectory_matches_oracle(name, levels):
     finally:
         capi.pfmp_action_destroy(A)
         g.close()
+
+
+def test_mixed_solver_action(world):
+    """1PF-2MP with the action's CG in mixed precision (FP32 iterations, FP64-accurate
+    true residual, 1e-12): heatbath, every term and the Hasenbusch-ratio forces = oracle."""
+    from oracle.action import Action, scheme
+
+    lat, U, g, capi = world
+    act = Action(lat, BETA, CSW, KAPPAS, scheme("1PF-2MP", **SCHEMES["1PF-2MP"][3]), mu=MU, nu=NU, tol=TOL)
+    d = _def(capi, scheme="1PF-2MP")
+    d.solver = capi.PFMP_SOLVER_CG_MIXED
+    A = capi.pfmp_action_create_def(g.ctx, d)
+    try:
+        xi = _noise(lat, len(act.pf), 90)
+        phis = act.heatbath(U, xi)
+        capi.pfmp_action_heatbath(A, np.concatenate([canon(x) for x in xi]))
+        S = capi.pfmp_action_eval(A)
+        for i in range(len(act.terms)):
+            phi = phis[act.pf.index(i)] if i in act.pf else None
+            ref = act.S(U, i, phi).item()
+            assert abs(S[i] - ref) < 1e-9 * max(1.0, abs(ref)), (i, S[i], ref)
+        for i in (4, 5):   # J_1 J_2^{-1} and J_2 K^{-1}
+            F = np.zeros(lat.V * 32)
+            capi.pfmp_action_force(A, i, F)
+            ref = act.F(U, i, phis[act.pf.index(i)])
+            assert rel_l2(torch.tensor(F).reshape(*lat.shape, 4, 8), ref) < 1e-9
+    finally:
+        capi.pfmp_action_destroy(A)
+
+
+@pytest.mark.slow
+def test_force_balanced_schedule(world):
+    """Sec. 2.4: forces measured in one PF-MP trajectory set the step counts of the next
+    (F_l h_l = const on the maximal forces), and the cost of three trajectories comes out
+    finite (Sec. 3.1)."""
+    from oracle.integrator import LAMBDA_2MN
+    from oracle.tuning import balance_steps
+
+    lat, U0, g, capi = world
+    Ug = np.zeros(lat.V * 72)
+    capi.pfmp_gauge_get(g.ctx, Ug, capi.PFMP_HOST)
+    A = capi.pfmp_action_create_def(g.ctx, _def(capi, scheme="PF-MP"))
+    try:
+        levels = [1, 1, 1, 0, 0]
+        xi = np.concatenate([canon(x) for x in _noise(lat, 3, 120)])
+        mom = np.ascontiguousarray(pin.momenta(DIMS, 121)).reshape(-1)
+        T, S = capi.pfmp_schedule_merge([capi.pfmp_schedule_2mn(n, 0.5, LAMBDA_2MN) for n in (4, 8)])
+        info = capi.pfmp_trajectory(A, T, S, levels, mom, xi, 2.0)     # u = 2: rejected, U kept
+        fl = [max(info.fmax[t] for t in range(5) if levels[t] == l) for l in (0, 1)]
+        n = capi.pfmp_balance_steps(fl, 4)
+        assert n == balance_steps(fl, 4) and 4 in n
+        T, S = capi.pfmp_schedule_merge([capi.pfmp_schedule_2mn(k, 0.5, LAMBDA_2MN) for k in n])
+        acc, nmat, dh = [], [], []
+        for k in range(3):
+            capi.pfmp_gauge_set(g.ctx, Ug, capi.PFMP_HOST)
+            capi.pfmp_action_refresh(A)
+            mom = np.ascontiguousarray(pin.momenta(DIMS, 130 + k)).reshape(-1)
+            xi = np.concatenate([canon(x) for x in _noise(lat, 3, 140 + 3 * k)])
+            r = capi.pfmp_trajectory(A, T, S, levels, mom, xi, float(pin.uniform(150 + k)[0]))
+            acc.append(r.accepted)
+            nmat.append(r.k_apply)
+            dh.append(r.dH)
+        c = capi.pfmp_cost(acc, nmat, dh)
+        assert np.isfinite(c.nmat) and c.nmat > 0 and np.isfinite(c.exp_mdh)
+    finally:
+        capi.pfmp_gauge_set(g.ctx, Ug, capi.PFMP_HOST)
+        capi.pfmp_action_destroy(A)
