@@ -87,10 +87,6 @@ __global__ void __launch_bounds__(256) k_batch_hop(const BatchSys* __restrict__ 
   }
 }
 
-__device__ __forceinline__ double dot4d(float4 a) {
-  return (double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z + (double)a.w * a.w;
-}
-
 // x += alpha p, r -= alpha Ap, |r|^2 -> beta, rr, iter, done_next
 __global__ void __launch_bounds__(256) k_batch_xr(const BatchSys* __restrict__ sys, const int* __restrict__ map) {
   const TileRef T = tile(sys, map);
@@ -102,6 +98,7 @@ __global__ void __launch_bounds__(256) k_batch_xr(const BatchSys* __restrict__ s
   const int cb = T.sb * blockDim.x + threadIdx.x;
   const float al = (float)sc->alpha;
   double v[1] = {0.0};
+  float acc = 0.f;  // the site's |r|^2 in FP32, across sites in FP64
   if (cb < Vh) {
     for (int k = 0; k < 6; ++k) {
       const long i = off + (long)k * Vh + cb;
@@ -117,9 +114,10 @@ __global__ void __launch_bounds__(256) k_batch_xr(const BatchSys* __restrict__ s
       rr.w -= al * aa.w;
       S.x[i] = xx;
       S.r[i] = rr;
-      v[0] += dot4d(rr);
+      acc += rr.x * rr.x + rr.y * rr.y + rr.z * rr.z + rr.w * rr.w;
     }
   }
+  v[0] = acc;
   double t[1];
   if (group_sum<1>(v, S.partials + (size_t)T.r * S.nsb, S.tickets + T.r, S.nsb, T.sb, t)) {
     sc->rr_new = t[0];

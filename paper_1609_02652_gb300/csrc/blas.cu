@@ -20,9 +20,6 @@ static int blas_grid(long n) {
 }
 
 __device__ __forceinline__ double dot2(double2 a) { return a.x * a.x + a.y * a.y; }
-__device__ __forceinline__ double dot4(float4 a) {
-  return (double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z + (double)a.w * a.w;
-}
 
 // ---------------------------------------------------------------- elementwise
 // F64 [12][Vh] double2 -> F32 [6][Vh] float4 and back
@@ -73,12 +70,15 @@ __global__ void k_axpy32(float are, float aim, const float4* __restrict__ x, flo
 
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double sq(double2 a) { return dot2(a); }
-__device__ __forceinline__ double sq(float4 a) { return dot4(a); }
+__device__ __forceinline__ float sq(float4 a) { return a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w; }
 
+// FP32 fields: each thread's few terms summed in FP32 (GB300's FP64 pipe is a small
+// fraction of the FP32 one), the sums across threads and blocks in FP64
 template <typename V>
 __global__ void k_norm2(const V* __restrict__ x, long n, ReduceBuf rb, double* out) {
-  double v[1] = {0.0};
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) v[0] += sq(x[i]);
+  decltype(sq(x[0])) acc = 0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) acc += sq(x[i]);
+  double v[1] = {(double)acc};
   double t[1];
   if (grid_sum<1>(v, rb, t)) *out = t[0];
 }
@@ -158,7 +158,7 @@ __global__ void k_cg_xr32(float4* __restrict__ x, float4* __restrict__ r, const 
                           const float4* __restrict__ Ap, long n, ReduceBuf rb, CGScalars* s) {
   if (s->done) return;
   const float al = (float)s->alpha;
-  double v[1] = {0.0};
+  float acc = 0.f;  // per-thread |r|^2 in FP32, across threads in FP64
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     float4 xx = x[i], rr = r[i], pp = p[i], aa = Ap[i];
     xx.x += al * pp.x;
@@ -171,8 +171,9 @@ __global__ void k_cg_xr32(float4* __restrict__ x, float4* __restrict__ r, const 
     rr.w -= al * aa.w;
     x[i] = xx;
     r[i] = rr;
-    v[0] += dot4(rr);
+    acc += sq(rr);
   }
+  double v[1] = {(double)acc};
   double t[1];
   if (grid_sum<1>(v, rb, t)) {
     s->rr_new = t[0];

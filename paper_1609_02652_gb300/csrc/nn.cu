@@ -373,25 +373,52 @@ __device__ bool grid_sum_n(double* v, int nv, double* partials, unsigned* ticket
 // scalars' `done` flag (set by the step kernel's last block once |r| has fallen by delta)
 // makes every later kernel of the cycle return at once.
 
-// h_j = <W_j, w> (j < k) and <w, r>: out[2j], out[2j+1], out[2k], out[2k+1]
-__global__ void k_fgcr_dots(float4* const* __restrict__ Wp, int k, const float4* __restrict__ w,
-                            const float4* __restrict__ r, long n, double* partials, unsigned* ticket, double* out,
-                            const CGScalars* __restrict__ s) {
+// h_j = <W_j, w> (j < k) and <w, r>: out[2j], out[2j+1], out[2k], out[2k+1].  Block row
+// y of the grid takes one product (y < k: <W_y, w>, y = k: <w, r>) and writes one partial
+// per block; k_fgcr_dots_final adds each row's partials in a fixed order.
+__global__ void k_fgcr_dots_part(float4* const* __restrict__ Wp, int k, const float4* __restrict__ w,
+                                 const float4* __restrict__ r, long n, double* partials,
+                                 const CGScalars* __restrict__ s) {
   if (s->done) return;
-  double v[34];
-  for (int j = 0; j < 2 * k + 2; ++j) v[j] = 0.0;
+  const int y = blockIdx.y;
+  const float4* __restrict__ q = y < k ? Wp[y] : r;
+  // each thread's few products in FP32 (GB300's FP64 pipe is a small fraction of the FP32
+  // one), the sums across threads and blocks in FP64
+  float pr = 0.f, pi = 0.f;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const float4 a = w[i];
-    for (int j = 0; j < k; ++j) {
-      const float4 q = Wp[j][i];
-      v[2 * j] += (double)q.x * a.x + (double)q.y * a.y + (double)q.z * a.z + (double)q.w * a.w;
-      v[2 * j + 1] += (double)q.x * a.y - (double)q.y * a.x + (double)q.z * a.w - (double)q.w * a.z;
+    const float4 a = w[i], c = q[i];
+    if (y < k) {  // conj(W_y) w
+      pr += c.x * a.x + c.y * a.y + c.z * a.z + c.w * a.w;
+      pi += c.x * a.y - c.y * a.x + c.z * a.w - c.w * a.z;
+    } else {      // conj(w) r
+      pr += a.x * c.x + a.y * c.y + a.z * c.z + a.w * c.w;
+      pi += a.x * c.y - a.y * c.x + a.z * c.w - a.w * c.z;
     }
-    const float4 rr = r[i];
-    v[2 * k] += (double)a.x * rr.x + (double)a.y * rr.y + (double)a.z * rr.z + (double)a.w * rr.w;
-    v[2 * k + 1] += (double)a.x * rr.y - (double)a.y * rr.x + (double)a.z * rr.w - (double)a.w * rr.z;
   }
-  grid_sum_n(v, 2 * k + 2, partials, ticket, out);
+  double v[2] = {(double)pr, (double)pi};
+  __shared__ double sh[2 * 32];
+  block_sum<2>(v, sh);
+  if (threadIdx.x == 0) {
+    partials[((size_t)y * gridDim.x + blockIdx.x) * 2] = v[0];
+    partials[((size_t)y * gridDim.x + blockIdx.x) * 2 + 1] = v[1];
+  }
+}
+
+__global__ void k_fgcr_dots_final(int nblk, const double* __restrict__ partials, double* __restrict__ out,
+                                  const CGScalars* __restrict__ s) {
+  if (s->done) return;
+  const int y = blockIdx.x;
+  double v[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    v[0] += partials[((size_t)y * nblk + b) * 2];
+    v[1] += partials[((size_t)y * nblk + b) * 2 + 1];
+  }
+  __shared__ double sh[2 * 32];
+  block_sum<2>(v, sh);
+  if (threadIdx.x == 0) {
+    out[2 * y] = v[0];
+    out[2 * y + 1] = v[1];
+  }
 }
 
 // w -= sum_j h_j W_j, z -= sum_j h_j Z_j with h from the dots; *n2 = |w|^2
@@ -403,6 +430,7 @@ __global__ void k_fgcr_orth(float4* const* __restrict__ Wp, float4* const* __res
   if (threadIdx.x < k) h[threadIdx.x] = make_float2((float)hd[2 * threadIdx.x], (float)hd[2 * threadIdx.x + 1]);
   __syncthreads();
   double v[1] = {0.0};
+  float nt = 0.f;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     float4 a = w[i], b = z[i];
     for (int j = 0; j < k; ++j) {
@@ -419,8 +447,9 @@ __global__ void k_fgcr_orth(float4* const* __restrict__ Wp, float4* const* __res
     }
     w[i] = a;
     z[i] = b;
-    v[0] += (double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z + (double)a.w * a.w;
+    nt += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
   }
+  v[0] = nt;  // per-thread sum in FP32, across threads in FP64
   grid_sum_n(v, 1, partials, ticket, n2);
 }
 
@@ -1010,7 +1039,9 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
           PFMP_CHECK_LAUNCH();
         }
         kop(op, PFMP_F32, w, z, nullptr, wk.scal);
-        k_fgcr_dots<<<fgrid, kBlock, 0, c->stream>>>(wk.dW, k, w, wk.r, n32, wk.part, wk.ticket, wk.out, wk.scal);
+        k_fgcr_dots_part<<<dim3(fgrid, k + 1), kBlock, 0, c->stream>>>(wk.dW, k, w, wk.r, n32, wk.part, wk.scal);
+        PFMP_CHECK_LAUNCH();
+        k_fgcr_dots_final<<<k + 1, kBlock, 0, c->stream>>>(fgrid, wk.part, wk.out, wk.scal);
         PFMP_CHECK_LAUNCH();
         k_fgcr_orth<<<fgrid, kBlock, 0, c->stream>>>(wk.dW, wk.dZ, k, wk.out, w, z, n32, wk.part, wk.ticket,
                                                      wk.out + 36, wk.scal);

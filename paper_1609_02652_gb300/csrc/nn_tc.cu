@@ -145,12 +145,13 @@ __global__ void k_pack_b(const float2* __restrict__ W, __half* __restrict__ B) {
 __global__ void k_rms_scale(const float4* __restrict__ in, int Vh, ReduceBuf rb, float* sigma,
                             const int* __restrict__ skip) {
   if (skip && *skip) return;
-  double s[1] = {0.0};
+  float st = 0.f;  // per-thread sum in FP32, across threads in FP64
   const long n = 6L * Vh;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const float4 v = in[i];
-    s[0] += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+    st += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
   }
+  double s[1] = {(double)st};
   double t[1];
   if (grid_sum<1>(s, rb, t)) *sigma = t[0] > 0 ? (float)sqrt(24.0 * Vh / t[0]) : 1.0f;
 }
