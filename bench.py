@@ -264,8 +264,8 @@ def run_ours(args, rank, world):
     # FP64 CG baseline (same system, same flush)
     for _ in range(1):
         capi.pfmp_solve(op, plain, x, b)
-    t_plain, info_plain = timed(plain, max(2, min(args.steps, 3)))
-    fp64_ms = statistics.mean(t_plain)
+    t_plain, info_plain = timed(plain, 3)
+    fp64_ms = statistics.median(t_plain)
 
     # end to end through host memory (pinned), wall clock
     bh = torch.empty(DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] * 24, dtype=torch.float64, pin_memory=True)

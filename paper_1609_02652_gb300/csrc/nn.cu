@@ -543,6 +543,7 @@ struct pfmp_nn {
   bool packed = false;           // Bp holds the current weights
   std::vector<void*> Bp;         // packed FP16 operand per layer
   std::vector<void*> act16;      // FP16 scaled inputs of each layer
+  void* z16 = nullptr;           // last layer: FP16 per-direction mixed outputs [9][12][V]
   float* sigma = nullptr;        // device scalar: 1 / rms of the network input
   int* err = nullptr;            // device error flag of the tensor-core kernel
   long long id = 0;              // unique per network (keys the FGCR cycle graphs)
@@ -558,8 +559,9 @@ void nn_tc_pack(pfmp_ctx* c, int cin, int cout, const void* W, void* Bp);
 void nn_tc_scale(pfmp_ctx* c, const void* in_even_f32, float* sigma_dev, const int* skip);
 void nn_tc_layer(pfmp_ctx* c, int cin, int cout, bool last, const void* Bp, const void* in, void* out,
                  const float* sigma, int* err, const int* skip);
-void nn_tc_embed(pfmp_ctx* c, const void* in_even_f32, const float* sigma, void* act16, const int* skip);
-void nn_tc_extract(pfmp_ctx* c, const void* act32, void* out_even_f32, const int* skip);
+void nn_tc_embed(pfmp_ctx* c, const void* in_even_f32, float* sigma, void* act16, const int* skip, const double* rr);
+void nn_tc_last(pfmp_ctx* c, const void* Bp, const void* in, void* z16, void* out_even_f32, const float* sigma,
+                int* err, const int* skip);
 void nn_tc_init();
 
 void nn_destroy(pfmp_nn* N) {
@@ -568,6 +570,7 @@ void nn_destroy(pfmp_nn* N) {
     for (auto p : *vec) dev_free(p);
   dev_free(N->sigma);
   dev_free(N->err);
+  dev_free(N->z16);
   dev_free(N->gbuf[0]);
   dev_free(N->gbuf[1]);
   dev_free(N->target);
@@ -610,6 +613,7 @@ pfmp_nn* nn_create(pfmp_ctx* c, int nl, const int* ch, int prec) {
         N->Bp.push_back(dev_alloc(nn_tc_packed_bytes(ch[l], ch[l + 1])));
         N->act16.push_back(dev_alloc((size_t)ch[l] * 12 * c->g.V * 4));
       }
+      N->z16 = dev_alloc((size_t)9 * 12 * c->g.V * 4);
       N->tc = true;
       N->sigma = (float*)dev_alloc(sizeof(float));
       N->err = (int*)dev_alloc(sizeof(int));
@@ -706,17 +710,17 @@ static void tc_prepare(pfmp_nn* N) {
 
 // tensor-core forward pass: in (even FP32) -> out (even FP32) through FP16 activations;
 // every kernel returns at once while *skip is set (FGCR after convergence)
-static void forward_tc(pfmp_nn* N, void* out, const void* in, const int* skip) {
+// rr (optional): device |in|^2 known to the caller, used for the input scale
+static void forward_tc(pfmp_nn* N, void* out, const void* in, const int* skip, const double* rr) {
   pfmp_ctx* c = N->ctx;
   const int L = (int)N->W.size();
-  nn_tc_scale(c, in, N->sigma, skip);
-  nn_tc_embed(c, in, N->sigma, N->act16[0], skip);
-  for (int l = 0; l < L; ++l) {
-    const bool last = l == L - 1;
-    nn_tc_layer(c, N->ch[l], N->ch[l + 1], last, N->Bp[l], N->act16[l], last ? N->act[L] : N->act16[l + 1],
-                N->sigma, N->err, skip);
-  }
-  nn_tc_extract(c, N->act[L], out, skip);
+  if (!rr) nn_tc_scale(c, in, N->sigma, skip);
+  nn_tc_embed(c, in, N->sigma, N->act16[0], skip, rr);
+  for (int l = 0; l < L - 1; ++l)
+    nn_tc_layer(c, N->ch[l], N->ch[l + 1], false, N->Bp[l], N->act16[l], N->act16[l + 1], N->sigma, N->err, skip);
+  // the last layer mixes channels at each site first and transports after (the colour
+  // transport commutes with the spin/channel weights), on even sites only
+  nn_tc_last(c, N->Bp[L - 1], N->act16[L - 1], N->z16, out, N->sigma, N->err, skip);
 }
 
 template <typename T>
@@ -739,7 +743,8 @@ static void forward_t(pfmp_nn* N) {
 
 // out_even = N(in_even); io precision prec_io (device layout of the library); skip: see
 // forward_tc (tensor-core path only)
-static void nn_apply_skip(pfmp_nn* N, void* out, const void* in, int prec_io, const int* skip) {
+static void nn_apply_skip(pfmp_nn* N, void* out, const void* in, int prec_io, const int* skip,
+                          const double* rr = nullptr) {
   pfmp_ctx* c = N->ctx;
   const Geom& g = c->g;
   const int L = (int)N->W.size();
@@ -757,7 +762,7 @@ static void nn_apply_skip(pfmp_nn* N, void* out, const void* in, int prec_io, co
   } else {
     if (N->tc && prec_io == PFMP_F32) {
       tc_prepare(N);
-      forward_tc(N, out, in, skip);
+      forward_tc(N, out, in, skip, rr);
       return;
     }
     if (prec_io == PFMP_F64)
@@ -1033,7 +1038,7 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
         float4* z = wk.Z[k];
         float4* w = wk.W[k];
         if (nn) {
-          nn_apply_skip(nn, z, wk.r, PFMP_F32, &wk.scal->done);
+          nn_apply_skip(nn, z, wk.r, PFMP_F32, &wk.scal->done, &wk.scal->rr);
         } else {
           k_fgcr_copy<<<fgrid, kBlock, 0, c->stream>>>(z, wk.r, n32, wk.scal);
           PFMP_CHECK_LAUNCH();

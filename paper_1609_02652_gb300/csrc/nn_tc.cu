@@ -38,12 +38,15 @@ namespace tc {
 
 constexpr int kM = 128;        // sites per tile = TMEM lanes
 constexpr int kThreads = 512;  // four threads per site in the gather
+// COUT = 9 marks the local mixing of the last layer: z_d = sum_i W_d[0][i] a_i at every
+// site for the nine directions d (no gather; the transport follows in k_last_stencil)
 template <int CIN, int COUT>
 struct Shape {
-  static constexpr int NST = CIN == 1 ? 5 : 9;        // K stages
+  static constexpr bool LOCAL = COUT == 9;
+  static constexpr int NST = LOCAL ? 1 : (CIN == 1 ? 5 : 9);  // K stages
   static constexpr int DPS = CIN == 1 ? 2 : 1;        // directions per stage
   static constexpr int K = CIN == 1 ? 16 : 8 * CIN;   // reals per stage
-  static constexpr int N = 8 * COUT < 16 ? 16 : 8 * COUT;  // output reals per colour (padded)
+  static constexpr int N = (8 * COUT + 15) / 16 * 16;  // output reals per colour (padded to 16)
   static constexpr int A_TILE = kM * K * 2;
   static constexpr int A_BUF = 3 * A_TILE;
   static constexpr int B_ST = N * K * 2;
@@ -129,14 +132,21 @@ __global__ void k_pack_b(const float2* __restrict__ W, __half* __restrict__ B) {
   const int st = i / (S::N * S::K), rem = i % (S::N * S::K);
   const int n = rem / S::K, k = rem % S::K;
   const int di = st * S::DPS + (CIN == 1 ? (k >> 3) : 0);
-  const int d = di < 9 ? dir_of(di) : 9;
   const int ic = CIN == 1 ? 0 : (k >> 3);
   const int o = n >> 3, a = (n >> 1) & 3, ro = n & 1;
   const int b = (k >> 1) & 3, ri = k & 1;
   float v = 0.f;
-  if (d < 9 && o < COUT) {
-    const float2 w = W[(((size_t)d * COUT + o) * CIN + ic) * 16 + a * 4 + b];
-    v = ro == ri ? w.x : (ro == 0 ? -w.y : w.y);
+  if (S::LOCAL) {  // output block o is the direction d of the single output channel
+    if (o < 9) {
+      const float2 w = W[((size_t)o * CIN + ic) * 16 + a * 4 + b];
+      v = ro == ri ? w.x : (ro == 0 ? -w.y : w.y);
+    }
+  } else {
+    const int d = di < 9 ? dir_of(di) : 9;
+    if (d < 9 && o < COUT) {
+      const float2 w = W[(((size_t)d * COUT + o) * CIN + ic) * 16 + a * 4 + b];
+      v = ro == ri ? w.x : (ro == 0 ? -w.y : w.y);
+    }
   }
   B[(size_t)st * (S::B_ST / 2) + kmajor(n, k, S::K) / 2] = __float2half_rn(v);
 }
@@ -267,9 +277,16 @@ __device__ __forceinline__ void gather_stage(const Geom& g, const float4* __rest
 
 // network input: sigma * (even FP32 field [6][Vh] float4) on even sites, 0 on odd sites,
 // as FP16 complex [12][V] (lexicographic sites)
-__global__ void k_embed16(Geom g, const float4* __restrict__ src, const float* __restrict__ sigma_p,
-                          __half2* __restrict__ dst, const int* __restrict__ skip) {
+// rr (optional): |src|^2 already known to the caller (FGCR's residual norm); sigma is then
+// computed here, stored for the later kernels, and no separate reduction is needed
+__global__ void k_embed16(Geom g, const float4* __restrict__ src, float* __restrict__ sigma_p,
+                          __half2* __restrict__ dst, const int* __restrict__ skip, const double* __restrict__ rr) {
   if (skip && *skip) return;
+  if (rr) {
+    const double t = *rr;
+    const float sg0 = t > 0 ? (float)sqrt(24.0 * g.Vh / t) : 1.0f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *sigma_p = sg0;
+  }
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int r = s, x[4];
@@ -280,7 +297,7 @@ __global__ void k_embed16(Geom g, const float4* __restrict__ src, const float* _
   x[2] = r % g.L[2];
   x[3] = r / g.L[2];
   const bool even = ((x[0] + x[1] + x[2] + x[3]) & 1) == 0;
-  const float sg = *sigma_p;
+  const float sg = rr ? (*rr > 0 ? (float)sqrt(24.0 * g.Vh / *rr) : 1.0f) : *sigma_p;
   const int cb = s >> 1;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
@@ -290,20 +307,68 @@ __global__ void k_embed16(Geom g, const float4* __restrict__ src, const float* _
   }
 }
 
-// network output: even sites of the FP32 activation [12][V] -> even FP32 field [6][Vh]
-__global__ void k_extract32(Geom g, const float2* __restrict__ src, float4* __restrict__ dst,
-                            const int* __restrict__ skip) {
+// last layer, second half: out(x) = sum_d U_d(x) z_d(x + d) on even sites (the only ones
+// the network output is read on): z_0(x) + sum_mu [U_mu(x) z_{1+mu}(x + mu)
+// + U_mu(x - mu)^dag z_{5+mu}(x - mu)] with the fermion boundary factor on time hops; z
+// is FP16 [9][12][V] scaled by sigma, out the even FP32 field [6][Vh] divided by sigma
+__global__ void k_last_stencil(Geom g, const float4* __restrict__ U32, const __half2* __restrict__ z,
+                               float4* __restrict__ out, const float* __restrict__ sigma_p,
+                               const int* __restrict__ skip) {
   if (skip && *skip) return;
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   if (cb >= g.Vh) return;
   int x[4];
   cb_coords(g, cb, 0, x);
-  const size_t s = (size_t)lex_index(g, x);
+  const size_t V = (size_t)g.V;
+  cplx<float> acc[12];
+  {
+    const size_t s0 = (size_t)lex_index(g, x);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const float2 a = src[(size_t)(2 * k) * g.V + s], b = src[(size_t)(2 * k + 1) * g.V + s];
-    dst[(size_t)k * g.Vh + cb] = make_float4(a.x, a.y, b.x, b.y);
+    for (int k = 0; k < 12; ++k) {
+      const float2 v = __half22float2(__ldg(z + (size_t)k * V + s0));
+      acc[k] = mk(v.x, v.y);
+    }
   }
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll 1
+    for (int dir = 0; dir < 2; ++dir) {
+      int y[4] = {x[0], x[1], x[2], x[3]};
+      float f = 1.0f;
+      Mat3<float> Um;
+      if (dir == 0) {
+        y[mu] = y[mu] + 1 == g.L[mu] ? 0 : y[mu] + 1;
+        if (mu == 3 && x[3] == g.L[3] - 1) f = (float)g.bc_t;
+        load_link(Um, U32 + (size_t)(mu * 3) * g.Vh, cb, g.Vh);  // x is even: parity 0
+      } else {
+        y[mu] = y[mu] == 0 ? g.L[mu] - 1 : y[mu] - 1;
+        if (mu == 3 && x[3] == 0) f = (float)g.bc_t;
+        Mat3<float> L;
+        load_link(L, U32 + (size_t)((4 + mu) * 3) * g.Vh, cb_index(g, y), g.Vh);  // y is odd
+        Um = dagger(L);
+      }
+      const int d = dir == 0 ? 1 + mu : 5 + mu;
+      const size_t sy = (size_t)lex_index(g, y);
+      cplx<float> v[4][3];
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 w = __half22float2(__ldg(z + ((size_t)d * 12 + sp * 3 + c) * V + sy));
+          v[sp][c] = mk(w.x, w.y);
+        }
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          acc[sp * 3 + r] = acc[sp * 3 + r] + f * (Um.m[r][0] * v[sp][0] + Um.m[r][1] * v[sp][1] + Um.m[r][2] * v[sp][2]);
+    }
+  }
+  const float inv = 1.0f / *sigma_p;
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+    out[(size_t)j * g.Vh + cb] =
+        make_float4(inv * acc[2 * j].re, inv * acc[2 * j].im, inv * acc[2 * j + 1].re, inv * acc[2 * j + 1].im);
 }
 
 // OUT16: FP16 scaled output for the next layer; otherwise FP32 output divided by sigma
@@ -468,9 +533,10 @@ bool nn_tc_supported(int cin, int cout) {
   return (cin == 1 && cout == 8) || (cin == 8 && cout == 8) || (cin == 8 && cout == 1);
 }
 
+// the last layer (8 -> 1) is packed for the local mixing (Shape<8, 9>)
 size_t nn_tc_packed_bytes(int cin, int cout) {
   if (cin == 1) return tc::Shape<1, 8>::B_ALL;
-  if (cout == 1) return tc::Shape<8, 1>::B_ALL;
+  if (cout == 1) return tc::Shape<8, 9>::B_ALL;
   return tc::Shape<8, 8>::B_ALL;
 }
 
@@ -486,7 +552,7 @@ void nn_tc_pack(pfmp_ctx* c, int cin, int cout, const void* W, void* Bp) {
   if (cin == 1)
     pack_t<1, 8>(c, W, Bp);
   else if (cout == 1)
-    pack_t<8, 1>(c, W, Bp);
+    pack_t<8, 9>(c, W, Bp);
   else
     pack_t<8, 8>(c, W, Bp);
 }
@@ -496,12 +562,6 @@ void nn_tc_scale(pfmp_ctx* c, const void* in_even_f32, float* sigma_dev, const i
   long b = (n + kBlock - 1) / kBlock;
   const int grid = (int)(b < 152 * 4 ? b : 152 * 4);
   tc::k_rms_scale<<<grid, kBlock, 0, c->stream>>>((const float4*)in_even_f32, c->g.Vh, c->rb, sigma_dev, skip);
-  PFMP_CHECK_LAUNCH();
-}
-
-void nn_tc_extract(pfmp_ctx* c, const void* act32, void* out_even_f32, const int* skip) {
-  tc::k_extract32<<<nblocks(c->g.Vh, 256), 256, 0, c->stream>>>(c->g, (const float2*)act32, (float4*)out_even_f32,
-                                                                 skip);
   PFMP_CHECK_LAUNCH();
 }
 
@@ -523,7 +583,7 @@ static int layer_init() {
 void nn_tc_init() {
   layer_init<1, 8, true>();
   layer_init<8, 8, true>();
-  layer_init<8, 1, false>();
+  layer_init<8, 9, true>();
 }
 
 template <int CIN, int COUT, bool OUT16>
@@ -541,18 +601,26 @@ static void layer_t(pfmp_ctx* c, const void* Bp, const void* in, void* out, cons
 // in: FP16 scaled activations; out: FP16 scaled (last = false) or FP32 / sigma (last)
 void nn_tc_layer(pfmp_ctx* c, int cin, int cout, bool last, const void* Bp, const void* in, void* out,
                  const float* sigma, int* err, const int* skip) {
-  PFMP_REQUIRE(!(last && cout == 8) && !(!last && cout == 1), PFMP_E_INVALID, "tensor-core layer sequence");
+  PFMP_REQUIRE(!last && cout == 8, PFMP_E_INVALID, "tensor-core layer sequence (the last layer: nn_tc_last)");
   if (cin == 1)
     layer_t<1, 8, true>(c, Bp, in, out, sigma, err, skip);
-  else if (cout == 1)
-    layer_t<8, 1, false>(c, Bp, in, out, sigma, err, skip);
   else
     layer_t<8, 8, true>(c, Bp, in, out, sigma, err, skip);
 }
 
-void nn_tc_embed(pfmp_ctx* c, const void* in_even_f32, const float* sigma, void* act16, const int* skip) {
+// the last layer (8 -> 1) as local mixing on the tensor cores (z, FP16 [9][12][V]) and
+// the even-site transport stencil, straight into the even FP32 output field
+void nn_tc_last(pfmp_ctx* c, const void* Bp, const void* in, void* z16, void* out_even_f32, const float* sigma,
+                int* err, const int* skip) {
+  layer_t<8, 9, true>(c, Bp, in, z16, sigma, err, skip);
+  tc::k_last_stencil<<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(c->g, c->U32, (const __half2*)z16,
+                                                                   (float4*)out_even_f32, sigma, skip);
+  PFMP_CHECK_LAUNCH();
+}
+
+void nn_tc_embed(pfmp_ctx* c, const void* in_even_f32, float* sigma, void* act16, const int* skip, const double* rr) {
   tc::k_embed16<<<nblocks(c->g.V, 256), 256, 0, c->stream>>>(c->g, (const float4*)in_even_f32, sigma,
-                                                             (__half2*)act16, skip);
+                                                             (__half2*)act16, skip, rr);
   PFMP_CHECK_LAUNCH();
 }
 
