@@ -700,6 +700,34 @@ def kernel_only(dims, reps):
     print(json.dumps({"kernel_only": list(dims), "reps": reps, "launches_per_rep": 4}))
 
 
+def nn_only(reps):
+    """Applications of a [1,8,8,8,1] network (weights pfmp_inputs.nn_weights(ch, 5)) on the
+    16^3x32 benchmark field through the tensor-core path (no timing): the case the ncu
+    captures of the network kernels run."""
+    import torch
+
+    import pfmp_inputs as pin
+    from paper_1609_02652_gb300 import capi
+
+    torch.cuda.set_device(0)
+    ctx = capi.pfmp_ctx_create(DIMS, -1, None)
+    h = torch.tensor(np.ascontiguousarray(pin.gauge_algebra(DIMS, GAUGE_SEED)).reshape(-1), device="cuda")
+    torch.cuda.synchronize()
+    capi.pfmp_gauge_from_algebra(ctx, h, EPS, capi.PFMP_DEVICE)
+    ch = [1, 8, 8, 8, 1]
+    net = capi.pfmp_nn_create(ctx, ch, capi.PFMP_F32)
+    capi.pfmp_nn_set_weights(net, pin.nn_weights(ch, 5))
+    n32 = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F32) // 4
+    a = torch.randn(n32, dtype=torch.float32, device="cuda")
+    o = torch.zeros_like(a)
+    for _ in range(reps):
+        capi.pfmp_nn_apply(net, capi.PFMP_F32, o, a)
+    torch.cuda.synchronize()
+    capi.pfmp_nn_destroy(net)
+    capi.pfmp_ctx_destroy(ctx)
+    print(json.dumps({"nn_only": list(DIMS), "reps": reps, "network": ch}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -715,11 +743,16 @@ def main():
     ap.add_argument("--nn-steps", type=int, default=300, help="training steps of the learned preconditioner")
     ap.add_argument("--delta", type=float, default=1e-4, help="reliable-update threshold of the mixed solver")
     ap.add_argument("--chunk", type=int, default=8, help="CG iterations per CUDA-graph chunk")
+    ap.add_argument("--nn-only", action="store_true",
+                    help="three applications of the [1,8,8,8,1] network at 16^3x32 (for ncu captures)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only apply K (FP32) --kernel-reps times on --kernel-dims: the small case for ncu")
     ap.add_argument("--kernel-dims", default="24,24,24,48")
     ap.add_argument("--kernel-reps", type=int, default=8)
     args = ap.parse_args()
+    if args.nn_only:
+        nn_only(3)
+        return
     if args.kernel_only:
         kernel_only(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_reps)
         return
