@@ -361,6 +361,14 @@ int pfmp_trajectory(pfmp_action* action, int len, const double* T, int nlevels, 
                     const int* term_level, const double* mom, const double* xi, int where, double u,
                     pfmp_traj_info* info);
 
+/* MD alone (Sec. 2.1, App. B): evolve the gauge field and the momenta mom (canonical
+ * [V][4][8], read and overwritten) along the merged schedule with the pseudofermions the
+ * action holds (from pfmp_action_heatbath or _set_phi); term_level as for
+ * pfmp_trajectory.  No heatbath, no Hamiltonian, no accept/reject.  With mom negated
+ * the scheme runs backwards (time reversibility).  Synchronises.                      */
+int pfmp_md(pfmp_action* action, int len, const double* T, int nlevels, const double* S, const int* term_level,
+            double* mom, int where);
+
 /* ---- step-size balancing and cost (Sec. 2.4 eq. force_tune, Sec. 3.1 eqs. cost_func,
  * error_corrected) ---------------------------------------------------------------------
  * pfmp_balance_steps: step counts over tau for nlev levels from each level's maximal

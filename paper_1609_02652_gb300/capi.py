@@ -133,6 +133,7 @@ SIGNATURES = {
     "pfmp_action_scheme": (I, [I, I, I, C.POINTER(ActionDef)]),
     "pfmp_spectrum": (I, [P, I, P, DP, DP, DP, DP, C.POINTER(I)]),
     "pfmp_balance_steps": (I, [I, DP, I, C.POINTER(I)]),
+    "pfmp_md": (I, [P, I, DP, I, DP, C.POINTER(I), P, I]),
     "pfmp_cost": (I, [I, C.POINTER(I), DP, DP, D, C.POINTER(CostInfo)]),
     "pfmp_action_create_def": (I, [P, C.POINTER(ActionDef), C.POINTER(P)]),
     "pfmp_action_counts": (I, [P, C.POINTER(I), C.POINTER(I)]),
@@ -410,6 +411,14 @@ def pfmp_spectrum(op, nsteps, v0):
     check(lib().pfmp_spectrum(op, nsteps, _ptr(v0), C.byref(lo), C.byref(hi), a.ctypes.data_as(DP),
                               b.ctypes.data_as(DP), C.byref(k)))
     return lo.value, hi.value, a[:k.value].copy(), b[:k.value].copy()
+
+
+def pfmp_md(a, T, S_levels, term_level, mom, where=PFMP_HOST):
+    """MD alone; mom (host float64 array or device address) is overwritten."""
+    T, pT = _dp(T)
+    S, pS = _dp(np.asarray(S_levels).reshape(-1))
+    tl = (I * len(term_level))(*term_level)
+    check(lib().pfmp_md(a, len(T), pT, np.asarray(S_levels).shape[0], pS, tl, _ptr(mom), where))
 
 
 def pfmp_balance_steps(fmax, n_coarse):

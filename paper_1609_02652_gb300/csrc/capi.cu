@@ -36,6 +36,8 @@ int schedule_merge(int ns, const int* len, const double* T, const double* S, int
 void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int* term_level,
                 const double* mom, int where, const void* const* xi, double u, pfmp_traj_info* info);
 pfmp_ctx* action_ctx(pfmp_action* A);
+void action_md(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int* term_level,
+               double* mom, int where);
 pfmp_batch* batch_create(int nsys, pfmp_op* const* ops, const int* nrhs);
 void batch_destroy(pfmp_batch* B);
 int batch_solve(pfmp_batch* B, double tol, int max_iter, double delta, int check, void* const* x, const void* const* b,
@@ -696,6 +698,15 @@ int pfmp_trajectory(pfmp_action* A, int len, const double* T, int nlev, const do
   NoiseFields nf(A, xi, where);
   auto p = nf.ptrs();
   trajectory(A, len, T, nlev, S, term_level, mom, where, p.data(), u, info);
+  API_END
+}
+
+int pfmp_md(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int* term_level, double* mom,
+            int where) {
+  API_BEGIN
+  PFMP_REQUIRE(A && T && S && term_level && mom, PFMP_E_INVALID, "null argument");
+  check_where(where);
+  action_md(A, len, T, nlev, S, term_level, mom, where);
   API_END
 }
 

@@ -624,6 +624,54 @@ void force_norms(pfmp_action* A, double* sum, double* mx) {
   *mx = v[1];
 }
 
+// the MD part of a trajectory (Sec. 2.1, App. B): for each step of the merged schedule
+// T-hat, then P -= eps F_t for every term t on each level with a non-zero step, one term
+// at a time so that each term's force is measured (sums of the link averages into favg)
+static void md_steps(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int* term_level,
+                     pfmp_traj_info* info) {
+  const int nt = (int)A->t.size();
+  const double nlinks = 4.0 * A->ctx->g.V;
+  for (int i = 0; i < len; ++i) {
+    if (T[i] != 0.0) link_update(A, T[i]);
+    for (int l = 0; l < nlev; ++l) {
+      const double eps = S[(size_t)l * len + i];
+      if (eps == 0.0) continue;
+      for (int t = 0; t < nt; ++t) {
+        if (term_level[t] != l) continue;
+        const long long kt = kapply_total(A);
+        action_zero_force(A);
+        action_force(A, t);
+        mom_update(A, eps);
+        info->k_apply_term[t] += kapply_total(A) - kt;
+        double fs, fm;
+        force_norms(A, &fs, &fm);
+        info->nforce[t] += 1;
+        info->fmax[t] = std::max(info->fmax[t], fm);
+        info->favg[t] += fs / nlinks;
+      }
+    }
+  }
+}
+
+// MD alone with the current pseudofermions: U and the momenta (canonical [V][4][8], in
+// and out) evolve along the schedule; no heatbath, no Hamiltonian, no accept/reject
+void action_md(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int* term_level,
+               double* mom, int where) {
+  pfmp_ctx* c = A->ctx;
+  const int nt = (int)A->t.size();
+  PFMP_REQUIRE(len >= 1 && nlev >= 1, PFMP_E_INVALID, "empty schedule");
+  for (int t = 0; t < nt; ++t)
+    PFMP_REQUIRE(term_level[t] >= -1 && term_level[t] < nlev, PFMP_E_INVALID, "term level out of range");
+  bool stale = false;
+  for (auto op : A->ops) stale = stale || op->built_version != c->gauge_version;
+  if (stale) refresh_ops(A);
+  alg_pack(c, A->mom, mom, where);
+  pfmp_traj_info scratch{};
+  md_steps(A, len, T, nlev, S, term_level, &scratch);
+  alg_unpack(c, mom, where, A->mom);
+  PFMP_CUDA(cudaStreamSynchronize(c->stream));
+}
+
 void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int* term_level,
                 const double* mom, int where, const void* const* xi, double u, pfmp_traj_info* info) {
   pfmp_ctx* c = A->ctx;
@@ -645,28 +693,7 @@ void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double
   double H0 = kinetic(A);
   for (int t = 0; t < nt; ++t)
     if (term_level[t] >= 0) H0 += (S0[t] = action_term(A, t));
-  // per term: P -= eps F_t, one term at a time so that each term's force is measured
-  const double nlinks = 4.0 * g.V;
-  for (int i = 0; i < len; ++i) {
-    if (T[i] != 0.0) link_update(A, T[i]);
-    for (int l = 0; l < nlev; ++l) {
-      const double eps = S[(size_t)l * len + i];
-      if (eps == 0.0) continue;
-      for (int t = 0; t < nt; ++t) {
-        if (term_level[t] != l) continue;
-        const long long kt = kapply_total(A);
-        action_zero_force(A);
-        action_force(A, t);
-        mom_update(A, eps);
-        info->k_apply_term[t] += kapply_total(A) - kt;
-        double fs, fm;
-        force_norms(A, &fs, &fm);
-        info->nforce[t] += 1;
-        info->fmax[t] = std::max(info->fmax[t], fm);
-        info->favg[t] += fs / nlinks;
-      }
-    }
-  }
+  md_steps(A, len, T, nlev, S, term_level, info);
   double H1 = kinetic(A);
   for (int t = 0; t < nt; ++t)
     if (term_level[t] >= 0) H1 += (S1[t] = action_term(A, t));
