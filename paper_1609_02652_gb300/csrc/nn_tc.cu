@@ -10,7 +10,7 @@
 // (padded to 16), with B = [[Re W, -Im W], [Im W, Re W]] so that the complex product
 // comes out in (re, im) column pairs.  Operands are FP16, the accumulator FP32 in
 // tensor memory.  K is consumed in stages: one direction per stage (K = 8 C_in), or for
-// C_in = 1 two directions per stage (K = 16, the last stage half zero).
+// C_in = 1 four directions per stage (K = 32, the last stage three quarters zero).
 //
 // Activations between the layers are FP16 complex [C][12][V], scaled by sigma = 1/rms of
 // the network input so that FP16 keeps its precision (the network is linear; the last
@@ -43,9 +43,9 @@ constexpr int kThreads = 512;  // four threads per site in the gather
 template <int CIN, int COUT>
 struct Shape {
   static constexpr bool LOCAL = COUT == 9;
-  static constexpr int NST = LOCAL ? 1 : (CIN == 1 ? 5 : 9);  // K stages
-  static constexpr int DPS = CIN == 1 ? 2 : 1;        // directions per stage
-  static constexpr int K = CIN == 1 ? 16 : 8 * CIN;   // reals per stage
+  static constexpr int NST = LOCAL ? 1 : (CIN == 1 ? 3 : 9);  // K stages
+  static constexpr int DPS = CIN == 1 ? 4 : 1;        // directions per stage
+  static constexpr int K = CIN == 1 ? 32 : 8 * CIN;   // reals per stage
   static constexpr int N = (8 * COUT + 15) / 16 * 16;  // output reals per colour (padded to 16)
   static constexpr int A_TILE = kM * K * 2;
   static constexpr int A_BUF = 3 * A_TILE;
@@ -244,15 +244,14 @@ __device__ __forceinline__ void store_channel(const Hop& h, const cplx<float> v[
 
 // the gather of one stage by one thread: part p of the site's (direction, channel) items.
 // C_in = 8: one direction per stage, channels p and p + 4 (one link, 24 loads in flight);
-// C_in = 1: parts 0 and 1 take the stage's two directions (part 1 of the last stage
-// writes the zero padding), parts 2 and 3 have nothing to do.
+// C_in = 1: the four parts take the stage's four directions (the last stage's parts
+// 1 to 3 write the zero padding).
 template <int CIN, int K>
 __device__ __forceinline__ void gather_stage(const Geom& g, const float4* __restrict__ U32,
                                              const __half2* __restrict__ in, size_t V, bool live, const int x[4],
                                              int st, int part, unsigned char* A, int row, int a_tile) {
   if (CIN == 1) {
-    if (part >= 2) return;
-    const int di = 2 * st + part;
+    const int di = 4 * st + part;
     const bool on = live && di < 9;
     Hop h;
     cplx<float> v[4][3];
