@@ -261,6 +261,16 @@ def run_ours(args, rank, world):
     ms_step = allmax(sum(t_mixed), world) / args.steps
     value = ms_step / world  # whole-job ms per solve (replicas)
 
+    # the same solve with the stencil on FP16 storage, a few reliable-update thresholds
+    half_res = {}
+    for dl in (1e-1, 3e-2, 1e-2):
+        hp = capi.SolverParams(method=capi.PFMP_SOLVER_CG_HALF, tol=TOL, max_iter=20000, delta=dl, check_every=8)
+        capi.pfmp_solve(op, hp, x, b)
+        t_h, info_h = timed(hp, 3)
+        half_res[f"delta_{dl:g}"] = {"ms": statistics.median(t_h), "iterations": info_h[-1].iters,
+                                     "reliable_updates": info_h[-1].reliable_updates,
+                                     "true_rel_res": info_h[-1].true_rel_res}
+
     # FP64 CG baseline (same system, same flush)
     for _ in range(1):
         capi.pfmp_solve(op, plain, x, b)
@@ -288,7 +298,7 @@ def run_ours(args, rank, world):
     capi.pfmp_ctx_destroy(ctx)
 
     # roofline of the stencil kernels on a lattice far larger than L2
-    roof = roofline(capi, stream, l2_flush)
+    roof, roof_h16 = roofline(capi, stream, l2_flush)
     batched = None if args.no_batched else batched_96(capi, stream, l2_flush, args)
 
     hbm, src = peaks()
@@ -301,6 +311,8 @@ def run_ours(args, rank, world):
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{world}"},
         "iterations": info_mixed[-1].iters, "reliable_updates": info_mixed[-1].reliable_updates,
         "true_rel_res": info_mixed[-1].true_rel_res,
+        "roofline_h16": roof_h16,
+        "half_cg": half_res,
         "fp64_cg": {"ms": fp64_ms, "iterations": info_plain[-1].iters, "true_rel_res": info_plain[-1].true_rel_res,
                     "speedup_mixed_vs_fp64": fp64_ms / ms_step},
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 8),
@@ -663,16 +675,33 @@ def roofline(capi, stream, l2_flush, reps=12):
         l2_flush()
         capi.pfmp_kop(op, capi.PFMP_F32, o, a)
     n, ms, by = capi.pfmp_profile_end(ctx, capi.PFMP_KERNEL_HOP_F32)
+    # the same K on FP16 storage (spinors with per-site FP32 scales, links and clover FP16)
+    nh = capi.pfmp_spinor_bytes(ctx, capi.PFMP_H16) // 4
+    ah = torch.zeros(nh, dtype=torch.float32, device="cuda")
+    oh = torch.zeros_like(ah)
+    capi.pfmp_convert(ctx, ah, capi.PFMP_H16, a, capi.PFMP_F32)
+    for _ in range(3):
+        capi.pfmp_kop(op, capi.PFMP_H16, oh, ah)
+    capi.pfmp_profile_begin(ctx)
+    for _ in range(reps):
+        l2_flush()
+        capi.pfmp_kop(op, capi.PFMP_H16, oh, ah)
+    n16, ms16, by16 = capi.pfmp_profile_end(ctx, capi.PFMP_KERNEL_HOP_H16)
     capi.pfmp_op_destroy(op)
     capi.pfmp_ctx_destroy(ctx)
     hbm, src = peaks()
     achieved = by / (ms * 1e-3) / 1e9
     traffic = recorded_traffic()
+    a16 = by16 / (ms16 * 1e-3) / 1e9
+    h16 = {"bound": "hbm", "achieved": a16, "peak": hbm, "unit": "GB/s", "frac": a16 / hbm, "peak_source": src,
+           "kernel": "k_hop FP16 storage (FP32 arithmetic), 4 launches per K", "launches": n16,
+           "avg_us": ms16 * 1e3 / n16, "bytes_per_launch": by16 / n16,
+           "k_time_ratio_f32_over_h16": (ms / n) / (ms16 / n16)}
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": traffic, "peak_source": src,
             "kernel": "k_hop FP32 (Wilson hop + fused clover epilogues), 4 launches per K",
             "workload": "K applications on 32^3x64, FP32, L2 flushed before each K",
-            "launches": n, "avg_us": ms * 1e3 / n, "bytes_per_launch": by / n}
+            "launches": n, "avg_us": ms * 1e3 / n, "bytes_per_launch": by / n}, h16
 
 
 def kernel_only(dims, reps):

@@ -57,6 +57,13 @@ extern "C" {
 /* ---- precisions and locations ---------------------------------------------------- */
 #define PFMP_F64 0
 #define PFMP_F32 1
+/* FP16 storage, FP32 arithmetic (the sloppy precision of PFMP_SOLVER_CG_HALF): an even
+ * or odd spinor field is [6][Vh] of 8-byte words (two complex FP16 each) followed by one
+ * FP32 scale per site (the site's largest |component|; stored values are value / scale),
+ * 52 bytes per site; links and clover blocks in FP16 without scale (|entries| = O(1)).
+ * Accepted by pfmp_dslash, pfmp_mhat, pfmp_kop, pfmp_spinor_pack/unpack, pfmp_convert
+ * (to and from PFMP_F32) and pfmp_spinor_bytes.                                      */
+#define PFMP_H16 3
 #define PFMP_HOST 0
 #define PFMP_DEVICE 1
 
@@ -174,6 +181,9 @@ int pfmp_convert(pfmp_ctx* ctx, void* dst, int dst_prec, const void* src, int sr
 #define PFMP_SOLVER_CG64 0      /* CG in FP64 throughout                                 */
 #define PFMP_SOLVER_CG_MIXED 1  /* FP32 CG with FP64 reliable updates (true residual in  */
                                 /* FP64, solution accumulated in FP64)                    */
+#define PFMP_SOLVER_CG_HALF 2   /* the same with the stencil on FP16 storage (p and Kp    */
+                                /* FP16 with per-site scales, x and r FP32, FP32 sums    */
+                                /* per thread); delta ~ 1e-2..1e-1 suits FP16            */
 typedef struct {
   int method;        /* PFMP_SOLVER_*                                                     */
   double tol;        /* stop when ||b - K x|| / ||b|| < tol, residual recomputed in FP64  */
@@ -459,6 +469,7 @@ int pfmp_solve_fgcr(pfmp_op* op, pfmp_nn* nn, const pfmp_solver_params* params, 
 #define PFMP_KERNEL_HOP_F32 0
 #define PFMP_KERNEL_HOP_F64 1
 #define PFMP_KERNEL_HOP_DF 2   /* double-float (FP32-pair) stencil of the true residual   */
+#define PFMP_KERNEL_HOP_H16 3  /* FP16-storage stencil (PFMP_SOLVER_CG_HALF)              */
 int pfmp_profile_begin(pfmp_ctx* ctx);
 int pfmp_profile_end(pfmp_ctx* ctx, int kernel_class, int64_t* launches, double* total_ms, double* total_bytes);
 

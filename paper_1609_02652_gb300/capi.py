@@ -25,12 +25,16 @@ PFMP_E_UNSUPPORTED = 7
 PFMP_F64 = 0
 PFMP_F32 = 1
 PFMP_DF = 2
+PFMP_H16 = 3
 PFMP_HOST = 0
 PFMP_DEVICE = 1
 PFMP_KERNEL_HOP_F32 = 0
 PFMP_KERNEL_HOP_F64 = 1
+PFMP_KERNEL_HOP_DF = 2
+PFMP_KERNEL_HOP_H16 = 3
 PFMP_SOLVER_CG64 = 0
 PFMP_SOLVER_CG_MIXED = 1
+PFMP_SOLVER_CG_HALF = 2
 
 
 class PfmpError(RuntimeError):

@@ -208,6 +208,84 @@ __global__ void k_cg_p32(float4* __restrict__ p, const float4* __restrict__ r, l
   if (grid_sum<1>(v, rb, t)) s->done = s->done_next;
 }
 
+// ---------------------------------------------------------------- FP16 storage
+// (site-parallel: a site's scale covers its 24 reals)
+__global__ void k_f32_to_h16(const float4* __restrict__ s, uint2* __restrict__ d, int Vh) {
+  for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < Vh; cb += gridDim.x * blockDim.x) {
+    Spinor<float> v;
+    load_spinor(v, s, cb, Vh);
+    store_spinor(d, v, cb, Vh);
+  }
+}
+__global__ void k_h16_to_f32(const uint2* __restrict__ s, float4* __restrict__ d, int Vh) {
+  for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < Vh; cb += gridDim.x * blockDim.x) {
+    Spinor<float> v;
+    load_spinor(v, s, cb, Vh);
+    store_spinor(d, v, cb, Vh);
+  }
+}
+
+__device__ __forceinline__ float h16_scale(const uint2* f, int cb, int Vh) {
+  return reinterpret_cast<const float*>(f + (size_t)6 * Vh)[cb];
+}
+
+// FP32 x, r with FP16 p, Ap: x += alpha p, r -= alpha Ap, |r|^2 -> beta, rr, iter, done_next
+__global__ void k_cg_xr_h(float4* __restrict__ x, float4* __restrict__ r, const uint2* __restrict__ p,
+                          const uint2* __restrict__ Ap, int Vh, ReduceBuf rb, CGScalars* s) {
+  if (s->done) return;
+  const float al = (float)s->alpha;
+  float acc = 0.f;
+  for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < Vh; cb += gridDim.x * blockDim.x) {
+    const float sp = h16_scale(p, cb, Vh), sa = h16_scale(Ap, cb, Vh);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const size_t i = (size_t)k * Vh + cb;
+      const uint2 pv = p[i], av = Ap[i];
+      const float2 p0 = h2_to_f2(pv.x), p1 = h2_to_f2(pv.y), a0 = h2_to_f2(av.x), a1 = h2_to_f2(av.y);
+      const float ap = al * sp, aa = al * sa;
+      float4 xx = x[i], rr = r[i];
+      xx.x += ap * p0.x;
+      xx.y += ap * p0.y;
+      xx.z += ap * p1.x;
+      xx.w += ap * p1.y;
+      rr.x -= aa * a0.x;
+      rr.y -= aa * a0.y;
+      rr.z -= aa * a1.x;
+      rr.w -= aa * a1.y;
+      x[i] = xx;
+      r[i] = rr;
+      acc += sq(rr);
+    }
+  }
+  double v[1] = {(double)acc};
+  double t[1];
+  if (grid_sum<1>(v, rb, t)) {
+    s->rr_new = t[0];
+    s->beta = t[0] / s->rr;
+    s->rr = t[0];
+    s->iter += 1;
+    if (t[0] < s->stop_rr || !(t[0] == t[0])) s->done_next = 1;
+  }
+}
+
+// FP16 p = r + beta p (new per-site scale); the last block then raises `done` if asked
+__global__ void k_cg_p_h(uint2* __restrict__ p, const float4* __restrict__ r, int Vh, ReduceBuf rb, CGScalars* s) {
+  if (s->done) return;
+  const float be = (float)s->beta;
+  for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < Vh; cb += gridDim.x * blockDim.x) {
+    Spinor<float> pp, rr;
+    load_spinor(pp, p, cb, Vh);
+    load_spinor(rr, r, cb, Vh);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) pp.s[a][c] = rr.s[a][c] + be * pp.s[a][c];
+    store_spinor(p, pp, cb, Vh);
+  }
+  double v[1] = {0.0}, t[1];
+  if (grid_sum<1>(v, rb, t)) s->done = s->done_next;
+}
+
 // ---------------------------------------------------------------- host
 static long words(const pfmp_ctx* c, int prec) { return prec == PFMP_F64 ? 12L * c->g.Vh : 6L * c->g.Vh; }
 
@@ -221,10 +299,17 @@ void blas_copy(pfmp_ctx* c, void* dst, int dprec, const void* src, int sprec) {
     PFMP_CUDA(cudaMemcpyAsync(dst, src, spinor_bytes(c->g, dprec), cudaMemcpyDeviceToDevice, c->stream));
     return;
   }
-  if (dprec == PFMP_F32)
+  if (dprec == PFMP_H16) {
+    PFMP_REQUIRE(sprec == PFMP_F32, PFMP_E_UNSUPPORTED, "FP16 fields are converted from FP32");
+    k_f32_to_h16<<<blas_grid(Vh), kBlock, 0, c->stream>>>((const float4*)src, (uint2*)dst, Vh);
+  } else if (sprec == PFMP_H16) {
+    PFMP_REQUIRE(dprec == PFMP_F32, PFMP_E_UNSUPPORTED, "FP16 fields are converted to FP32");
+    k_h16_to_f32<<<blas_grid(Vh), kBlock, 0, c->stream>>>((const uint2*)src, (float4*)dst, Vh);
+  } else if (dprec == PFMP_F32) {
     k_f64_to_f32<<<blas_grid(6L * Vh), kBlock, 0, c->stream>>>((const double2*)src, (float4*)dst, Vh);
-  else
+  } else {
     k_f32_to_f64<<<blas_grid(6L * Vh), kBlock, 0, c->stream>>>((const float4*)src, (double2*)dst, Vh, 0);
+  }
   PFMP_CHECK_LAUNCH();
 }
 
@@ -268,7 +353,14 @@ void blas_xmy_norm(pfmp_ctx* c, const void* b, const void* Ax, void* r, double* 
   PFMP_CHECK_LAUNCH();
 }
 
+// prec = PFMP_H16: x and r FP32, p and Ap FP16
 void cg_step_xr(pfmp_ctx* c, int prec, void* x, void* r, const void* p, const void* Ap, CGScalars* s) {
+  if (prec == PFMP_H16) {
+    k_cg_xr_h<<<blas_grid(c->g.Vh), kBlock, 0, c->stream>>>((float4*)x, (float4*)r, (const uint2*)p,
+                                                           (const uint2*)Ap, c->g.Vh, c->rb, s);
+    PFMP_CHECK_LAUNCH();
+    return;
+  }
   const long n = words(c, prec);
   if (prec == PFMP_F64)
     k_cg_xr64<<<blas_grid(n), kBlock, 0, c->stream>>>((double2*)x, (double2*)r, (const double2*)p,
@@ -279,7 +371,13 @@ void cg_step_xr(pfmp_ctx* c, int prec, void* x, void* r, const void* p, const vo
   PFMP_CHECK_LAUNCH();
 }
 
+// prec = PFMP_H16: p FP16, r FP32
 void cg_step_p(pfmp_ctx* c, int prec, void* p, const void* r, CGScalars* s) {
+  if (prec == PFMP_H16) {
+    k_cg_p_h<<<blas_grid(c->g.Vh), kBlock, 0, c->stream>>>((uint2*)p, (const float4*)r, c->g.Vh, c->rb, s);
+    PFMP_CHECK_LAUNCH();
+    return;
+  }
   const long n = words(c, prec);
   if (prec == PFMP_F64)
     k_cg_p64<<<blas_grid(n), kBlock, 0, c->stream>>>((double2*)p, (const double2*)r, n, c->rb, s);

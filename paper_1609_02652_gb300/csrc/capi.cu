@@ -84,6 +84,10 @@ using namespace pfmp;
   return PFMP_OK;
 
 static void check_prec(int prec) { PFMP_REQUIRE(prec == PFMP_F64 || prec == PFMP_F32, PFMP_E_INVALID, "bad precision"); }
+// the entry points that also take FP16 storage
+static void check_prec_h(int prec) {
+  PFMP_REQUIRE(prec == PFMP_F64 || prec == PFMP_F32 || prec == PFMP_H16, PFMP_E_INVALID, "bad precision");
+}
 static void check_where(int w) { PFMP_REQUIRE(w == PFMP_HOST || w == PFMP_DEVICE, PFMP_E_INVALID, "bad location"); }
 
 namespace pfmp {
@@ -99,7 +103,11 @@ void pfmp::op_delete(pfmp_op* op) {
     dev_free(op->clov64[p]);
     dev_free(op->clov32[p]);
     dev_free(op->clovdf[p]);
+    dev_free(op->clov16[p]);
   }
+  dev_free(op->t16);
+  dev_free(op->e16);
+  for (auto q : op->cg16) dev_free(q);
   dev_free(op->tdf);
   dev_free(op->edf);
   dev_free(op->xdf);
@@ -132,7 +140,11 @@ pfmp_op* pfmp::op_new(pfmp_ctx* ctx, double kappa, double csw) {
       op->clov64[p] = (double2*)dev_alloc((size_t)g.Vh * 36 * sizeof(double2));
       op->clov32[p] = (float4*)dev_alloc((size_t)g.Vh * 18 * sizeof(float4));
       op->clovdf[p] = (float4*)dev_alloc((size_t)g.Vh * 36 * sizeof(float4));
+      op->clov16[p] = (uint2*)dev_alloc((size_t)g.Vh * 18 * sizeof(uint2));
     }
+    op->t16 = (uint2*)dev_alloc(spinor_bytes(g, PFMP_H16));
+    op->e16 = (uint2*)dev_alloc(spinor_bytes(g, PFMP_H16));
+    for (auto& q : op->cg16) q = (uint2*)dev_alloc(spinor_bytes(g, PFMP_H16));
     op->tdf = (float4*)dev_alloc((size_t)g.Vh * 12 * sizeof(float4));
     op->edf = (float4*)dev_alloc((size_t)g.Vh * 12 * sizeof(float4));
     op->xdf = (float4*)dev_alloc((size_t)g.Vh * 12 * sizeof(float4));
@@ -195,7 +207,7 @@ int pfmp_ctx_set_stream(pfmp_ctx* ctx, void* stream) {
 
 int64_t pfmp_half_volume(const pfmp_ctx* ctx) { return ctx ? ctx->g.Vh : -1; }
 int64_t pfmp_spinor_bytes(const pfmp_ctx* ctx, int prec) {
-  if (!ctx || (prec != PFMP_F64 && prec != PFMP_F32)) return -1;
+  if (!ctx || (prec != PFMP_F64 && prec != PFMP_F32 && prec != PFMP_H16)) return -1;
   return (int64_t)spinor_bytes(ctx->g, prec);
 }
 
@@ -233,7 +245,7 @@ int pfmp_plaquette(pfmp_ctx* ctx, double* plaq) {
 int pfmp_spinor_pack(pfmp_ctx* ctx, void* dst, int prec, const double* src, int where, int parity) {
   API_BEGIN
   PFMP_REQUIRE(ctx && dst && src && (parity == 0 || parity == 1), PFMP_E_INVALID, "bad argument");
-  check_prec(prec);
+  check_prec_h(prec);
   check_where(where);
   spinor_pack_any(ctx, dst, prec, src, where, parity);
   API_END
@@ -242,7 +254,7 @@ int pfmp_spinor_pack(pfmp_ctx* ctx, void* dst, int prec, const double* src, int 
 int pfmp_spinor_unpack(pfmp_ctx* ctx, double* dst, int where, const void* src, int prec, int parity) {
   API_BEGIN
   PFMP_REQUIRE(ctx && dst && src && (parity == 0 || parity == 1), PFMP_E_INVALID, "bad argument");
-  check_prec(prec);
+  check_prec_h(prec);
   check_where(where);
   spinor_unpack_any(ctx, dst, where, src, prec, parity);
   API_END
@@ -314,7 +326,7 @@ int pfmp_op_get_split(pfmp_op* op, int prec, int* ns) {
 int pfmp_dslash(pfmp_op* op, int prec, void* out, const void* in, int out_parity, int dagger) {
   API_BEGIN
   PFMP_REQUIRE(op && out && in && out != in && (out_parity == 0 || out_parity == 1), PFMP_E_INVALID, "bad argument");
-  check_prec(prec);
+  check_prec_h(prec);
   hop(op, prec, out, in, out_parity, dagger != 0);
   API_END
 }
@@ -332,7 +344,7 @@ int pfmp_clover_apply(pfmp_op* op, int prec, void* out, const void* in, int pari
 int pfmp_mhat(pfmp_op* op, int prec, void* out, const void* in, int dagger) {
   API_BEGIN
   PFMP_REQUIRE(op && out && in && out != in, PFMP_E_INVALID, "bad argument");
-  check_prec(prec);
+  check_prec_h(prec);
   mhat(op, prec, out, in, dagger != 0, nullptr, nullptr);
   API_END
 }
@@ -340,7 +352,7 @@ int pfmp_mhat(pfmp_op* op, int prec, void* out, const void* in, int dagger) {
 int pfmp_kop(pfmp_op* op, int prec, void* out, const void* in, double* in_K_in) {
   API_BEGIN
   PFMP_REQUIRE(op && out && in && out != in, PFMP_E_INVALID, "bad argument");
-  check_prec(prec);
+  check_prec_h(prec);
   pfmp_ctx* c = op->ctx;
   kop(op, prec, out, in, in_K_in ? c->d_sums : nullptr, nullptr);
   if (in_K_in) {
@@ -410,8 +422,11 @@ int pfmp_axpy(pfmp_ctx* ctx, int prec, double a_re, double a_im, const void* x, 
 int pfmp_convert(pfmp_ctx* ctx, void* dst, int dst_prec, const void* src, int src_prec) {
   API_BEGIN
   PFMP_REQUIRE(ctx && dst && src, PFMP_E_INVALID, "null argument");
-  check_prec(dst_prec);
-  check_prec(src_prec);
+  check_prec_h(dst_prec);
+  check_prec_h(src_prec);
+  PFMP_REQUIRE(dst_prec == src_prec || (dst_prec != PFMP_H16 && src_prec != PFMP_H16) ||
+                   dst_prec == PFMP_F32 || src_prec == PFMP_F32,
+               PFMP_E_UNSUPPORTED, "FP16 fields convert to and from FP32 only");
   blas_copy(ctx, dst, dst_prec, src, src_prec);
   API_END
 }
@@ -838,7 +853,9 @@ int pfmp_profile_begin(pfmp_ctx* ctx) {
 int pfmp_profile_end(pfmp_ctx* ctx, int cls, int64_t* launches, double* total_ms, double* total_bytes) {
   API_BEGIN
   PFMP_REQUIRE(ctx && launches && total_ms && total_bytes, PFMP_E_INVALID, "null argument");
-  PFMP_REQUIRE(cls == PFMP_KERNEL_HOP_F32 || cls == PFMP_KERNEL_HOP_F64 || cls == PFMP_KERNEL_HOP_DF, PFMP_E_INVALID,
+  PFMP_REQUIRE(cls == PFMP_KERNEL_HOP_F32 || cls == PFMP_KERNEL_HOP_F64 || cls == PFMP_KERNEL_HOP_DF ||
+                   cls == PFMP_KERNEL_HOP_H16,
+               PFMP_E_INVALID,
                "bad kernel class");
   long n = 0;
   profile_end(ctx, cls, &n, total_ms, total_bytes);

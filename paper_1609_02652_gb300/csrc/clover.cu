@@ -203,6 +203,14 @@ __global__ void k_clover_build(Geom g, const double2* __restrict__ U, double kc,
   if (grid_sum<1>(ld, rb, tot)) *logdet_out = tot[0];
 }
 
+// FP16 copy of the FP32 clover blocks (same word order, 4 reals per 8-byte word)
+__global__ void k_clover_h16(const float4* __restrict__ src, uint2* __restrict__ dst, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float4 v = src[i];
+    dst[i] = make_uint2(f2_to_h2(v.x, v.y), f2_to_h2(v.z, v.w));
+  }
+}
+
 void clover_build(pfmp_op* op) {
   pfmp_ctx* c = op->ctx;
   CloverOut o;
@@ -223,6 +231,11 @@ void clover_build(pfmp_op* op) {
   memcpy(&bad, c->h_sums + 8, sizeof(int));
   PFMP_REQUIRE(bad == 0, PFMP_E_NAN, "clover block not positive definite (A has a non-positive eigenvalue)");
   op->logdet_oo = c->h_sums[0];
+  const long n = 18L * c->g.Vh;
+  for (int p = 0; p < 2; ++p) {
+    k_clover_h16<<<nblocks(n), kBlock, 0, c->stream>>>(op->clov32[p], op->clov16[p], n);
+    PFMP_CHECK_LAUNCH();
+  }
   op->built_version = c->gauge_version;
 }
 

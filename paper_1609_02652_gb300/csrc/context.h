@@ -51,6 +51,7 @@ struct pfmp_ctx {
   double2* U64c = nullptr;   // compressed [2][4][6][Vh]
   float4* U32 = nullptr;     // compressed [2][4][3][Vh]
   float4* Udf = nullptr;     // double-float full links [2][4][9][Vh] (complex as hi/lo pairs)
+  uint2* U16 = nullptr;      // FP16 compressed [2][4][3][Vh] (two complex per word)
   pfmp::ReduceBuf rb{};
   double* d_sums = nullptr;  // [64] results of generic reductions
   double* h_sums = nullptr;  // pinned mirror [64]
@@ -75,6 +76,10 @@ struct pfmp_op {
   float4* t32 = nullptr;
   double2* e64 = nullptr;
   float4* e32 = nullptr;
+  uint2* clov16[2] = {nullptr, nullptr};    // FP16 copy of clov32: [18][Vh] per parity
+  uint2* t16 = nullptr;                     // FP16 odd / even temporaries (with scales)
+  uint2* e16 = nullptr;
+  uint2* cg16[2] = {nullptr, nullptr};      // p and Ap of the FP16 CG
   double2* cg64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // r p Ap | b x (host solve) | spare
   float4* cg32[4] = {nullptr, nullptr, nullptr, nullptr};
   pfmp::CGScalars* scal = nullptr;
@@ -86,7 +91,7 @@ struct pfmp_op {
     const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
     int chunk = 0;
     long long kernels = 0;  // kernel nodes in the graph (for the launch counter)
-  } graph[2];
+  } graph[4];
   cudaStream_t cap = nullptr;
   pfmp::MSWork* ms = nullptr;  // multi-shift workspace (grown on demand)
   void* fgcr = nullptr;         // FGCR workspace (kept between solves), freed by fgcr_free
@@ -98,7 +103,10 @@ struct pfmp_op {
 
 namespace pfmp {
 
-inline size_t spinor_bytes(const Geom& g, int prec) { return (size_t)g.Vh * 24 * (prec == PFMP_F64 ? 8 : 4); }
+inline size_t spinor_bytes(const Geom& g, int prec) {
+  if (prec == PFMP_H16) return (size_t)g.Vh * 52;  // 24 FP16 reals + one FP32 scale per site
+  return (size_t)g.Vh * 24 * (prec == PFMP_F64 ? 8 : 4);
+}
 void* dev_alloc(size_t bytes);
 void dev_free(void* p);
 

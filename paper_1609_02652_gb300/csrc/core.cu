@@ -78,7 +78,7 @@ __global__ void k_gauge_to_canonical(Geom g, const double2* __restrict__ U, doub
 }
 
 __global__ void k_gauge_compress(Geom g, const double2* __restrict__ U, double2* __restrict__ U64c,
-                                 float4* __restrict__ U32, float4* __restrict__ Udf) {
+                                 float4* __restrict__ U32, float4* __restrict__ Udf, uint2* __restrict__ U16) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   const int pm = blockIdx.y;  // parity*4 + mu
   if (cb >= g.Vh) return;
@@ -93,6 +93,10 @@ __global__ void k_gauge_compress(Geom g, const double2* __restrict__ U, double2*
   for (int k = 0; k < 3; ++k)
     d32[(size_t)k * g.Vh + cb] =
         make_float4((float)v[2 * k].x, (float)v[2 * k].y, (float)v[2 * k + 1].x, (float)v[2 * k + 1].y);
+  uint2* d16 = U16 + (size_t)(pm * 3) * g.Vh;
+  for (int k = 0; k < 3; ++k)
+    d16[(size_t)k * g.Vh + cb] = make_uint2(f2_to_h2((float)v[2 * k].x, (float)v[2 * k].y),
+                                            f2_to_h2((float)v[2 * k + 1].x, (float)v[2 * k + 1].y));
 }
 
 __global__ void k_gauge_from_algebra(Geom g, const double* __restrict__ h, double eps, double2* __restrict__ U) {
@@ -172,7 +176,7 @@ static double* canon_scratch(pfmp_ctx* c, size_t doubles) {
 
 void gauge_refresh_compressed(pfmp_ctx* c) {
   dim3 grid(nblocks(c->g.Vh), 8);
-  k_gauge_compress<<<grid, kBlock, 0, c->stream>>>(c->g, c->U64, c->U64c, c->U32, c->Udf);
+  k_gauge_compress<<<grid, kBlock, 0, c->stream>>>(c->g, c->U64, c->U64c, c->U32, c->Udf, c->U16);
   PFMP_CHECK_LAUNCH();
   c->gauge_version++;
 }
@@ -180,6 +184,8 @@ void gauge_refresh_compressed(pfmp_ctx* c) {
 void spinor_pack(pfmp_ctx* c, void* dst, int prec, const double* src_dev, int parity) {
   if (prec == PFMP_F64)
     k_spinor_pack<PFMP_F64><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, src_dev, (double2*)dst, parity);
+  else if (prec == PFMP_H16)
+    k_spinor_pack<PFMP_H16><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, src_dev, (uint2*)dst, parity);
   else
     k_spinor_pack<PFMP_F32><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, src_dev, (float4*)dst, parity);
   PFMP_CHECK_LAUNCH();
@@ -187,6 +193,8 @@ void spinor_pack(pfmp_ctx* c, void* dst, int prec, const double* src_dev, int pa
 void spinor_unpack(pfmp_ctx* c, double* dst_dev, const void* src, int prec, int parity) {
   if (prec == PFMP_F64)
     k_spinor_unpack<PFMP_F64><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, dst_dev, (const double2*)src, parity);
+  else if (prec == PFMP_H16)
+    k_spinor_unpack<PFMP_H16><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, dst_dev, (const uint2*)src, parity);
   else
     k_spinor_unpack<PFMP_F32><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, dst_dev, (const float4*)src, parity);
   PFMP_CHECK_LAUNCH();
@@ -209,6 +217,7 @@ pfmp_ctx* ctx_create(const int dims[4], int bc_t, void* stream) {
     c->U64c = (double2*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 6 * sizeof(double2));
     c->U32 = (float4*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 3 * sizeof(float4));
     c->Udf = (float4*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 9 * sizeof(float4));
+    c->U16 = (uint2*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 3 * sizeof(uint2));
     c->rb.partials = (double*)dev_alloc((size_t)kMaxReduceBlocks * kMaxSums * sizeof(double));
     c->rb.counter = (unsigned*)dev_alloc(sizeof(unsigned));
     PFMP_CUDA(cudaMemset(c->rb.counter, 0, sizeof(unsigned)));
@@ -219,6 +228,7 @@ pfmp_ctx* ctx_create(const int dims[4], int bc_t, void* stream) {
     dev_free(c->U64c);
     dev_free(c->U32);
     dev_free(c->Udf);
+    dev_free(c->U16);
     dev_free(c->rb.partials);
     dev_free(c->rb.counter);
     dev_free(c->d_sums);
@@ -284,6 +294,7 @@ void ctx_destroy(pfmp_ctx* c) {
   dev_free(c->U64c);
   dev_free(c->U32);
   dev_free(c->Udf);
+  dev_free(c->U16);
   dev_free(c->rb.partials);
   dev_free(c->rb.counter);
   dev_free(c->d_sums);

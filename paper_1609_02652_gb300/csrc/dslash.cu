@@ -60,6 +60,7 @@ static HopParams<PREC> params(pfmp_op* op, int p, void* out, const void* in) {
   a.in = (const vec*)in;
   a.gauge = PREC == PFMP_F64   ? (const vec*)(const void*)op->ctx->U64c
             : PREC == PREC_DF  ? (const vec*)(const void*)op->ctx->Udf
+            : PREC == PFMP_H16 ? (const vec*)(const void*)op->ctx->U16
                                : (const vec*)(const void*)op->ctx->U32;
   a.clov = nullptr;
   a.x = nullptr;
@@ -75,6 +76,10 @@ static HopParams<PREC> params(pfmp_op* op, int p, void* out, const void* in) {
 // blocks (72 reals) and for EPI_XPAY the local input spinor
 template <int PREC>
 static double hop_bytes(int epi, int Vh) {
+  if (PREC == PFMP_H16) {  // FP16 reals, plus the FP32 scale of every spinor read or written
+    const double b = 8 * 12 * 2 + 52 + 52 + (epi >= EPI_CLOV ? 72 * 2 : 0) + (epi == EPI_XPAY ? 52 : 0);
+    return b * (double)Vh;
+  }
   const double link = PREC == PREC_DF ? 18 : 12;
   const double reals = 8 * link + 24 + 24 + (epi >= EPI_CLOV ? 72 : 0) + (epi == EPI_XPAY ? 24 : 0);
   return reals * (PREC == PFMP_F32 ? 4 : 8) * (double)Vh;
@@ -90,17 +95,25 @@ static void launch(const HopParams<PREC>& a, pfmp_op* op) {
   pfmp_ctx* c = op->ctx;
   cudaEvent_t ev;
   prof_start(c, &ev);
-  const int ns = split_of<PREC>(op);
-  const long n = (long)a.g.Vh * ns;
   const int bs = op->hop_block;
-  switch (ns) {
-    case 2: k_hop_split<PREC, DAG, EPI, RED, 2><<<nblocks(n, bs), bs, 0, c->stream>>>(a); break;
-    case 4: k_hop_split<PREC, DAG, EPI, RED, 4><<<nblocks(n, bs), bs, 0, c->stream>>>(a); break;
-    case 8: k_hop_split<PREC, DAG, EPI, RED, 8><<<nblocks(n, bs), bs, 0, c->stream>>>(a); break;
-    default: k_hop<PREC, DAG, EPI, RED><<<nblocks(a.g.Vh, bs), bs, 0, c->stream>>>(a); break;
+  if constexpr (PREC == PFMP_H16) {  // one thread per site only
+    k_hop<PREC, DAG, EPI, RED><<<nblocks(a.g.Vh, bs), bs, 0, c->stream>>>(a);
+  } else {
+    const int ns = split_of<PREC>(op);
+    const long n = (long)a.g.Vh * ns;
+    switch (ns) {
+      case 2: k_hop_split<PREC, DAG, EPI, RED, 2><<<nblocks(n, bs), bs, 0, c->stream>>>(a); break;
+      case 4: k_hop_split<PREC, DAG, EPI, RED, 4><<<nblocks(n, bs), bs, 0, c->stream>>>(a); break;
+      case 8: k_hop_split<PREC, DAG, EPI, RED, 8><<<nblocks(n, bs), bs, 0, c->stream>>>(a); break;
+      default: k_hop<PREC, DAG, EPI, RED><<<nblocks(a.g.Vh, bs), bs, 0, c->stream>>>(a); break;
+    }
   }
   PFMP_CHECK_LAUNCH();
-  prof_stop(c, PREC == PFMP_F64 ? PFMP_KERNEL_HOP_F64 : (PREC == PREC_DF ? PFMP_KERNEL_HOP_DF : PFMP_KERNEL_HOP_F32),
+  prof_stop(c,
+            PREC == PFMP_F64   ? PFMP_KERNEL_HOP_F64
+            : PREC == PREC_DF  ? PFMP_KERNEL_HOP_DF
+            : PREC == PFMP_H16 ? PFMP_KERNEL_HOP_H16
+                               : PFMP_KERNEL_HOP_F32,
             hop_bytes<PREC>(EPI, a.g.Vh), ev);
 }
 
@@ -108,6 +121,7 @@ template <int PREC>
 static const typename Prec<PREC>::vec* clov_ptr(pfmp_op* op, int parity) {
   if (PREC == PFMP_F64) return (const typename Prec<PREC>::vec*)(const void*)op->clov64[parity];
   if (PREC == PREC_DF) return (const typename Prec<PREC>::vec*)(const void*)op->clovdf[parity];
+  if (PREC == PFMP_H16) return (const typename Prec<PREC>::vec*)(const void*)op->clov16[parity];
   return (const typename Prec<PREC>::vec*)(const void*)op->clov32[parity];
 }
 
@@ -128,6 +142,8 @@ static void hop_t(pfmp_op* op, void* out, const void* in, int p, bool dagger) {
 void hop(pfmp_op* op, int prec, void* out, const void* in, int out_parity, bool dagger) {
   if (prec == PFMP_F64)
     hop_t<PFMP_F64>(op, out, in, out_parity, dagger);
+  else if (prec == PFMP_H16)
+    hop_t<PFMP_H16>(op, out, in, out_parity, dagger);
   else
     hop_t<PFMP_F32>(op, out, in, out_parity, dagger);
 }
@@ -146,7 +162,10 @@ void clover_mul(pfmp_op* op, int prec, void* out, const void* in, int parity) {
 
 template <int PREC>
 static void mhat_t(pfmp_op* op, void* out, const void* in, bool dagger, double* norm_out, CGScalars* scal) {
-  void* t = PREC == PFMP_F64 ? (void*)op->t64 : (PREC == PREC_DF ? (void*)op->tdf : (void*)op->t32);
+  void* t = PREC == PFMP_F64   ? (void*)op->t64
+            : PREC == PREC_DF  ? (void*)op->tdf
+            : PREC == PFMP_H16 ? (void*)op->t16
+                               : (void*)op->t32;
   pfmp_op* s = op;
   // t = A_oo^{-1} H_oe in
   auto a1 = params<PREC>(op, 1, t, in);
@@ -205,6 +224,8 @@ void mhat(pfmp_op* op, int prec, void* out, const void* in, bool dagger, double*
   require_clover(op);
   if (prec == PFMP_F64)
     mhat_t<PFMP_F64>(op, out, in, dagger, norm_out, scal);
+  else if (prec == PFMP_H16)
+    mhat_t<PFMP_H16>(op, out, in, dagger, norm_out, scal);
   else
     mhat_t<PFMP_F32>(op, out, in, dagger, norm_out, scal);
 }
@@ -232,7 +253,7 @@ void hop_clov_odd(pfmp_op* op, void* out, const void* in, bool dagger) {
 // out = K in; <in, K in> = ||M-hat in||^2 is reduced in the second kernel of M-hat
 void kop(pfmp_op* op, int prec, void* out, const void* in, double* pKp_dev, CGScalars* scal) {
   op->kapply += 1;
-  void* e = prec == PFMP_F64 ? (void*)op->e64 : (void*)op->e32;
+  void* e = prec == PFMP_F64 ? (void*)op->e64 : (prec == PFMP_H16 ? (void*)op->e16 : (void*)op->e32);
   mhat(op, prec, e, in, false, pKp_dev, scal);
   mhat(op, prec, out, e, true, nullptr, scal);
 }

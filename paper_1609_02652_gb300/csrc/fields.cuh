@@ -1,6 +1,8 @@
 // Load/store of spinors, links and clover blocks in the device layouts (see
 // pfmp_internal.cuh), templated on the storage precision.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "pfmp_internal.cuh"
 
 namespace pfmp {
@@ -23,6 +25,27 @@ struct Prec<PFMP_F32> {
   static constexpr int link_vecs = 3;
   static constexpr int clover_vecs = 18;
 };
+
+template <>
+struct Prec<PFMP_H16> {  // FP16 storage, FP32 arithmetic
+  using real = float;
+  using vec = uint2;  // two complex FP16
+  static constexpr int spinor_vecs = 6;  // followed by one FP32 scale per site
+  static constexpr int link_vecs = 3;
+  static constexpr int clover_vecs = 18;
+};
+
+__device__ __forceinline__ float2 h2_to_f2(uint32_t u) {
+  __half2 h;
+  memcpy(&h, &u, 4);
+  return __half22float2(h);
+}
+__device__ __forceinline__ uint32_t f2_to_h2(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  uint32_t u;
+  memcpy(&u, &h, 4);
+  return u;
+}
 
 // ---------------------------------------------------------------- spinors
 __device__ __forceinline__ void load_spinor(Spinor<double>& s, const double2* __restrict__ f, int cb, int Vh) {
@@ -52,6 +75,32 @@ __device__ __forceinline__ void store_spinor(float4* __restrict__ f, const Spino
   }
 }
 
+// FP16: [6][Vh] uint2 (complex 2k, 2k+1 in word k) then FP32 scale[Vh]; value = scale * h
+__device__ __forceinline__ void load_spinor(Spinor<float>& s, const uint2* __restrict__ f, int cb, int Vh) {
+  const float sc = __ldg(reinterpret_cast<const float*>(f + (size_t)6 * Vh) + cb);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const uint2 v = __ldg(f + (size_t)k * Vh + cb);
+    const float2 a = h2_to_f2(v.x), b = h2_to_f2(v.y);
+    s.s[(2 * k) / 3][(2 * k) % 3] = mk(sc * a.x, sc * a.y);
+    s.s[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(sc * b.x, sc * b.y);
+  }
+}
+__device__ __forceinline__ void store_spinor(uint2* __restrict__ f, const Spinor<float>& s, int cb, int Vh) {
+  float m = 0.f;
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m = fmaxf(m, fmaxf(fabsf(s.s[sp][c].re), fabsf(s.s[sp][c].im)));
+  const float inv = m > 0.f ? 1.0f / m : 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const cplx<float> a = s.s[(2 * k) / 3][(2 * k) % 3], b = s.s[(2 * k + 1) / 3][(2 * k + 1) % 3];
+    f[(size_t)k * Vh + cb] = make_uint2(f2_to_h2(inv * a.re, inv * a.im), f2_to_h2(inv * b.re, inv * b.im));
+  }
+  reinterpret_cast<float*>(f + (size_t)6 * Vh)[cb] = m;
+}
+
 // ---------------------------------------------------------------- links (12-real)
 // link field of one (parity, mu): base pointer at [parity][mu], vectors strided by Vh
 __device__ __forceinline__ void load_link(Mat3<double>& U, const double2* __restrict__ f, int cb, int Vh) {
@@ -68,6 +117,18 @@ __device__ __forceinline__ void load_link(Mat3<float>& U, const float4* __restri
     float4 v = __ldg(f + (size_t)k * Vh + cb);
     U.m[(2 * k) / 3][(2 * k) % 3] = mk(v.x, v.y);
     U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(v.z, v.w);
+  }
+  reconstruct_row2(U);
+}
+
+// FP16 12-real link: [3][Vh] uint2, rows 0 and 1 (complex 2k, 2k+1 in word k)
+__device__ __forceinline__ void load_link(Mat3<float>& U, const uint2* __restrict__ f, int cb, int Vh) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint2 v = __ldg(f + (size_t)k * Vh + cb);
+    const float2 a = h2_to_f2(v.x), b = h2_to_f2(v.y);
+    U.m[(2 * k) / 3][(2 * k) % 3] = mk(a.x, a.y);
+    U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(b.x, b.y);
   }
   reconstruct_row2(U);
 }
@@ -139,6 +200,29 @@ __device__ __forceinline__ void load_clover(HermBlock<float> b[2], const float4*
       b[blk].o[1 + 2 * k] = mk(v.x, v.y);
       b[blk].o[2 + 2 * k] = mk(v.z, v.w);
     }
+  }
+}
+
+// FP16 clover: per block 9 words of 4 reals, the same real sequence as the FP32 layout
+// (6 diagonal reals, then the 15 lower-triangle complex entries)
+__device__ __forceinline__ void load_clover(HermBlock<float> b[2], const uint2* __restrict__ f, int cb, int Vh) {
+#pragma unroll
+  for (int blk = 0; blk < 2; ++blk) {
+    const uint2* g = f + (size_t)(9 * blk) * Vh;
+    float r[36];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const uint2 v = __ldg(g + (size_t)j * Vh + cb);
+      const float2 a = h2_to_f2(v.x), c = h2_to_f2(v.y);
+      r[4 * j] = a.x;
+      r[4 * j + 1] = a.y;
+      r[4 * j + 2] = c.x;
+      r[4 * j + 3] = c.y;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) b[blk].d[i] = r[i];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) b[blk].o[k] = mk(r[6 + 2 * k], r[7 + 2 * k]);
   }
 }
 

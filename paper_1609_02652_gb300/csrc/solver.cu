@@ -1,5 +1,7 @@
 // Conjugate gradient on K = M-hat^dag M-hat (the paper's solver, Sec. 2.1, Sec. 3.1):
 //  * CG64: FP64 throughout.
+//  * half: as mixed, with the search direction p and K p in FP16 storage (per-site FP32
+//    scales) and FP32 arithmetic; x and r stay FP32.
 //  * mixed: FP32 CG ("sloppy") with FP64 reliable updates: every time the sloppy residual
 //    has fallen by `delta` (or reached the target) the accumulated FP32 solution is
 //    added to the FP64 solution and the true residual b - K x is recomputed in FP64;
@@ -166,14 +168,16 @@ int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int c
       if (std::sqrt(rr_true / bb) < tol) break;
     }
     PFMP_CUDA(cudaMemcpyAsync(x, xa, spinor_bytes(c->g, PFMP_F64), cudaMemcpyDeviceToDevice, c->stream));
-  } else if (method == PFMP_SOLVER_CG_MIXED) {
+  } else if (method == PFMP_SOLVER_CG_MIXED || method == PFMP_SOLVER_CG_HALF) {
+    // sloppy CG: x and r in FP32; p and Kp in FP32, or in FP16 storage for CG_HALF
+    const int sp = method == PFMP_SOLVER_CG_HALF ? PFMP_H16 : PFMP_F32;
     float4* r32 = op->cg32[0];
-    float4* p32 = op->cg32[1];
-    float4* Ap32 = op->cg32[2];
+    void* p32 = sp == PFMP_H16 ? (void*)op->cg16[0] : (void*)op->cg32[1];
+    void* Ap32 = sp == PFMP_H16 ? (void*)op->cg16[1] : (void*)op->cg32[2];
     float4* xs32 = op->cg32[3];
     PFMP_CUDA(cudaMemcpyAsync(r, b, spinor_bytes(c->g, PFMP_F64), cudaMemcpyDeviceToDevice, c->stream));
     blas_copy(c, r32, PFMP_F32, r, PFMP_F64);
-    blas_copy(c, p32, PFMP_F32, r32, PFMP_F32);
+    blas_copy(c, p32, sp, r32, PFMP_F32);
     blas_zero(c, PFMP_F32, xs32);
     double rr_s = host_norm2(op, PFMP_F32, r32);
     while (total < max_iter) {
@@ -182,7 +186,7 @@ int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int c
       const double floor_rr = 0.25 * tol * tol * bb;
       if (stop < floor_rr) stop = floor_rr;
       put_scalars(op, rr_s, stop);
-      const int it = run_cg(op, PFMP_F32, xs32, r32, p32, Ap32, max_iter - total, check_every);
+      const int it = run_cg(op, sp, xs32, r32, p32, Ap32, max_iter - total, check_every);
       total += it;
       *kapply += it;
       PFMP_REQUIRE(std::isfinite(op->h_scal->rr), PFMP_E_NAN, "sloppy CG residual became NaN/Inf");
@@ -196,7 +200,7 @@ int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int c
       blas_zero(c, PFMP_F32, xs32);
       rr_s = host_norm2(op, PFMP_F32, r32);
       if (it == 0) {  // stalled: restart the direction as well
-        blas_copy(c, p32, PFMP_F32, r32, PFMP_F32);
+        blas_copy(c, p32, sp, r32, PFMP_F32);
       }
     }
   } else {

@@ -13,6 +13,13 @@ from _util import Gpu, canon, from_canon, oracle_gauge, rel_l2
 pytestmark = pytest.mark.gpu
 
 F64_BAR, F32_BAR = 1e-13, 1e-6
+# FP16 storage (unit roundoff u = 2^-11): spinors to u of their site's largest component,
+# links and clover entries (|.| <= O(1)) to u absolutely, FP32 arithmetic.  One hop sums
+# 8 products of a rounded link and a rounded spinor (~2u each, random signs) and rounds
+# the output (u): ~4u of its norm; K chains four stencil passes with FP16 intermediates
+# and the clover blocks, ~16u.  Bar: 16u = 7.8e-3 for every FP16 result.
+H16_BAR = 7.8e-3
+BARS = {0: F64_BAR, 1: F32_BAR, 3: H16_BAR}
 # several thread blocks and a ragged tail (Vh = 288, 512, 1152 with 128-thread blocks)
 LATTICES = [(6, 4, 4, 6), (4, 4, 4, 8), (4, 6, 8, 12)]
 
@@ -56,7 +63,7 @@ def test_plaquette(setup):
     assert abs(capi.pfmp_plaquette(g.ctx) - mean_plaquette(lat, U)) < 1e-14
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["f64", "f32"])
+@pytest.mark.parametrize("prec", [0, 1, 3], ids=["f64", "f32", "h16"])
 @pytest.mark.parametrize("dagger", [0, 1])
 @pytest.mark.parametrize("parity", [0, 1])
 def test_hop(setup, prec, dagger, parity):
@@ -71,7 +78,7 @@ def test_hop(setup, prec, dagger, parity):
     b_out = g.buf(prec)
     capi.pfmp_dslash(op, prec, b_out, b_in, parity, dagger)
     got = lat.mask(parity) * g.unpack(b_out, prec, parity)
-    assert rel_l2(got, ref) < (F64_BAR if prec == 0 else F32_BAR)
+    assert rel_l2(got, ref) < BARS[prec], rel_l2(got, ref)
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["f64", "f32"])
@@ -93,7 +100,7 @@ def test_clover_blocks(setup, prec):
     assert abs(capi.pfmp_op_logdet(op) - W.logdet_oo().item()) < 1e-11 * lat.V
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["f64", "f32"])
+@pytest.mark.parametrize("prec", [0, 1, 3], ids=["f64", "f32", "h16"])
 def test_mhat_and_K(setup, prec):
     from oracle.dirac import WilsonClover
 
@@ -102,7 +109,7 @@ def test_mhat_and_K(setup, prec):
     W = WilsonClover(lat, U, kappa, csw)
     op = g.op(kappa, csw)
     psi = lat.even * spinor(lat, 5)
-    bar = F64_BAR if prec == 0 else F32_BAR
+    bar = BARS[prec]
     b_in = g.pack(psi, prec, 0)
     b_out = g.buf(prec)
     for dagger, ref in [(0, W.mhat(psi)), (1, W.mhat_dag(psi))]:
@@ -157,3 +164,22 @@ def test_split_site_kernels(setup, prec, ns):
     bo1 = g.buf(prec)
     capi.pfmp_dslash(op, prec, bo1, bi, 1, 0)
     assert rel_l2(lat.odd * g.unpack(bo1, prec, 1), lat.odd * hop(lat, U, psi)) < bar
+
+
+def test_h16_storage_roundtrip(setup):
+    """FP16 spinor storage keeps every component to u = 2^-11 of its site's largest
+    |component| (round to nearest: u/2 plus the scale's own rounding), and converts
+    to and from FP32 through the library."""
+    lat, U, g, capi = setup
+    psi = lat.even * spinor(lat, 12)
+    h = g.pack(psi, 3, 0)
+    back = lat.even * g.unpack(h, 3, 0)
+    site_max = torch.view_as_real(psi).abs().amax(dim=(-1, -2, -3))
+    err = torch.view_as_real(back - psi).abs().amax(dim=(-1, -2, -3))
+    assert float((err / site_max.clamp_min(1e-30))[site_max > 0].max()) <= 2.0 ** -11
+    f = g.buf(1)
+    capi.pfmp_convert(g.ctx, f, 1, h, 3)
+    assert rel_l2(lat.even * g.unpack(f, 1, 0), back) < 1e-7
+    h2 = g.buf(3)
+    capi.pfmp_convert(g.ctx, h2, 3, f, 1)
+    assert rel_l2(lat.even * g.unpack(h2, 3, 0), back) < 1e-7

@@ -1,6 +1,7 @@
-"""GPU solves against the oracle: FP64 CG and mixed FP32/FP64-reliable-update CG reach
-a true relative residual below 1e-10, recomputed by the ORACLE's K on the GPU's
-solution, and agree with the oracle's own CG solution."""
+"""GPU solves against the oracle: FP64 CG, mixed FP32/FP64-reliable-update CG and the
+same with the stencil on FP16 storage reach a true relative residual below 1e-10,
+recomputed by the ORACLE's K on the GPU's solution, and agree with the oracle's own CG
+solution."""
 import numpy as np
 import pytest
 import torch
@@ -12,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("dims,eps,kappa", [((4, 4, 4, 8), 0.3, 0.125), ((6, 4, 4, 6), 0.5, 0.130)])
-@pytest.mark.parametrize("method", [0, 1], ids=["cg64", "mixed"])
+@pytest.mark.parametrize("method", [0, 1, 2], ids=["cg64", "mixed", "half"])
 def test_solve_true_residual(dims, eps, kappa, method):
     from oracle.dirac import WilsonClover
     from oracle.solvers import cg
@@ -35,7 +36,7 @@ def test_solve_true_residual(dims, eps, kappa, method):
         assert abs(true_res - info.true_rel_res) < 1e-11
         xo, _, _ = cg(W.K, b, tol=1e-12)
         assert rel_l2(x, xo) < 1e-8
-        if method == 1:
+        if method >= 1:
             assert info.reliable_updates >= 1
     finally:
         g.close()
