@@ -704,9 +704,9 @@ def roofline(capi, stream, l2_flush, reps=12):
             "launches": n, "avg_us": ms * 1e3 / n, "bytes_per_launch": by / n}, h16
 
 
-def kernel_only(dims, reps):
-    """K = M-hat^dag M-hat applications in FP32 on `dims` (no timing): the case the ncu
-    captures of the stencil kernels run."""
+def kernel_only(dims, reps, prec="f32"):
+    """K = M-hat^dag M-hat applications in FP32 (or on FP16 storage) on `dims` (no
+    timing): the case the ncu captures of the stencil kernels run."""
     import torch
 
     import pfmp_inputs as pin
@@ -720,13 +720,19 @@ def kernel_only(dims, reps):
     op = capi.pfmp_op_create(ctx, KAPPA, CSW)
     n32 = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F32) // 4
     a = torch.randn(n32, dtype=torch.float32, device="cuda")
+    pr = capi.PFMP_F32
+    if prec == "h16":
+        pr = capi.PFMP_H16
+        ah = torch.zeros(capi.pfmp_spinor_bytes(ctx, pr) // 4, dtype=torch.float32, device="cuda")
+        capi.pfmp_convert(ctx, ah, pr, a, capi.PFMP_F32)
+        a = ah
     o = torch.zeros_like(a)
     for _ in range(reps):
-        capi.pfmp_kop(op, capi.PFMP_F32, o, a)
+        capi.pfmp_kop(op, pr, o, a)
     torch.cuda.synchronize()
     capi.pfmp_op_destroy(op)
     capi.pfmp_ctx_destroy(ctx)
-    print(json.dumps({"kernel_only": list(dims), "reps": reps, "launches_per_rep": 4}))
+    print(json.dumps({"kernel_only": list(dims), "reps": reps, "launches_per_rep": 4, "prec": prec}))
 
 
 def nn_only(reps):
@@ -774,6 +780,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=8, help="CG iterations per CUDA-graph chunk")
     ap.add_argument("--nn-only", action="store_true",
                     help="three applications of the [1,8,8,8,1] network at 16^3x32 (for ncu captures)")
+    ap.add_argument("--kernel-prec", default="f32", choices=["f32", "h16"])
     ap.add_argument("--kernel-only", action="store_true",
                     help="only apply K (FP32) --kernel-reps times on --kernel-dims: the small case for ncu")
     ap.add_argument("--kernel-dims", default="24,24,24,48")
@@ -783,7 +790,7 @@ def main():
         nn_only(3)
         return
     if args.kernel_only:
-        kernel_only(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_reps)
+        kernel_only(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_reps, args.kernel_prec)
         return
     rank, world = dist_setup(args.gpus)
     if args.impl == "reference":
