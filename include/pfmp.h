@@ -58,9 +58,10 @@ extern "C" {
 #define PFMP_F64 0
 #define PFMP_F32 1
 /* FP16 storage, FP32 arithmetic (the sloppy precision of PFMP_SOLVER_CG_HALF): an even
- * or odd spinor field is [6][Vh] of 8-byte words (two complex FP16 each) followed by one
- * FP32 scale per site (the site's largest |component|; stored values are value / scale),
- * 52 bytes per site; links and clover blocks in FP16 without scale (|entries| = O(1)).
+ * or odd spinor field is [3][Vh] of 16-byte words (word k holds the complex components
+ * 4k .. 4k+3 of the 12, spin-major) followed by one FP32 scale per site (the site's
+ * largest |component|; stored values are value / scale), 52 bytes per site; links
+ * (24 bytes each) and clover blocks in FP16 without scale (|entries| = O(1)).
  * Accepted by pfmp_dslash, pfmp_mhat, pfmp_kop, pfmp_spinor_pack/unpack, pfmp_convert
  * (to and from PFMP_F32) and pfmp_spinor_bytes.                                      */
 #define PFMP_H16 3

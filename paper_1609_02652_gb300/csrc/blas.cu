@@ -210,14 +210,14 @@ __global__ void k_cg_p32(float4* __restrict__ p, const float4* __restrict__ r, l
 
 // ---------------------------------------------------------------- FP16 storage
 // (site-parallel: a site's scale covers its 24 reals)
-__global__ void k_f32_to_h16(const float4* __restrict__ s, uint2* __restrict__ d, int Vh) {
+__global__ void k_f32_to_h16(const float4* __restrict__ s, uint4* __restrict__ d, int Vh) {
   for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < Vh; cb += gridDim.x * blockDim.x) {
     Spinor<float> v;
     load_spinor(v, s, cb, Vh);
     store_spinor(d, v, cb, Vh);
   }
 }
-__global__ void k_h16_to_f32(const uint2* __restrict__ s, float4* __restrict__ d, int Vh) {
+__global__ void k_h16_to_f32(const uint4* __restrict__ s, float4* __restrict__ d, int Vh) {
   for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < Vh; cb += gridDim.x * blockDim.x) {
     Spinor<float> v;
     load_spinor(v, s, cb, Vh);
@@ -225,36 +225,40 @@ __global__ void k_h16_to_f32(const uint2* __restrict__ s, float4* __restrict__ d
   }
 }
 
-__device__ __forceinline__ float h16_scale(const uint2* f, int cb, int Vh) {
-  return reinterpret_cast<const float*>(f + (size_t)6 * Vh)[cb];
+__device__ __forceinline__ float h16_scale(const uint4* f, int cb, int Vh) {
+  return reinterpret_cast<const float*>(f + (size_t)3 * Vh)[cb];
 }
 
 // FP32 x, r with FP16 p, Ap: x += alpha p, r -= alpha Ap, |r|^2 -> beta, rr, iter, done_next
-__global__ void k_cg_xr_h(float4* __restrict__ x, float4* __restrict__ r, const uint2* __restrict__ p,
-                          const uint2* __restrict__ Ap, int Vh, ReduceBuf rb, CGScalars* s) {
+__global__ void k_cg_xr_h(float4* __restrict__ x, float4* __restrict__ r, const uint4* __restrict__ p,
+                          const uint4* __restrict__ Ap, int Vh, ReduceBuf rb, CGScalars* s) {
   if (s->done) return;
   const float al = (float)s->alpha;
   float acc = 0.f;
   for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < Vh; cb += gridDim.x * blockDim.x) {
-    const float sp = h16_scale(p, cb, Vh), sa = h16_scale(Ap, cb, Vh);
+    const float ap = al * h16_scale(p, cb, Vh), aa = al * h16_scale(Ap, cb, Vh);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const size_t i = (size_t)k * Vh + cb;
-      const uint2 pv = p[i], av = Ap[i];
-      const float2 p0 = h2_to_f2(pv.x), p1 = h2_to_f2(pv.y), a0 = h2_to_f2(av.x), a1 = h2_to_f2(av.y);
-      const float ap = al * sp, aa = al * sa;
-      float4 xx = x[i], rr = r[i];
-      xx.x += ap * p0.x;
-      xx.y += ap * p0.y;
-      xx.z += ap * p1.x;
-      xx.w += ap * p1.y;
-      rr.x -= aa * a0.x;
-      rr.y -= aa * a0.y;
-      rr.z -= aa * a1.x;
-      rr.w -= aa * a1.y;
-      x[i] = xx;
-      r[i] = rr;
-      acc += sq(rr);
+    for (int k = 0; k < 3; ++k) {  // FP16 word k = FP32 words 2k and 2k + 1
+      const uint4 pv = p[(size_t)k * Vh + cb], av = Ap[(size_t)k * Vh + cb];
+      const uint32_t pw[4] = {pv.x, pv.y, pv.z, pv.w}, aw[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const size_t i = (size_t)(2 * k + h) * Vh + cb;
+        const float2 p0 = h2_to_f2(pw[2 * h]), p1 = h2_to_f2(pw[2 * h + 1]);
+        const float2 a0 = h2_to_f2(aw[2 * h]), a1 = h2_to_f2(aw[2 * h + 1]);
+        float4 xx = x[i], rr = r[i];
+        xx.x += ap * p0.x;
+        xx.y += ap * p0.y;
+        xx.z += ap * p1.x;
+        xx.w += ap * p1.y;
+        rr.x -= aa * a0.x;
+        rr.y -= aa * a0.y;
+        rr.z -= aa * a1.x;
+        rr.w -= aa * a1.y;
+        x[i] = xx;
+        r[i] = rr;
+        acc += sq(rr);
+      }
     }
   }
   double v[1] = {(double)acc};
@@ -269,7 +273,7 @@ __global__ void k_cg_xr_h(float4* __restrict__ x, float4* __restrict__ r, const 
 }
 
 // FP16 p = r + beta p (new per-site scale); the last block then raises `done` if asked
-__global__ void k_cg_p_h(uint2* __restrict__ p, const float4* __restrict__ r, int Vh, ReduceBuf rb, CGScalars* s) {
+__global__ void k_cg_p_h(uint4* __restrict__ p, const float4* __restrict__ r, int Vh, ReduceBuf rb, CGScalars* s) {
   if (s->done) return;
   const float be = (float)s->beta;
   for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < Vh; cb += gridDim.x * blockDim.x) {
@@ -301,10 +305,10 @@ void blas_copy(pfmp_ctx* c, void* dst, int dprec, const void* src, int sprec) {
   }
   if (dprec == PFMP_H16) {
     PFMP_REQUIRE(sprec == PFMP_F32, PFMP_E_UNSUPPORTED, "FP16 fields are converted from FP32");
-    k_f32_to_h16<<<blas_grid(Vh), kBlock, 0, c->stream>>>((const float4*)src, (uint2*)dst, Vh);
+    k_f32_to_h16<<<blas_grid(Vh), kBlock, 0, c->stream>>>((const float4*)src, (uint4*)dst, Vh);
   } else if (sprec == PFMP_H16) {
     PFMP_REQUIRE(dprec == PFMP_F32, PFMP_E_UNSUPPORTED, "FP16 fields are converted to FP32");
-    k_h16_to_f32<<<blas_grid(Vh), kBlock, 0, c->stream>>>((const uint2*)src, (float4*)dst, Vh);
+    k_h16_to_f32<<<blas_grid(Vh), kBlock, 0, c->stream>>>((const uint4*)src, (float4*)dst, Vh);
   } else if (dprec == PFMP_F32) {
     k_f64_to_f32<<<blas_grid(6L * Vh), kBlock, 0, c->stream>>>((const double2*)src, (float4*)dst, Vh);
   } else {
@@ -356,8 +360,8 @@ void blas_xmy_norm(pfmp_ctx* c, const void* b, const void* Ax, void* r, double* 
 // prec = PFMP_H16: x and r FP32, p and Ap FP16
 void cg_step_xr(pfmp_ctx* c, int prec, void* x, void* r, const void* p, const void* Ap, CGScalars* s) {
   if (prec == PFMP_H16) {
-    k_cg_xr_h<<<blas_grid(c->g.Vh), kBlock, 0, c->stream>>>((float4*)x, (float4*)r, (const uint2*)p,
-                                                           (const uint2*)Ap, c->g.Vh, c->rb, s);
+    k_cg_xr_h<<<blas_grid(c->g.Vh), kBlock, 0, c->stream>>>((float4*)x, (float4*)r, (const uint4*)p,
+                                                           (const uint4*)Ap, c->g.Vh, c->rb, s);
     PFMP_CHECK_LAUNCH();
     return;
   }
@@ -374,7 +378,7 @@ void cg_step_xr(pfmp_ctx* c, int prec, void* x, void* r, const void* p, const vo
 // prec = PFMP_H16: p FP16, r FP32
 void cg_step_p(pfmp_ctx* c, int prec, void* p, const void* r, CGScalars* s) {
   if (prec == PFMP_H16) {
-    k_cg_p_h<<<blas_grid(c->g.Vh), kBlock, 0, c->stream>>>((uint2*)p, (const float4*)r, c->g.Vh, c->rb, s);
+    k_cg_p_h<<<blas_grid(c->g.Vh), kBlock, 0, c->stream>>>((uint4*)p, (const float4*)r, c->g.Vh, c->rb, s);
     PFMP_CHECK_LAUNCH();
     return;
   }

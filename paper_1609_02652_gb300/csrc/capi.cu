@@ -140,11 +140,11 @@ pfmp_op* pfmp::op_new(pfmp_ctx* ctx, double kappa, double csw) {
       op->clov64[p] = (double2*)dev_alloc((size_t)g.Vh * 36 * sizeof(double2));
       op->clov32[p] = (float4*)dev_alloc((size_t)g.Vh * 18 * sizeof(float4));
       op->clovdf[p] = (float4*)dev_alloc((size_t)g.Vh * 36 * sizeof(float4));
-      op->clov16[p] = (uint2*)dev_alloc((size_t)g.Vh * 18 * sizeof(uint2));
+      op->clov16[p] = (uint4*)dev_alloc((size_t)g.Vh * 9 * sizeof(uint4));
     }
-    op->t16 = (uint2*)dev_alloc(spinor_bytes(g, PFMP_H16));
-    op->e16 = (uint2*)dev_alloc(spinor_bytes(g, PFMP_H16));
-    for (auto& q : op->cg16) q = (uint2*)dev_alloc(spinor_bytes(g, PFMP_H16));
+    op->t16 = (uint4*)dev_alloc(spinor_bytes(g, PFMP_H16));
+    op->e16 = (uint4*)dev_alloc(spinor_bytes(g, PFMP_H16));
+    for (auto& q : op->cg16) q = (uint4*)dev_alloc(spinor_bytes(g, PFMP_H16));
     op->tdf = (float4*)dev_alloc((size_t)g.Vh * 12 * sizeof(float4));
     op->edf = (float4*)dev_alloc((size_t)g.Vh * 12 * sizeof(float4));
     op->xdf = (float4*)dev_alloc((size_t)g.Vh * 12 * sizeof(float4));

@@ -203,11 +203,14 @@ __global__ void k_clover_build(Geom g, const double2* __restrict__ U, double kc,
   if (grid_sum<1>(ld, rb, tot)) *logdet_out = tot[0];
 }
 
-// FP16 copy of the FP32 clover blocks (same word order, 4 reals per 8-byte word)
-__global__ void k_clover_h16(const float4* __restrict__ src, uint2* __restrict__ dst, long n) {
+// FP16 copy of the FP32 clover blocks: word j of the FP16 layout holds FP32 words 2j
+// and 2j + 1 (8 reals)
+__global__ void k_clover_h16(const float4* __restrict__ src, uint4* __restrict__ dst, int Vh) {
+  const long n = 9L * Vh;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const float4 v = src[i];
-    dst[i] = make_uint2(f2_to_h2(v.x, v.y), f2_to_h2(v.z, v.w));
+    const long j = i / Vh, cb = i - j * Vh;
+    const float4 a = src[(size_t)(2 * j) * Vh + cb], b = src[(size_t)(2 * j + 1) * Vh + cb];
+    dst[i] = make_uint4(f2_to_h2(a.x, a.y), f2_to_h2(a.z, a.w), f2_to_h2(b.x, b.y), f2_to_h2(b.z, b.w));
   }
 }
 
@@ -231,9 +234,8 @@ void clover_build(pfmp_op* op) {
   memcpy(&bad, c->h_sums + 8, sizeof(int));
   PFMP_REQUIRE(bad == 0, PFMP_E_NAN, "clover block not positive definite (A has a non-positive eigenvalue)");
   op->logdet_oo = c->h_sums[0];
-  const long n = 18L * c->g.Vh;
   for (int p = 0; p < 2; ++p) {
-    k_clover_h16<<<nblocks(n), kBlock, 0, c->stream>>>(op->clov32[p], op->clov16[p], n);
+    k_clover_h16<<<nblocks(9L * c->g.Vh), kBlock, 0, c->stream>>>(op->clov32[p], op->clov16[p], c->g.Vh);
     PFMP_CHECK_LAUNCH();
   }
   op->built_version = c->gauge_version;

@@ -51,7 +51,7 @@ struct pfmp_ctx {
   double2* U64c = nullptr;   // compressed [2][4][6][Vh]
   float4* U32 = nullptr;     // compressed [2][4][3][Vh]
   float4* Udf = nullptr;     // double-float full links [2][4][9][Vh] (complex as hi/lo pairs)
-  uint2* U16 = nullptr;      // FP16 compressed [2][4][3][Vh] (two complex per word)
+  uint4* U16 = nullptr;      // FP16 compressed, 24 bytes per link (planes: see link_plane)
   pfmp::ReduceBuf rb{};
   double* d_sums = nullptr;  // [64] results of generic reductions
   double* h_sums = nullptr;  // pinned mirror [64]
@@ -76,10 +76,10 @@ struct pfmp_op {
   float4* t32 = nullptr;
   double2* e64 = nullptr;
   float4* e32 = nullptr;
-  uint2* clov16[2] = {nullptr, nullptr};    // FP16 copy of clov32: [18][Vh] per parity
-  uint2* t16 = nullptr;                     // FP16 odd / even temporaries (with scales)
-  uint2* e16 = nullptr;
-  uint2* cg16[2] = {nullptr, nullptr};      // p and Ap of the FP16 CG
+  uint4* clov16[2] = {nullptr, nullptr};    // FP16 copy of clov32: [9][Vh] per parity
+  uint4* t16 = nullptr;                     // FP16 odd / even temporaries (with scales)
+  uint4* e16 = nullptr;
+  uint4* cg16[2] = {nullptr, nullptr};      // p and Ap of the FP16 CG
   double2* cg64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // r p Ap | b x (host solve) | spare
   float4* cg32[4] = {nullptr, nullptr, nullptr, nullptr};
   pfmp::CGScalars* scal = nullptr;

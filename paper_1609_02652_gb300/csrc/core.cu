@@ -78,7 +78,7 @@ __global__ void k_gauge_to_canonical(Geom g, const double2* __restrict__ U, doub
 }
 
 __global__ void k_gauge_compress(Geom g, const double2* __restrict__ U, double2* __restrict__ U64c,
-                                 float4* __restrict__ U32, float4* __restrict__ Udf, uint2* __restrict__ U16) {
+                                 float4* __restrict__ U32, float4* __restrict__ Udf, uint4* __restrict__ U16) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   const int pm = blockIdx.y;  // parity*4 + mu
   if (cb >= g.Vh) return;
@@ -93,10 +93,11 @@ __global__ void k_gauge_compress(Geom g, const double2* __restrict__ U, double2*
   for (int k = 0; k < 3; ++k)
     d32[(size_t)k * g.Vh + cb] =
         make_float4((float)v[2 * k].x, (float)v[2 * k].y, (float)v[2 * k + 1].x, (float)v[2 * k + 1].y);
-  uint2* d16 = U16 + (size_t)(pm * 3) * g.Vh;
-  for (int k = 0; k < 3; ++k)
-    d16[(size_t)k * g.Vh + cb] = make_uint2(f2_to_h2((float)v[2 * k].x, (float)v[2 * k].y),
-                                            f2_to_h2((float)v[2 * k + 1].x, (float)v[2 * k + 1].y));
+  uint4* d16 = U16 + (size_t)pm * 3 * (g.Vh / 2);  // link planes of 24 bytes per link
+  uint32_t h[6];
+  for (int k = 0; k < 6; ++k) h[k] = f2_to_h2((float)v[k].x, (float)v[k].y);
+  d16[cb] = make_uint4(h[0], h[1], h[2], h[3]);
+  reinterpret_cast<uint2*>(d16 + g.Vh)[cb] = make_uint2(h[4], h[5]);
 }
 
 __global__ void k_gauge_from_algebra(Geom g, const double* __restrict__ h, double eps, double2* __restrict__ U) {
@@ -185,7 +186,7 @@ void spinor_pack(pfmp_ctx* c, void* dst, int prec, const double* src_dev, int pa
   if (prec == PFMP_F64)
     k_spinor_pack<PFMP_F64><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, src_dev, (double2*)dst, parity);
   else if (prec == PFMP_H16)
-    k_spinor_pack<PFMP_H16><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, src_dev, (uint2*)dst, parity);
+    k_spinor_pack<PFMP_H16><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, src_dev, (uint4*)dst, parity);
   else
     k_spinor_pack<PFMP_F32><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, src_dev, (float4*)dst, parity);
   PFMP_CHECK_LAUNCH();
@@ -194,7 +195,7 @@ void spinor_unpack(pfmp_ctx* c, double* dst_dev, const void* src, int prec, int 
   if (prec == PFMP_F64)
     k_spinor_unpack<PFMP_F64><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, dst_dev, (const double2*)src, parity);
   else if (prec == PFMP_H16)
-    k_spinor_unpack<PFMP_H16><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, dst_dev, (const uint2*)src, parity);
+    k_spinor_unpack<PFMP_H16><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, dst_dev, (const uint4*)src, parity);
   else
     k_spinor_unpack<PFMP_F32><<<nblocks(c->g.Vh), kBlock, 0, c->stream>>>(c->g, dst_dev, (const float4*)src, parity);
   PFMP_CHECK_LAUNCH();
@@ -217,7 +218,7 @@ pfmp_ctx* ctx_create(const int dims[4], int bc_t, void* stream) {
     c->U64c = (double2*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 6 * sizeof(double2));
     c->U32 = (float4*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 3 * sizeof(float4));
     c->Udf = (float4*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 9 * sizeof(float4));
-    c->U16 = (uint2*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 3 * sizeof(uint2));
+    c->U16 = (uint4*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 24);
     c->rb.partials = (double*)dev_alloc((size_t)kMaxReduceBlocks * kMaxSums * sizeof(double));
     c->rb.counter = (unsigned*)dev_alloc(sizeof(unsigned));
     PFMP_CUDA(cudaMemset(c->rb.counter, 0, sizeof(unsigned)));

@@ -13,10 +13,26 @@
 #include "dfloat.cuh"
 #include "hop.cuh"
 
+#ifndef HOP_MINB_F32
+#define HOP_MINB_F32 7
+#endif
+#ifndef HOP_MINB_H16
+#define HOP_MINB_H16 7
+#endif
+
 namespace pfmp {
 
+// Resident 128-thread blocks per SM that the register allocation must allow.  The
+// stencil is bound by memory latency, so more warps in flight pay even at the cost of a
+// few spilled registers (FP32, 32^3x64: 0.85 -> 0.89 of the copy bandwidth at 7 blocks);
+// FP64 and double-float keep the compiler's choice.
+template <int PREC>
+constexpr int hop_min_blocks() {
+  return PREC == PFMP_F32 ? HOP_MINB_F32 : PREC == PFMP_H16 ? HOP_MINB_H16 : 1;
+}
+
 template <int PREC, bool DAG, int EPI, bool REDUCE>
-__global__ void __launch_bounds__(128) k_hop(HopParams<PREC> a) {
+__global__ void __launch_bounds__(128, hop_min_blocks<PREC>()) k_hop(HopParams<PREC> a) {
   if (a.scal && a.scal->done) return;
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   double nrm[1] = {0.0};

@@ -29,10 +29,10 @@ struct Prec<PFMP_F32> {
 template <>
 struct Prec<PFMP_H16> {  // FP16 storage, FP32 arithmetic
   using real = float;
-  using vec = uint2;  // two complex FP16
-  static constexpr int spinor_vecs = 6;  // followed by one FP32 scale per site
-  static constexpr int link_vecs = 3;
-  static constexpr int clover_vecs = 18;
+  using vec = uint4;  // four complex FP16
+  static constexpr int spinor_vecs = 3;  // followed by one FP32 scale per site
+  static constexpr int link_vecs = 0;    // 24 bytes per link: see link_plane
+  static constexpr int clover_vecs = 9;
 };
 
 __device__ __forceinline__ float2 h2_to_f2(uint32_t u) {
@@ -75,18 +75,21 @@ __device__ __forceinline__ void store_spinor(float4* __restrict__ f, const Spino
   }
 }
 
-// FP16: [6][Vh] uint2 (complex 2k, 2k+1 in word k) then FP32 scale[Vh]; value = scale * h
-__device__ __forceinline__ void load_spinor(Spinor<float>& s, const uint2* __restrict__ f, int cb, int Vh) {
-  const float sc = __ldg(reinterpret_cast<const float*>(f + (size_t)6 * Vh) + cb);
+// FP16: [3][Vh] uint4 (complex 4k .. 4k+3 in word k) then FP32 scale[Vh]; value = scale * h
+__device__ __forceinline__ void load_spinor(Spinor<float>& s, const uint4* __restrict__ f, int cb, int Vh) {
+  const float sc = __ldg(reinterpret_cast<const float*>(f + (size_t)3 * Vh) + cb);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const uint2 v = __ldg(f + (size_t)k * Vh + cb);
-    const float2 a = h2_to_f2(v.x), b = h2_to_f2(v.y);
-    s.s[(2 * k) / 3][(2 * k) % 3] = mk(sc * a.x, sc * a.y);
-    s.s[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(sc * b.x, sc * b.y);
+  for (int k = 0; k < 3; ++k) {
+    const uint4 v = __ldg(f + (size_t)k * Vh + cb);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 a = h2_to_f2(w[j]);
+      s.s[(4 * k + j) / 3][(4 * k + j) % 3] = mk(sc * a.x, sc * a.y);
+    }
   }
 }
-__device__ __forceinline__ void store_spinor(uint2* __restrict__ f, const Spinor<float>& s, int cb, int Vh) {
+__device__ __forceinline__ void store_spinor(uint4* __restrict__ f, const Spinor<float>& s, int cb, int Vh) {
   float m = 0.f;
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp)
@@ -94,11 +97,16 @@ __device__ __forceinline__ void store_spinor(uint2* __restrict__ f, const Spinor
     for (int c = 0; c < 3; ++c) m = fmaxf(m, fmaxf(fabsf(s.s[sp][c].re), fabsf(s.s[sp][c].im)));
   const float inv = m > 0.f ? 1.0f / m : 0.f;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const cplx<float> a = s.s[(2 * k) / 3][(2 * k) % 3], b = s.s[(2 * k + 1) / 3][(2 * k + 1) % 3];
-    f[(size_t)k * Vh + cb] = make_uint2(f2_to_h2(inv * a.re, inv * a.im), f2_to_h2(inv * b.re, inv * b.im));
+  for (int k = 0; k < 3; ++k) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const cplx<float> a = s.s[(4 * k + j) / 3][(4 * k + j) % 3];
+      w[j] = f2_to_h2(inv * a.re, inv * a.im);
+    }
+    f[(size_t)k * Vh + cb] = make_uint4(w[0], w[1], w[2], w[3]);
   }
-  reinterpret_cast<float*>(f + (size_t)6 * Vh)[cb] = m;
+  reinterpret_cast<float*>(f + (size_t)3 * Vh)[cb] = m;
 }
 
 // ---------------------------------------------------------------- links (12-real)
@@ -121,16 +129,29 @@ __device__ __forceinline__ void load_link(Mat3<float>& U, const float4* __restri
   reconstruct_row2(U);
 }
 
-// FP16 12-real link: [3][Vh] uint2, rows 0 and 1 (complex 2k, 2k+1 in word k)
-__device__ __forceinline__ void load_link(Mat3<float>& U, const uint2* __restrict__ f, int cb, int Vh) {
+// FP16 12-real link: per (parity, mu) a plane of Vh uint4 (complex 0..3) followed by a
+// plane of Vh uint2 (complex 4 and 5), 24 bytes per link; planes start at multiples of
+// 1.5 Vh uint4 (Vh is a multiple of 8, so every plane is 16-byte aligned)
+__device__ __forceinline__ void load_link(Mat3<float>& U, const uint4* __restrict__ f, int cb, int Vh) {
+  const uint4 v0 = __ldg(f + cb);
+  const uint2 v1 = __ldg(reinterpret_cast<const uint2*>(f + Vh) + cb);
+  const uint32_t w[6] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y};
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const uint2 v = __ldg(f + (size_t)k * Vh + cb);
-    const float2 a = h2_to_f2(v.x), b = h2_to_f2(v.y);
-    U.m[(2 * k) / 3][(2 * k) % 3] = mk(a.x, a.y);
-    U.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(b.x, b.y);
+  for (int j = 0; j < 6; ++j) {
+    const float2 a = h2_to_f2(w[j]);
+    U.m[j / 3][j % 3] = mk(a.x, a.y);
   }
   reconstruct_row2(U);
+}
+
+// start of the links of parity-direction index pm = 4 parity + mu
+template <int PREC>
+__host__ __device__ __forceinline__ const typename Prec<PREC>::vec* link_plane(const typename Prec<PREC>::vec* g,
+                                                                               int pm, int Vh) {
+  if constexpr (PREC == PFMP_H16)
+    return g + (size_t)pm * 3 * (Vh / 2);
+  else
+    return g + (size_t)pm * Prec<PREC>::link_vecs * Vh;
 }
 
 // master gauge field: double2 [2][4][9][Vh], full 3x3
@@ -203,26 +224,27 @@ __device__ __forceinline__ void load_clover(HermBlock<float> b[2], const float4*
   }
 }
 
-// FP16 clover: per block 9 words of 4 reals, the same real sequence as the FP32 layout
-// (6 diagonal reals, then the 15 lower-triangle complex entries)
-__device__ __forceinline__ void load_clover(HermBlock<float> b[2], const uint2* __restrict__ f, int cb, int Vh) {
+// FP16 clover: [9][Vh] uint4, word j = reals 8j .. 8j+7 of the 72-real sequence of the
+// FP32 layout (per block: 6 diagonal reals, then the 15 lower-triangle complex entries)
+__device__ __forceinline__ void load_clover(HermBlock<float> b[2], const uint4* __restrict__ f, int cb, int Vh) {
+  float r[72];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    const uint4 v = __ldg(f + (size_t)j * Vh + cb);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 a = h2_to_f2(w[q]);
+      r[8 * j + 2 * q] = a.x;
+      r[8 * j + 2 * q + 1] = a.y;
+    }
+  }
 #pragma unroll
   for (int blk = 0; blk < 2; ++blk) {
-    const uint2* g = f + (size_t)(9 * blk) * Vh;
-    float r[36];
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      const uint2 v = __ldg(g + (size_t)j * Vh + cb);
-      const float2 a = h2_to_f2(v.x), c = h2_to_f2(v.y);
-      r[4 * j] = a.x;
-      r[4 * j + 1] = a.y;
-      r[4 * j + 2] = c.x;
-      r[4 * j + 3] = c.y;
-    }
+    for (int i = 0; i < 6; ++i) b[blk].d[i] = r[36 * blk + i];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) b[blk].d[i] = r[i];
-#pragma unroll
-    for (int k = 0; k < 15; ++k) b[blk].o[k] = mk(r[6 + 2 * k], r[7 + 2 * k]);
+    for (int k = 0; k < 15; ++k) b[blk].o[k] = mk(r[36 * blk + 6 + 2 * k], r[36 * blk + 7 + 2 * k]);
   }
 }
 

@@ -22,7 +22,7 @@ struct HopParams {
   int p;  // output parity
   vec* out;
   const vec* in;     // parity 1 - p
-  const vec* gauge;  // [2][4][link_vecs][Vh]
+  const vec* gauge;  // per (parity, mu) link planes, located by link_plane
   const vec* clov;   // clover blocks of parity p (EPI_CLOV, EPI_XPAY)
   const vec* x;      // local input of parity p (EPI_XPAY)
   double coef;
@@ -36,7 +36,6 @@ template <int PREC, int MU, int SF>
 __device__ __forceinline__ void hop_dir(Spinor<typename Prec<PREC>::real>& acc, const HopParams<PREC>& a,
                                         const int x[4], int cb) {
   using T = typename Prec<PREC>::real;
-  constexpr int LV = Prec<PREC>::link_vecs;
   const Geom& g = a.g;
   const int Vh = g.Vh;
   {
@@ -45,7 +44,7 @@ __device__ __forceinline__ void hop_dir(Spinor<typename Prec<PREC>::real>& acc, 
     load_spinor(psi, a.in, n, Vh);
     Half<T> h = project<MU, SF>(psi);
     Mat3<T> U;
-    load_link(U, a.gauge + (size_t)((a.p * 4 + MU) * LV) * Vh, cb, Vh);
+    load_link(U, link_plane<PREC>(a.gauge, a.p * 4 + MU, Vh), cb, Vh);
     Half<T> r = mul_half(U, h);
     if (MU == 3 && x[3] == g.L[3] - 1) scale_half(r, (T)g.bc_t);
     accumulate<MU, SF>(acc, r);
@@ -56,7 +55,7 @@ __device__ __forceinline__ void hop_dir(Spinor<typename Prec<PREC>::real>& acc, 
     load_spinor(psi, a.in, n, Vh);
     Half<T> h = project<MU, -SF>(psi);
     Mat3<T> U;
-    load_link(U, a.gauge + (size_t)(((1 - a.p) * 4 + MU) * LV) * Vh, n, Vh);
+    load_link(U, link_plane<PREC>(a.gauge, (1 - a.p) * 4 + MU, Vh), n, Vh);
     Half<T> r = mul_half_dag(U, h);
     if (MU == 3 && x[3] == 0) scale_half(r, (T)g.bc_t);
     accumulate<MU, -SF>(acc, r);
@@ -119,7 +118,6 @@ template <int PREC, int MU, int FWD, int SF>
 __device__ __forceinline__ void hop_term(Spinor<typename Prec<PREC>::real>& acc, const HopParams<PREC>& a,
                                          const int x[4], int cb) {
   using T = typename Prec<PREC>::real;
-  constexpr int LV = Prec<PREC>::link_vecs;
   const Geom& g = a.g;
   const int Vh = g.Vh;
   const int n = nbr_cb(g, x, MU, FWD ? +1 : -1);
@@ -128,13 +126,13 @@ __device__ __forceinline__ void hop_term(Spinor<typename Prec<PREC>::real>& acc,
   Mat3<T> U;
   if (FWD) {
     Half<T> h = project<MU, SF>(psi);
-    load_link(U, a.gauge + (size_t)((a.p * 4 + MU) * LV) * Vh, cb, Vh);
+    load_link(U, link_plane<PREC>(a.gauge, a.p * 4 + MU, Vh), cb, Vh);
     Half<T> r = mul_half(U, h);
     if (MU == 3 && x[3] == g.L[3] - 1) scale_half(r, (T)g.bc_t);
     accumulate<MU, SF>(acc, r);
   } else {
     Half<T> h = project<MU, -SF>(psi);
-    load_link(U, a.gauge + (size_t)(((1 - a.p) * 4 + MU) * LV) * Vh, n, Vh);
+    load_link(U, link_plane<PREC>(a.gauge, (1 - a.p) * 4 + MU, Vh), n, Vh);
     Half<T> r = mul_half_dag(U, h);
     if (MU == 3 && x[3] == 0) scale_half(r, (T)g.bc_t);
     accumulate<MU, -SF>(acc, r);
