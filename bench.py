@@ -705,8 +705,9 @@ def roofline(capi, stream, l2_flush, reps=12):
 
 
 def kernel_only(dims, reps, prec="f32"):
-    """K = M-hat^dag M-hat applications in FP32 (or on FP16 storage) on `dims` (no
-    timing): the case the ncu captures of the stencil kernels run."""
+    """K = M-hat^dag M-hat applications in FP32 (or on FP16 storage) on `dims`, or true
+    residuals b - K x of FP64 fields in FP64 or double-float arithmetic (prec "f64",
+    "df"), with no timing: the case the ncu captures of the stencil kernels run."""
     import torch
 
     import pfmp_inputs as pin
@@ -718,6 +719,19 @@ def kernel_only(dims, reps, prec="f32"):
     torch.cuda.synchronize()
     capi.pfmp_gauge_from_algebra(ctx, h, EPS, capi.PFMP_DEVICE)
     op = capi.pfmp_op_create(ctx, KAPPA, CSW)
+    if prec in ("f64", "df"):
+        n64 = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F64) // 8
+        x = torch.randn(n64, dtype=torch.float64, device="cuda")
+        b = torch.randn_like(x)
+        r = torch.zeros_like(x)
+        ar = capi.PFMP_F64 if prec == "f64" else capi.PFMP_DF
+        for _ in range(reps):
+            capi.pfmp_true_residual(op, ar, r, x, b)
+        torch.cuda.synchronize()
+        capi.pfmp_op_destroy(op)
+        capi.pfmp_ctx_destroy(ctx)
+        print(json.dumps({"kernel_only": list(dims), "reps": reps, "launches_per_rep": 4, "prec": prec}))
+        return
     n32 = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F32) // 4
     a = torch.randn(n32, dtype=torch.float32, device="cuda")
     pr = capi.PFMP_F32
@@ -780,7 +794,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=8, help="CG iterations per CUDA-graph chunk")
     ap.add_argument("--nn-only", action="store_true",
                     help="three applications of the [1,8,8,8,1] network at 16^3x32 (for ncu captures)")
-    ap.add_argument("--kernel-prec", default="f32", choices=["f32", "h16"])
+    ap.add_argument("--kernel-prec", default="f32", choices=["f32", "h16", "f64", "df"])
     ap.add_argument("--kernel-only", action="store_true",
                     help="only apply K (FP32) --kernel-reps times on --kernel-dims: the small case for ncu")
     ap.add_argument("--kernel-dims", default="24,24,24,48")

@@ -81,19 +81,20 @@ __device__ __forceinline__ void load_link(Mat3<df>& U, const float4* __restrict_
   for (int k = 0; k < 9; ++k) U.m[k / 3][k % 3] = c_of(__ldg(f + (size_t)k * Vh + cb));
 }
 // clover blocks in the FP64 layout, each double2 (a, b) stored as float4 (a.hi, a.lo, b.hi, b.lo)
-__device__ __forceinline__ void load_clover(HermBlock<df> b[2], const float4* __restrict__ f, int cb, int Vh) {
+__device__ __forceinline__ void load_clover_block(HermBlock<df>& b, const float4* __restrict__ f, int blk, int cb, int Vh) {
+  const float4* g = f + (size_t)(18 * blk) * Vh;
 #pragma unroll
-  for (int blk = 0; blk < 2; ++blk) {
-    const float4* g = f + (size_t)(18 * blk) * Vh;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      float4 v = __ldg(g + (size_t)k * Vh + cb);
-      b[blk].d[2 * k] = df(v.x, v.y);
-      b[blk].d[2 * k + 1] = df(v.z, v.w);
-    }
-#pragma unroll
-    for (int k = 0; k < 15; ++k) b[blk].o[k] = c_of(__ldg(g + (size_t)(3 + k) * Vh + cb));
+  for (int k = 0; k < 3; ++k) {
+    float4 v = __ldg(g + (size_t)k * Vh + cb);
+    b.d[2 * k] = df(v.x, v.y);
+    b.d[2 * k + 1] = df(v.z, v.w);
   }
+#pragma unroll
+  for (int k = 0; k < 15; ++k) b.o[k] = c_of(__ldg(g + (size_t)(3 + k) * Vh + cb));
+}
+__device__ __forceinline__ void load_clover(HermBlock<df> b[2], const float4* __restrict__ f, int cb, int Vh) {
+  load_clover_block(b[0], f, 0, cb, Vh);
+  load_clover_block(b[1], f, 1, cb, Vh);
 }
 
 template <>

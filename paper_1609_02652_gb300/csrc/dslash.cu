@@ -25,10 +25,20 @@ namespace pfmp {
 // Resident 128-thread blocks per SM that the register allocation must allow.  The
 // stencil is bound by memory latency, so more warps in flight pay even at the cost of a
 // few spilled registers (FP32, 32^3x64: 0.85 -> 0.89 of the copy bandwidth at 7 blocks);
-// FP64 and double-float keep the compiler's choice.
+// FP64 and double-float keep the compiler's choice (a bound of 3 blocks made the rolled
+// double-float stencil 7-18% slower).
 template <int PREC>
 constexpr int hop_min_blocks() {
   return PREC == PFMP_F32 ? HOP_MINB_F32 : PREC == PFMP_H16 ? HOP_MINB_H16 : 1;
+}
+
+// Double-float arithmetic takes the rolled stencil: unrolled, its ~18k instructions per
+// thread stall on instruction fetch (ncu at 16^3x32: ~10 "no instruction" stall cycles
+// per issue, 13% of the FP32 pipe); rolled, a K application is 2.5-2.9x faster.  FP64 is
+// bound by GB300's FP64 rate and runs slower rolled (+28%), so it stays unrolled.
+template <int PREC>
+__host__ __device__ constexpr bool hop_rolled() {
+  return PREC == PREC_DF;
 }
 
 template <int PREC, bool DAG, int EPI, bool REDUCE>
@@ -37,7 +47,11 @@ __global__ void __launch_bounds__(128, hop_min_blocks<PREC>()) k_hop(HopParams<P
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   double nrm[1] = {0.0};
   if (cb < a.g.Vh) {
-    auto out = hop_site<PREC, DAG, EPI>(a, cb);
+    Spinor<typename Prec<PREC>::real> out;
+    if constexpr (hop_rolled<PREC>())
+      out = hop_site_rolled<PREC, DAG, EPI>(a, cb);
+    else
+      out = hop_site<PREC, DAG, EPI>(a, cb);
     store_spinor(a.out, out, cb, a.g.Vh);
     if (REDUCE) nrm[0] = spinor_norm2(out);
   }

@@ -176,22 +176,25 @@ struct HermBlock {
 };
 __host__ __device__ __forceinline__ int tri_index(int i, int j) { return i * (i - 1) / 2 + j; }  // i > j
 
-__device__ __forceinline__ void load_clover(HermBlock<double> b[2], const double2* __restrict__ f, int cb, int Vh) {
+// one Hermitian block (blk = 0: spins 0, 1; blk = 1: spins 2, 3)
+__device__ __forceinline__ void load_clover_block(HermBlock<double>& b, const double2* __restrict__ f, int blk, int cb,
+                                                  int Vh) {
+  const double2* g = f + (size_t)(18 * blk) * Vh;
 #pragma unroll
-  for (int blk = 0; blk < 2; ++blk) {
-    const double2* g = f + (size_t)(18 * blk) * Vh;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      double2 v = __ldg(g + (size_t)k * Vh + cb);
-      b[blk].d[2 * k] = v.x;
-      b[blk].d[2 * k + 1] = v.y;
-    }
-#pragma unroll
-    for (int k = 0; k < 15; ++k) {
-      double2 v = __ldg(g + (size_t)(3 + k) * Vh + cb);
-      b[blk].o[k] = mk(v.x, v.y);
-    }
+  for (int k = 0; k < 3; ++k) {
+    double2 v = __ldg(g + (size_t)k * Vh + cb);
+    b.d[2 * k] = v.x;
+    b.d[2 * k + 1] = v.y;
   }
+#pragma unroll
+  for (int k = 0; k < 15; ++k) {
+    double2 v = __ldg(g + (size_t)(3 + k) * Vh + cb);
+    b.o[k] = mk(v.x, v.y);
+  }
+}
+__device__ __forceinline__ void load_clover(HermBlock<double> b[2], const double2* __restrict__ f, int cb, int Vh) {
+  load_clover_block(b[0], f, 0, cb, Vh);
+  load_clover_block(b[1], f, 1, cb, Vh);
 }
 __device__ __forceinline__ void store_clover(double2* __restrict__ f, const HermBlock<double> b[2], int cb, int Vh) {
 #pragma unroll

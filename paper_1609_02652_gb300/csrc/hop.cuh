@@ -107,6 +107,134 @@ __device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site(const HopP
   return out;
 }
 
+// ---------------------------------------------------------------- rolled stencil
+// The same stencil with the 8 hop terms in a run-time loop and the two clover blocks in
+// another, so that the colour multiply and the 6x6 block product exist once in the code
+// instead of eight and two times.  The projector and rebuild of direction mu with sign S
+// are written as unit phases c in {+-1, +-i}:
+//   h0 = psi0 + c0 psi_A,  h1 = psi1 + c1 psi_B      (A, B = 3, 2 for mu < 2; 2, 3 else)
+//   out0 += r0, out1 += r1, out2 += c2 r_P, out3 += c3 r_Q  (P, Q = 1, 0 for mu < 2; 0, 1 else)
+// with c imaginary for mu = 0, 2 and, for s = sign(S),
+//   c0 = -s (mu = 1) else s;  c1 = -s (mu = 2) else s;  c2 = -s (mu even) else s;
+//   c3 = -s (mu < 2) else s
+// (the chiral-basis projectors of spin.cuh; parity tests compare both forms).  Backward
+// terms multiply by U^dag, formed in registers by selects.
+
+// v times (isI ? i : 1) times (neg ? -1 : 1)
+template <typename T>
+__device__ __forceinline__ cplx<T> unit_phase(const cplx<T>& v, bool isI, bool neg) {
+  const cplx<T> w = isI ? mk(-v.im, v.re) : v;
+  return neg ? -w : w;
+}
+
+template <typename T>
+__device__ __forceinline__ void dagger_if(Mat3<T>& U, bool dag) {
+  Mat3<T> V;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) V.m[i][j] = dag ? conj(U.m[j][i]) : U.m[i][j];
+  U = V;
+}
+
+// checkerboard index of x + dir mu for a run-time mu (static indexing only)
+__device__ __forceinline__ int nbr_cb_rt(const Geom& g, const int x[4], int mu, int dir) {
+  int y[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int v = x[m] + (m == mu ? dir : 0);
+    y[m] = v == g.L[m] ? 0 : (v < 0 ? g.L[m] - 1 : v);
+  }
+  return cb_index(g, y);
+}
+
+template <int PREC, bool DAG, int EPI>
+__device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site_rolled(const HopParams<PREC>& a, int cb) {
+  using T = typename Prec<PREC>::real;
+  const Geom& g = a.g;
+  const int Vh = g.Vh;
+  int x[4];
+  cb_coords(g, cb, a.p, x);
+  Spinor<T> acc;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc.s[s][c] = mk<T>(0, 0);
+  constexpr bool SF_POS = DAG;  // forward projector 1 + SF g_mu, SF = +1 for the adjoint
+#pragma unroll 1
+  for (int d = 0; d < 8; ++d) {
+    const int mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    const bool sp = fwd ? SF_POS : !SF_POS;  // sign of this term's projector
+    const int n = nbr_cb_rt(g, x, mu, fwd ? +1 : -1);
+    Spinor<T> psi;
+    load_spinor(psi, a.in, n, Vh);
+    const bool low = mu < 2, isI = (mu & 1) == 0;
+    const bool n0 = (mu == 1) == sp, n1 = (mu == 2) == sp, n2 = isI == sp, n3 = low == sp;
+    Half<T> h;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cplx<T> pa = low ? psi.s[3][c] : psi.s[2][c];
+      const cplx<T> pb = low ? psi.s[2][c] : psi.s[3][c];
+      h.h[0][c] = psi.s[0][c] + unit_phase(pa, isI, n0);
+      h.h[1][c] = psi.s[1][c] + unit_phase(pb, isI, n1);
+    }
+    Mat3<T> U;
+    load_link(U, link_plane<PREC>(a.gauge, (fwd ? a.p : 1 - a.p) * 4 + mu, Vh), fwd ? cb : n, Vh);
+    dagger_if(U, !fwd);
+    Half<T> r = mul_half(U, h);
+    const bool edge = mu == 3 && (fwd ? x[3] == g.L[3] - 1 : x[3] == 0);
+    const bool flip = edge && g.bc_t < 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cplx<T> r0 = flip ? -r.h[0][c] : r.h[0][c];
+      const cplx<T> r1 = flip ? -r.h[1][c] : r.h[1][c];
+      acc.s[0][c] = acc.s[0][c] + r0;
+      acc.s[1][c] = acc.s[1][c] + r1;
+      acc.s[2][c] = acc.s[2][c] + unit_phase(low ? r1 : r0, isI, n2);
+      acc.s[3][c] = acc.s[3][c] + unit_phase(low ? r0 : r1, isI, n3);
+    }
+  }
+  const T cf = (T)a.coef;
+  if (EPI == EPI_PLAIN) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc.s[s][c] = cf * acc.s[s][c];
+    return acc;
+  }
+  // clover: out = cf C acc (EPI_CLOV) or C x + cf acc (EPI_XPAY), one 6x6 block at a time
+  Spinor<T> src;
+  if (EPI == EPI_XPAY)
+    load_spinor(src, a.x, cb, Vh);
+  else
+    src = acc;
+  Spinor<T> out;
+#pragma unroll 1
+  for (int blk = 0; blk < 2; ++blk) {
+    HermBlock<T> B;
+    load_clover_block(B, a.clov, blk, cb, Vh);
+    cplx<T> v[6], y[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = blk ? src.s[2 + k / 3][k % 3] : src.s[k / 3][k % 3];
+    herm_apply(B, v, y);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int s = k / 3, c = k % 3;
+      if (EPI == EPI_CLOV) {
+        y[k] = cf * y[k];
+      } else {
+        y[k] = y[k] + cf * (blk ? acc.s[2 + s][c] : acc.s[s][c]);
+      }
+      if (blk)
+        out.s[2 + s][c] = y[k];
+      else
+        out.s[s][c] = y[k];
+    }
+  }
+  return out;
+}
+
 // ---------------------------------------------------------------- split-site kernel
 // NS threads per output site: thread t takes the hop terms t, t + NS, ... (term =
 // 2 mu + {0 forward, 1 backward}), the partial spinors are summed by a butterfly of
