@@ -4,8 +4,9 @@ Workload (one "step"): solve K x = b to a true relative residual of 1e-10 on a
 16^3 x 32 lattice -- SU(3) links U = exp(i 0.5 H) with Gaussian H (seed 1),
 Wilson-clover c_sw = 1.0, kappa = 0.130, even-odd preconditioned, Gaussian complex
 right-hand side (seed 100) -- with the mixed-precision CG (FP32 iterations, FP64
-reliable updates, FP64 true residual).  Inputs are resident in HBM when the timed
-region starts; L2 is flushed (a 512 MiB write) before every timed step.
+reliable updates whose true residual is computed to FP64 accuracy in double-float).
+Inputs are resident in HBM when the timed region starts; L2 is flushed (a 512 MiB
+write) before every timed step.
 
 Also reported on the same line:
   fp64_cg    the same solve with CG in FP64 throughout (the baseline the mixed solver
