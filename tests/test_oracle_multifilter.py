@@ -15,7 +15,7 @@ from oracle.lattice import C128, F64, Lattice, algebra_to_matrix, expi_hermitian
 MU, NU = 1.2, 0.9
 
 
-@pytest.mark.parametrize("p1,p2", [(4, 24), (4, 14), (2, 8), (6, 48), (8, 26)])
+@pytest.mark.parametrize("p1,p2", [(4, 24), (4, 14), (2, 8), (6, 48), (8, 26), (12, 64), (12, 38)])
 def test_filter_factorisation(p1, p2):
     """P_p1(z) Q(z) = P_p2(z) at arbitrary complex z, with q = p2 - p1 roots."""
     z, c = cheby.filter_roots(p1, p2, MU, NU)

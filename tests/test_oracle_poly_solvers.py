@@ -113,15 +113,18 @@ def _setup(dims=(2, 2, 2, 2), kappa=0.125, csw=1.0, seed=3):
 
 
 def test_poly_apply_against_eigendecomposition():
-    """P(J) v by the product of roots equals V P(Lambda) V^dag v on a dense 2^4 J."""
+    """P(J) v by the product of roots equals V P(Lambda) V^dag v on a dense 2^4 J, up to
+    the orders of the large filters (12, 48, 64).  In the order k = 1..n the partial
+    products pass through values far from |P|, so rounding grows with the order: measured
+    2e-15 (n <= 12), 2e-13 (48), 4e-12 (64) of max |P v|; the bars allow 5x that."""
     lat, op, b = _setup()
     Jd = dense(lat, op.K)
     lam, V = torch.linalg.eigh(Jd)
-    for n in (4, 8):
+    for n, bar in ((4, 1e-14), (8, 1e-14), (12, 1e-14), (48, 1e-12), (64, 2e-11)):
         Plam = cheby.poly_scalar(lam, n, 1.2, 0.9)
         ref = V @ (Plam * (V.conj().T @ to_parity_vector(lat, b)))
         got = to_parity_vector(lat, cheby.apply_poly(op.K, b, n, 1.2, 0.9))
-        assert (got - ref).abs().max() < 1e-12 * ref.abs().max()
+        assert (got - ref).abs().max() < bar * ref.abs().max(), n
 
 
 def test_cg_against_dense_lu():
