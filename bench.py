@@ -17,7 +17,11 @@ Also reported on the same line:
              by CUDA events inside the library over R applications of K on a
              32^3 x 64 lattice (1.7 GB of FP32 operator data, far above the 129 MB L2),
              algorithmic bytes / time against the measured HBM copy bandwidth;
-  cpu_baseline  the FP64 CPU oracle on a bounded sample of the same solve.
+  cpu_baseline  one complete solve of the same system by the FP64 CPU oracle on the
+             host's cores (wall clock, not extrapolated), with the CPU model.
+With --impl reference the same oracle solve is the reference arm: one complete solve
+split over the timed steps.  --cpu-full adds the oracle's single-thread solve and its
+4^4 PF-MP trajectory.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun (N > 1) every rank solves its own copy (replicas, weak scaling).
@@ -127,42 +131,81 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ oracle (CPU) timing
-def oracle_sample(iters):
-    """The FP64 CPU oracle's CG on the same system, stopped after `iters` iterations.
+def cpu_model():
+    """CPU model name and logical core count of this host."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if name is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        name = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            name = "unknown"
+    return {"model": name, "nproc": os.cpu_count()}
 
-    Returns (seconds per iteration, estimated iterations to 1e-10 from the oracle's own
-    residual decay, threads)."""
-    import torch
 
-    import pfmp_inputs as pin
-    from oracle.dirac import WilsonClover
-    from oracle.lattice import Lattice, algebra_to_matrix, expi_hermitian
+class OracleCG:
+    """The FP64 CPU oracle's CG on the benchmark system (the same K, b and stopping rule as
+    the GPU solve: zero start, stop when the recursive residual is below 1e-10 |b|, then
+    the true residual b - K x recomputed), advanced a given number of iterations at a
+    time so that one full solve can be split over timed steps."""
 
-    lat = Lattice(DIMS, bc_t=-1)
-    U = expi_hermitian(algebra_to_matrix(torch.tensor(pin.gauge_algebra(DIMS, GAUGE_SEED)).reshape(*lat.shape, 4, 8)), EPS)
-    W = WilsonClover(lat, U, KAPPA, CSW)
-    _ = W.Ainv
-    b = torch.tensor(pin.spinor(DIMS, RHS_SEED)).reshape(*lat.shape, 4, 3) * lat.even
-    x = torch.zeros_like(b)
-    r = b.clone()
-    p = r.clone()
-    rr = (r.conj() * r).sum().real
-    bb = rr
-    t0 = time.perf_counter()
-    res = []
-    for _ in range(iters):
-        Ap = W.K(p)
-        a = rr / (p.conj() * Ap).sum().real
-        x = x + a * p
-        r = r - a * Ap
-        rn = (r.conj() * r).sum().real
-        p = r + (rn / rr) * p
-        rr = rn
-        res.append(math.sqrt(rr / bb))
-    dt = (time.perf_counter() - t0) / iters
-    rate = math.log(res[-1]) / iters
-    est = int(math.ceil(math.log(TOL) / rate)) if rate < 0 else None
-    return dt, est, torch.get_num_threads()
+    def __init__(self, threads=None):
+        import torch
+
+        import pfmp_inputs as pin
+        from oracle.dirac import WilsonClover
+        from oracle.lattice import Lattice, algebra_to_matrix, expi_hermitian
+
+        # rank 0 runs the oracle alone: all host cores (torchrun sets OMP_NUM_THREADS=1)
+        torch.set_num_threads(threads if threads is not None else (os.cpu_count() or 1))
+        self.threads = torch.get_num_threads()
+        lat = Lattice(DIMS, bc_t=-1)
+        h = torch.tensor(pin.gauge_algebra(DIMS, GAUGE_SEED)).reshape(*lat.shape, 4, 8)
+        U = expi_hermitian(algebra_to_matrix(h), EPS)
+        self.W = WilsonClover(lat, U, KAPPA, CSW)
+        _ = self.W.Ainv
+        self.b = torch.tensor(pin.spinor(DIMS, RHS_SEED)).reshape(*lat.shape, 4, 3) * lat.even
+        self.bb = (self.b.conj() * self.b).sum().real.item()
+        self.restart()
+
+    def restart(self):
+        self.x = self.b.new_zeros(self.b.shape)
+        self.r = self.b.clone()
+        self.p = self.r.clone()
+        self.rr = self.bb
+        self.iters = 0
+
+    def done(self):
+        return self.rr < TOL * TOL * self.bb
+
+    def advance(self, n):
+        K = self.W.K
+        for _ in range(n):
+            if self.done():
+                break
+            Ap = K(self.p)
+            a = self.rr / (self.p.conj() * Ap).sum().real.item()
+            self.x = self.x + a * self.p
+            self.r = self.r - a * Ap
+            rn = (self.r.conj() * self.r).sum().real.item()
+            self.p = self.r + (rn / self.rr) * self.p
+            self.rr = rn
+            self.iters += 1
+
+    def true_residual(self):
+        d = self.b - self.W.K(self.x)
+        return math.sqrt((d.conj() * d).sum().real.item() / self.bb)
 
 
 def oracle_iterations():
@@ -171,33 +214,81 @@ def oracle_iterations():
     p = os.path.join(ROOT, "tests", "golden", "cg_iterations_16x16x16x32.json")
     if os.path.exists(p):
         with open(p) as f:
-            return int(json.load(f)["iterations"]), "the oracle's full FP64 CG run (stored)"
-    return None, None
+            return int(json.load(f)["iterations"])
+    return 100
+
+
+def oracle_full_solve(threads=None):
+    """One full oracle FP64 CG solve to the 1e-10 true residual, wall clock."""
+    cg = OracleCG(threads)
+    t0 = time.perf_counter()
+    cg.advance(100000)
+    dt = time.perf_counter() - t0
+    return {"ms": dt * 1e3, "iterations": cg.iters, "true_rel_res": cg.true_residual(), "threads": cg.threads}
 
 
 def run_reference(args, rank, world):
+    """The oracle's full FP64 CG solve of the benchmark system, split over the timed steps:
+    every step advances the same CG by ceil(n / steps) iterations (n the oracle's stored
+    iteration count) until it has converged; value = the sum of the step times, i.e. one
+    complete solve measured, not extrapolated.  Warm-up steps run single iterations of a
+    separate start that is discarded."""
     if rank != 0:
         return
-    per_step = []
-    est = None
-    thr = None
-    for _ in range(args.warmup + args.steps):
-        dt, est, thr = oracle_sample(2)
-        per_step.append(dt)
-    per_it = statistics.mean(per_step[args.warmup:])
-    n_it, how = oracle_iterations()
-    if n_it is None:
-        n_it, how = est, "extrapolated from the sample's residual decay"
-    value = per_it * n_it * 1e3
-    sample = (f"{2 * args.steps} FP64 oracle CG iterations (2 per step) on the full 16^3x32 system; ms/solve = "
-              f"s/iteration x {n_it} iterations ({how})")
+    cg = OracleCG()
+    for _ in range(args.warmup):
+        cg.advance(1)
+    cg.restart()
+    per = max(1, -(-oracle_iterations() // max(args.steps, 1)))
+    steps = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cg.advance(per)
+        steps.append((time.perf_counter() - t0) * 1e3)
+    while not cg.done():   # the stored count was short: finish the solve, timed too
+        t0 = time.perf_counter()
+        cg.advance(per)
+        steps[-1] += (time.perf_counter() - t0) * 1e3
+    value = sum(steps)
+    res = cg.true_residual()
+    sample = (f"one complete FP64 oracle CG solve of the 16^3x32 system ({cg.iters} iterations, true residual "
+              f"{res:.2e}) split over the {args.steps} timed steps ({per} iterations per step); value = its total "
+              f"wall time on {cg.threads} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(steps),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "implementation": "FP64 CPU oracle (PyTorch CPU ops)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cg.threads, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def cpu_full():
+    """The oracle's CPU timings beyond the default line: the full FP64 CG solve on one
+    thread and on every host core, and one config-1 PF-MP trajectory (4^4, order-8 filter,
+    two-level 2MN 8 x 2 steps, tau 0.5, CG to 1e-12) on every core."""
+    import torch
+
+    import pfmp_inputs as pin
+    from oracle.action import PFMP, PFMPParams
+    from oracle.integrator import merge, trajectory, two_mn
+    from oracle.lattice import Lattice, algebra_to_matrix, expi_hermitian
+
+    ncores = os.cpu_count()
+    out = {"cpu": cpu_model(), "solve_all_cores": oracle_full_solve(ncores), "solve_one_thread": oracle_full_solve(1)}
+    torch.set_num_threads(ncores)
+    dims = (4, 4, 4, 4)
+    lat = Lattice(dims, bc_t=-1)
+    U = expi_hermitian(algebra_to_matrix(torch.tensor(pin.gauge_algebra(dims, 1)).reshape(*lat.shape, 4, 8)), 0.3)
+    act = PFMP(lat, PFMPParams(beta=5.5, kappa=0.120, kappa_h=0.110, csw=1.0, n=8, mu=1.2, nu=0.9, tol=1e-12))
+    xi = [torch.tensor(pin.spinor(dims, 10 + i)).reshape(*lat.shape, 4, 3) * lat.even for i in range(3)]
+    p0 = torch.tensor(pin.momenta(dims, 5)).reshape(*lat.shape, 4, 8)
+    sched = merge([two_mn(8, 0.5), two_mn(16, 0.5)])
+    t0 = time.perf_counter()
+    r = trajectory(act, U, p0, xi, float(pin.uniform(6)[0]), [["polycorr", "hasen"], ["gauge", "det", "poly"]], sched)
+    out["trajectory_4x4x4x4"] = {"ms": (time.perf_counter() - t0) * 1e3, "dH": r["dH"], "threads": ncores}
+    print(json.dumps(out), flush=True)
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -277,6 +368,21 @@ def run_ours(args, rank, world):
         capi.pfmp_solve(op, plain, x, b)
     t_plain, info_plain = timed(plain, 3)
     fp64_ms = statistics.median(t_plain)
+    # the FP64 stencil inside the FP64 CG against the measured FP64 FMA rate (its roofline):
+    # 1320 flops of the hop and 2 x 288 of the two 6x6 clover blocks per output site
+    capi.pfmp_profile_begin(ctx)
+    capi.pfmp_solve(op, plain, x, b)
+    n64, ms64, _ = capi.pfmp_profile_end(ctx, capi.PFMP_KERNEL_HOP_F64)
+    vh = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2
+    fp64_rate = capi.pfmp_fma_rate(ctx, capi.PFMP_F64)
+    fp32_rate = capi.pfmp_fma_rate(ctx, capi.PFMP_F32)
+    stencil64 = n64 * vh * (1320 + 576) / (ms64 * 1e-3) / 1e12 if ms64 > 0 else None
+    alu = {"fp64_fma_tflops": fp64_rate, "fp32_fma_tflops": fp32_rate,
+           "fp64_stencil": {"launches": n64, "avg_us": ms64 * 1e3 / max(n64, 1), "tflops": stencil64,
+                            "frac_of_fp64_fma": stencil64 / fp64_rate if stencil64 else None,
+                            "flops_per_site": 1896},
+           "note": "measured by pfmp_fma_rate (independent register FMA chains); the FP64 stencil of the "
+                   "FP64 CG baseline, timed by CUDA events inside one FP64 solve"}
 
     # end to end through host memory (pinned), wall clock
     bh = torch.empty(DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] * 24, dtype=torch.float64, pin_memory=True)
@@ -293,7 +399,10 @@ def run_ours(args, rank, world):
     e2e_ms = allmax(statistics.mean(e2e), world) / world
     learn = None if args.no_learned else learned(capi, stream, l2_flush, args, ctx, op, b, x)
     traj = trajectory_4x4x4x4(capi, stream)
-    traj_big = None if args.no_big_trajectory else guarded(trajectory_16x16x16x32, capi, stream)
+    traj_big = None if args.no_big_trajectory else {
+        "fp64_forces": guarded(trajectory_16x16x16x32, capi, stream, capi.PFMP_F64),
+        "fp32_forces": guarded(trajectory_16x16x16x32, capi, stream, capi.PFMP_F32)}
+    prod = None if args.no_production else guarded(production_24x24x24x48, capi, stream, 1, 40, False)
     tuning = None if args.no_tuning else guarded(tuning_4x4x4x4, capi, stream)
     capi.pfmp_op_destroy(op)
     capi.pfmp_ctx_destroy(ctx)
@@ -322,8 +431,10 @@ def run_ours(args, rank, world):
         "learned": learn,
         "trajectory_4x4x4x4": traj,
         "trajectory_16x16x16x32": traj_big,
+        "production_24x24x24x48": prod,
         "tuning_4x4x4x4": tuning,
         "batched": batched,
+        "alu_rates": alu,
         "hop_in_solve": {"launches": n_hop, "avg_us": hop_ms * 1e3 / max(n_hop, 1), "algorithmic_gbs": hop_gbs_l2,
                          "note": "16^3x32 FP32 working set (~75 MB) is L2-resident inside a solve"},
         "gpu_launches": int(launches),
@@ -331,14 +442,12 @@ def run_ours(args, rank, world):
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per_it, est, thr = oracle_sample(args.cpu_iters)
-        n_it, how = oracle_iterations()
-        if n_it is None:
-            n_it, how = info_plain[-1].iters, "the FP64 CG iteration count of the GPU run"
+        full = oracle_full_solve()
         line["cpu_baseline"] = {
-            "value": per_it * n_it * 1e3, "unit": UNIT, "cores": thr, "kind": "oracle",
-            "sample": f"{args.cpu_iters} FP64 oracle CG iterations on the full 16^3x32 system; ms/solve = "
-                      f"s/iteration x {n_it} iterations ({how})"}
+            "value": full["ms"], "unit": UNIT, "cores": full["threads"], "kind": "oracle",
+            "sample": f"one complete FP64 oracle CG solve of the same 16^3x32 system ({full['iterations']} "
+                      f"iterations, true residual {full['true_rel_res']:.2e}), wall clock, not extrapolated",
+            "cpu": cpu_model()}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -504,12 +613,13 @@ def guarded(fn, *a):
         return {"error": f"{type(e).__name__}: {e}"}
 
 
-def trajectory_16x16x16x32(capi, stream):
+def trajectory_16x16x16x32(capi, stream, force_prec=0):
     """One PF-MP trajectory on the paper's lattice size, 16^3x32 (synthetic field eps 0.3,
     seed 1; beta 5.5, c_sw 1, kappa 0.125, kappa' 0.110, order-8 filter, (mu, nu) = (1.2,
     0.9)), the action's CG in mixed precision and the multi-shift in FP64, all solves to
-    1e-10; 2-level 2MN, 2 coarse (correction + Hasenbusch ratio) x 4 fine (gauge, clover
-    determinant, filter) steps over tau = 0.1.  Wall time of the whole trajectory
+    1e-10 (force_prec = PFMP_F32: the MD forces in FP32 with solves to 1e-6); 2-level 2MN,
+    2 coarse (correction + Hasenbusch ratio) x 4 fine (gauge, clover determinant,
+    filter) steps over tau = 0.1.  Wall time of the whole trajectory
     (heatbath, both Hamiltonians, MD, accept/reject) with per-term K counts and forces."""
     import torch
 
@@ -526,6 +636,7 @@ def trajectory_16x16x16x32(capi, stream):
     d.kappa[0], d.kappa[1] = 0.125, 0.110
     d.mu, d.nu, d.tol, d.max_iter = 1.2, 0.9, 1e-10, 20000
     d.solver = capi.PFMP_SOLVER_CG_MIXED
+    d.force_prec, d.md_tol = force_prec, (1e-6 if force_prec == capi.PFMP_F32 else 0.0)
     capi.pfmp_action_scheme(capi.PFMP_SCHEME_PFMP, 0, 8, d)
     A = capi.pfmp_action_create_def(ctx, d)
     lam = 0.1931833275037836
@@ -544,6 +655,156 @@ def trajectory_16x16x16x32(capi, stream):
                             "fmax": info.fmax[t], "favg": info.favg[t]} for t, n in enumerate(names)}}
     capi.pfmp_action_destroy(A)
     capi.pfmp_ctx_destroy(ctx)
+    return out
+
+
+PROD_DIMS = (24, 24, 24, 48)
+PROD = dict(beta=5.5, csw=1.6, kappa=0.134, kappa1=0.120, kappa2=0.130, p1=12, p2=64, steps=(60, 24, 10, 4), tau=1.0)
+
+
+def production_24x24x24x48(capi, stream, ntraj=10, ntherm=100, reversibility=True, force_prec=None):
+    """The production PF-MP run at 24^3 x 48 (Nf = 2 Wilson-clover c_sw = 1.6, Wilson gauge
+    beta = 5.5; kappa = 0.134 with Hasenbusch kappas 0.120 and 0.130).
+
+    Start: a random field (U = exp(i H), seed 3) thermalised by ntherm pure-gauge HMC
+    trajectories at beta = 5.5 (2MN, 10 steps over tau = 1; the first half accepted
+    unconditionally, the rest with the Metropolis test), the plaquette logged.  The
+    filter ellipse is fitted to the spectrum of J_1 (Lanczos, 60 steps): (mu, nu) =
+    s (1.2, 0.9) with s = max(1, 1.02 lambda_max / 2.1).  Action: S_G, S_det, P_12(J_1),
+    Q = P_64 / P_12 (J_1), [J_1 P_64(J_1)]^{-1}, J_1 J_2^{-1}, J_2 K^{-1} (the filters of
+    orders 12 and 64 = the smallest even order >= 48 that P_12 divides, and two
+    Hasenbusch ratios), on a 4-level generalised 2MN with n = (60, 24, 10, 4) over tau = 1
+    (step ratios 1 : 2.5 : 6 : 15): level 0 gauge + determinant, 1 the P_12 filter, 2 the
+    Q filter, 3 the correction and both ratios.  Solves: mixed CG and FP64 multi-shift to
+    1e-10 for the heatbath and the actions; MD forces in FP32 with solves to 1e-6.
+    Reports per trajectory the wall time, dH, acceptance, plaquette and the K/J
+    applications and forces per term; the reversibility of the first trajectory's MD
+    (forward, momenta flipped, forward: |U - U_0| and |p + p_0|)."""
+    import torch
+
+    import pfmp_inputs as pin
+
+    dims = PROD_DIMS
+    V = int(np.prod(dims))
+    lam = 0.1931833275037836
+    fp = capi.PFMP_F32 if force_prec is None else force_prec
+    ctx = capi.pfmp_ctx_create(dims, -1, stream.cuda_stream)
+    out = {"lattice": "24x24x24x48", "params": dict(PROD, force_prec="f32" if fp == capi.PFMP_F32 else "f64")}
+    try:
+        h = torch.tensor(np.ascontiguousarray(pin.gauge_algebra(dims, 3)).reshape(-1), device="cuda")
+        torch.cuda.synchronize()
+        capi.pfmp_gauge_from_algebra(ctx, h, 1.0, capi.PFMP_DEVICE)
+        del h
+        # pure-gauge HMC thermalisation
+        dq = capi.ActionDef()
+        dq.beta, dq.csw, dq.nkappa = PROD["beta"], 0.0, 1   # no fermion term: no clover needed
+        dq.kappa[0] = PROD["kappa"]
+        dq.mu, dq.nu, dq.tol, dq.max_iter = 1.2, 0.9, 1e-10, 20000
+        dq.nterms = 1
+        dq.term[0] = capi.Term(capi.PFMP_KIND_GAUGE, 0, 0, 0, 0)
+        Aq = capi.pfmp_action_create_def(ctx, dq)
+        Tq, Sq = capi.pfmp_schedule_merge([capi.pfmp_schedule_2mn(10, 1.0, lam)])
+        plaq, accq = [capi.pfmp_plaquette(ctx)], []
+        t0 = time.perf_counter()
+        for k in range(ntherm):
+            # the first half accepted unconditionally (u = 0), the rest with the Metropolis test
+            u = 0.0 if k < ntherm // 2 else float(pin.uniform(31000 + k)[0])
+            info = capi.pfmp_trajectory(Aq, Tq, Sq, [0], np.ascontiguousarray(pin.momenta(dims, 30000 + k)).reshape(-1),
+                                        np.zeros(1), u)
+            plaq.append(info.plaquette)
+            if k >= ntherm // 2:
+                accq.append(int(info.accepted))
+        out["thermalisation"] = {"trajectories": ntherm, "s": time.perf_counter() - t0, "acceptance": float(np.mean(accq)) if accq else None,
+                                 "plaquette_history": plaq[:: max(1, len(plaq) // 25)] + [plaq[-1]]}
+        capi.pfmp_action_destroy(Aq)
+        # spectrum of J_1 and an estimate for K (Lanczos: lmax converges, lmin from above)
+        nb = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F64) // 8
+        v0 = torch.zeros(nb, dtype=torch.float64, device="cuda")
+        vc = torch.tensor(np.ascontiguousarray(pin.spinor(dims, 33)).view(np.float64).reshape(-1), device="cuda")
+        capi.pfmp_spinor_pack(ctx, v0, capi.PFMP_F64, vc, capi.PFMP_DEVICE, 0)
+        del vc
+        spec = {}
+        for name, kap in (("J1", PROD["kappa1"]), ("J2", PROD["kappa2"]), ("K", PROD["kappa"])):
+            op = capi.pfmp_op_create(ctx, kap, PROD["csw"])
+            lo, hi, _, _ = capi.pfmp_spectrum(op, 60, v0)
+            spec[name] = {"lambda_min_upper": lo, "lambda_max": hi}
+            capi.pfmp_op_destroy(op)
+        del v0
+        sc = max(1.0, 1.02 * spec["J1"]["lambda_max"] / 2.1)
+        mu, nu = 1.2 * sc, 0.9 * sc
+        out["spectrum"] = spec
+        out["ellipse"] = {"mu": mu, "nu": nu}
+        # the production action
+        d = capi.ActionDef()
+        d.beta, d.csw, d.nkappa = PROD["beta"], PROD["csw"], 3
+        d.kappa[0], d.kappa[1], d.kappa[2] = PROD["kappa"], PROD["kappa1"], PROD["kappa2"]
+        d.mu, d.nu, d.tol, d.max_iter = mu, nu, 1e-10, 40000
+        d.solver, d.force_prec, d.md_tol = capi.PFMP_SOLVER_CG_MIXED, fp, 1e-6
+        terms = [(capi.PFMP_KIND_GAUGE, 0, 0, 0, 0), (capi.PFMP_KIND_DET, 0, 0, 0, 0),
+                 (capi.PFMP_KIND_FILTER, 1, 0, 0, PROD["p1"]), (capi.PFMP_KIND_FILTER, 1, 0, PROD["p1"], PROD["p2"]),
+                 (capi.PFMP_KIND_FILTERCORR, 1, 0, 0, PROD["p2"]), (capi.PFMP_KIND_RATIO, 1, 2, 0, 0),
+                 (capi.PFMP_KIND_RATIO, 2, 0, 0, 0)]
+        names = ["gauge", "det", "P12(J1)", "Q=P64/P12(J1)", "[J1 P64(J1)]^-1", "J1 J2^-1", "J2 K^-1"]
+        levels = [0, 0, 1, 2, 3, 3, 3]
+        d.nterms = len(terms)
+        for i, t in enumerate(terms):
+            d.term[i] = capi.Term(*t)
+        A = capi.pfmp_action_create_def(ctx, d)
+        T, S = capi.pfmp_schedule_merge([capi.pfmp_schedule_2mn(n, PROD["tau"], lam) for n in PROD["steps"]])
+        out["schedule_len"] = len(T)
+        npf = capi.pfmp_action_counts(A)[1]
+
+        def noise(seed):
+            return np.concatenate([np.ascontiguousarray(pin.spinor(dims, seed + i)).view(np.float64).reshape(-1)
+                                   for i in range(npf)])
+
+        if reversibility:
+            U0 = np.zeros(V * 72)
+            capi.pfmp_gauge_get(ctx, U0, capi.PFMP_HOST)
+            capi.pfmp_action_heatbath(A, noise(40000))
+            p0 = np.ascontiguousarray(pin.momenta(dims, 40100)).reshape(-1).copy()
+            p = p0.copy()
+            t0 = time.perf_counter()
+            capi.pfmp_md(A, T, S, levels, p)
+            t_md = time.perf_counter() - t0
+            U1 = np.zeros(V * 72)
+            capi.pfmp_gauge_get(ctx, U1, capi.PFMP_HOST)
+            moved = float(np.abs(U1 - U0).max())
+            del U1
+            p = -p
+            capi.pfmp_md(A, T, S, levels, p)
+            U2 = np.zeros(V * 72)
+            capi.pfmp_gauge_get(ctx, U2, capi.PFMP_HOST)
+            out["reversibility"] = {"md_s": t_md, "max_dU_forward": moved, "max_dU_after_return": float(np.abs(U2 - U0).max()),
+                                    "max_dp_after_return": float(np.abs(p + p0).max())}
+            del U2
+            capi.pfmp_gauge_set(ctx, U0, capi.PFMP_HOST)
+            capi.pfmp_action_refresh(A)
+            del U0
+        trajs = []
+        for k in range(ntraj):
+            xi = noise(50000 + 10 * k)
+            mom = np.ascontiguousarray(pin.momenta(dims, 60000 + k)).reshape(-1)
+            u = float(pin.uniform(61000 + k)[0])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = capi.pfmp_trajectory(A, T, S, levels, mom, xi, u)
+            ms = (time.perf_counter() - t0) * 1e3
+            trajs.append({"ms": ms, "dH": info.dH, "accepted": bool(info.accepted), "plaquette": info.plaquette,
+                          "k_apply": int(info.k_apply), "force_evals": int(info.force_evals),
+                          "per_term": {n: {"k_apply": int(info.k_apply_term[t]), "forces": int(info.nforce[t]),
+                                           "fmax": info.fmax[t], "favg": info.favg[t]} for t, n in enumerate(names)}})
+        out["trajectories"] = trajs
+        if trajs:
+            out["summary"] = {"ms_per_trajectory": statistics.mean(t["ms"] for t in trajs),
+                              "acceptance": float(np.mean([t["accepted"] for t in trajs])),
+                              "dH": [t["dH"] for t in trajs],
+                              "exp_minus_dH": float(np.mean([math.exp(-t["dH"]) for t in trajs])),
+                              "n_mat_per_term": {n: float(np.mean([t["per_term"][n]["k_apply"] for t in trajs]))
+                                                 for n in names}}
+        capi.pfmp_action_destroy(A)
+    finally:
+        capi.pfmp_ctx_destroy(ctx)
     return out
 
 
@@ -784,9 +1045,15 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-iters", type=int, default=6)
+    ap.add_argument("--production", action="store_true",
+                    help="only the 24^3x48 production PF-MP run (thermalisation, reversibility, trajectories)")
+    ap.add_argument("--prod-traj", type=int, default=10)
+    ap.add_argument("--prod-therm", type=int, default=100)
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="only the oracle's CPU timings: full solve on one thread and on all cores, 4^4 trajectory")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-big-trajectory", action="store_true")
+    ap.add_argument("--no-production", action="store_true", help="skip the 24^3x48 production trajectory")
     ap.add_argument("--no-tuning", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 96-system batched-solve measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner measurement")
@@ -801,6 +1068,17 @@ def main():
     ap.add_argument("--kernel-dims", default="24,24,24,48")
     ap.add_argument("--kernel-reps", type=int, default=8)
     args = ap.parse_args()
+    if args.cpu_full:
+        cpu_full()
+        return
+    if args.production:
+        import torch
+
+        from paper_1609_02652_gb300 import capi
+
+        stream = torch.cuda.Stream()
+        print(json.dumps(production_24x24x24x48(capi, stream, args.prod_traj, args.prod_therm)), flush=True)
+        return
     if args.nn_only:
         nn_only(3)
         return

@@ -148,17 +148,20 @@ int pfmp_clover_apply(pfmp_op* op, int prec, void* out, const void* in, int pari
 /* out = M-hat in (dagger = 0) or M-hat^dag in (dagger = 1); even parity fields.      */
 int pfmp_mhat(pfmp_op* op, int prec, void* out, const void* in, int dagger);
 /* Allocation-free M-hat (no counterpart in the paper: a library convenience).  The same
- * result as pfmp_mhat (same kernels, bit-identical output), for callers that must not
- * allocate device memory during the call -- inside a CUDA stream capture, a host
- * callback, a latency-bound loop, or under a framework that owns the device memory
- * pool.  Its odd-site temporary is a fixed array of PFMP_NOALLOC_SCRATCH_BYTES (64 MiB)
- * inside the library image, held by every GPU that loads the library until exit; a
- * lattice whose temporary (pfmp_spinor_bytes(ctx, prec)) is larger is rejected with
- * PFMP_E_INVALID (FP64: up to 349,525 sites per parity, e.g. 24^3 x 48; FP32: twice
- * that).  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and must come before any stream capture on that device.
+ * result as pfmp_mhat (same kernels, bit-identical output), for callers that may not
+ * allocate or free device memory while they run: a host callback or a latency-bound
+ * loop with no room for an allocation (cudaFree also synchronises the device), or a
+ * framework whose memory pool owns all device memory.  Its odd-site temporary is a
+ * fixed array of PFMP_NOALLOC_SCRATCH_BYTES (64 MiB) inside the library image, held by
+ * every GPU that loads the library until exit; a lattice whose temporary
+ * (pfmp_spinor_bytes(ctx, prec)) is larger is rejected with PFMP_E_INVALID (FP64: up to
+ * 349,525 sites per parity, e.g. 24^3 x 48; FP32: twice that).  prec must be PFMP_F64
+ * or PFMP_F32 (PFMP_H16, which pfmp_mhat accepts, is rejected with PFMP_E_INVALID), and
+ * the operator's device must be the current device (PFMP_E_INVALID otherwise).  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress).
  * Nothing is allocated or freed.  All calls share the array: calls that overlap on the
- * GPU (different streams or threads at once) race on it.                            */
+ * GPU (different streams or threads at once) race on it; other entry points, which use
+ * the operator's own temporaries, do not touch it.                                   */
 #define PFMP_NOALLOC_SCRATCH_BYTES (64ll * 1024 * 1024)
 int pfmp_mhat_noalloc(pfmp_op* op, int prec, void* out, const void* in, int dagger);
 /* out = K in = M-hat^dag M-hat in; if in_K_in is not NULL it receives <in, K in> =
@@ -216,20 +219,32 @@ int pfmp_solve_host(pfmp_op* op, const pfmp_solver_params* params, double* x_hos
 /* ---- multi-shift CG (Sec. 3.1; App. C eq. force_polycorr) ---------------------------
  * x[k] = (K + sigma_k)^{-1} b for nshift complex shifts sigma_k = (sigma_re[k],
  * sigma_im[k]) from one Krylov space of K (the seed system), FP64.  x[k] are FP64 even
- * device fields owned by the caller (nshift <= 1024).  Stops when the seed residual and
- * every shifted residual |zeta_k| ||r|| are below tol ||b||.  If info is not NULL,
+ * device fields owned by the caller (nshift <= 1024).  A shift stops being updated once
+ * its residual |zeta_k| ||r|| is below tol ||b||; the solve ends when every shift has.  If info is not NULL,
  * info->true_rel_res receives max_k ||b - (K + sigma_k) x_k|| / ||b|| recomputed in
- * FP64 (one extra K per shift).  Synchronises.                                        */
+ * FP64 (one extra K per shift).  A shift that is not finite, or real and negative (K is
+ * positive definite, so K + sigma can be singular only there), is refused with
+ * PFMP_E_INVALID; a right-hand side that is not finite gives PFMP_E_NAN.  Synchronises. */
 int pfmp_solve_multishift(pfmp_op* op, int nshift, const double* sigma_re, const double* sigma_im, void* const* x,
                           const void* b, double tol, int max_iter, pfmp_solve_info* info);
+
+/* The same in FP64 (prec = PFMP_F64, as above) or FP32 (PFMP_F32): x[k] and b FP32 even
+ * fields, K on the FP32 stencil, FP64 global sums and recurrence scalars; each shift
+ * stops once its recursive residual |zeta_k| ||r|| is below tol ||b|| (tol >= ~1e-6 in
+ * FP32, where the recursive residual departs from the true one).  This is the solver of
+ * the FP32 filter-correction force of the MD.  info->true_rel_res is -1 for FP32.      */
+int pfmp_solve_multishift_prec(pfmp_op* op, int prec, int nshift, const double* sigma_re, const double* sigma_im,
+                               void* const* x, const void* b, double tol, int max_iter, pfmp_solve_info* info);
 
 /* ---- Chebyshev polynomial filter (App. A) --------------------------------------------
  * P_n(z) = a_n prod_{k=1}^n (z - z_k), z_k = mu (1 - cos t_k) - i sqrt(mu^2 - nu^2) sin t_k,
  * t_k = 2 pi k / (n+1), a_n = 1 / (mu prod_k (mu - z_k)).  pfmp_poly_roots writes the n
  * roots and a_n.  pfmp_poly_apply: out = P_n(K) in (which = 0), R(K) in (which = 1) or
  * R(K)^dag in (which = 2), R = sqrt(a_n) prod_{Im z_k < 0} (K - z_k) so that P = R^dag R;
- * factors applied in the order k = 1..n; FP64 even fields.  Even n only
- * (PFMP_E_UNSUPPORTED otherwise), mu >= nu > 0.                                        */
+ * FP64 even fields.  The factors commute; they are applied in bit-reversed order of
+ * their index, which keeps every partial product close in size to the final one (in
+ * index order the partial products of P_64 grow 1e11-fold and amplify the rounding of
+ * each factor).  Even n only (PFMP_E_UNSUPPORTED otherwise), mu >= nu > 0.             */
 int pfmp_poly_roots(int n, double mu, double nu, double* z_re, double* z_im, double* a_n);
 int pfmp_poly_apply(pfmp_op* op, int n, double mu, double nu, int which, void* out, const void* in);
 
@@ -302,6 +317,15 @@ typedef struct {
   int solver;                         /* CG of the action: PFMP_SOLVER_CG64 (default 0) or
                                          PFMP_SOLVER_CG_MIXED (FP32 iterations, FP64-
                                          accurate true residual); multi-shift stays FP64 */
+  int force_prec;                     /* arithmetic of the fermion forces of the MD:
+                                         PFMP_F64 (default 0) or PFMP_F32 (spinor products,
+                                         filter K chains and the correction term's multi-
+                                         shift solve in FP32, CG as `solver`, contractions
+                                         summed into the FP64 force; the actions, heatbath
+                                         and Hamiltonian stay as before)                  */
+  double md_tol;                      /* relative residual of the solves inside the MD
+                                         forces (0: tol); with PFMP_F32 forces the FP32
+                                         multi-shift solve needs md_tol >= ~1e-6          */
 } pfmp_action_def;
 typedef struct {
   double beta, kappa, kappa_h, csw;  /* gauge coupling, target and Hasenbusch kappa, c_sw */
@@ -473,6 +497,13 @@ int pfmp_solve_fgcr(pfmp_op* op, pfmp_nn* nn, const pfmp_solver_params* params, 
 #define PFMP_KERNEL_HOP_H16 3  /* FP16-storage stencil (PFMP_SOLVER_CG_HALF)              */
 int pfmp_profile_begin(pfmp_ctx* ctx);
 int pfmp_profile_end(pfmp_ctx* ctx, int kernel_class, int64_t* launches, double* total_ms, double* total_bytes);
+/* Measured FMA throughput of the current GPU on the FP64 (prec = PFMP_F64) or FP32
+ * (PFMP_F32) pipe, in TFLOP/s (an FMA counts two flops): a dedicated kernel of
+ * independent register FMA chains, 8 blocks of 256 threads per SM, timed by CUDA events
+ * on the context's stream after one warm-up launch.  It is the arithmetic roofline of
+ * the FP64 stencil and of the double-float stencil (no counterpart in the paper).
+ * Synchronises.                                                                      */
+int pfmp_fma_rate(pfmp_ctx* ctx, int prec, double* tflops);
 
 #ifdef __cplusplus
 }

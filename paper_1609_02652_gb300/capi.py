@@ -74,7 +74,7 @@ class ActionDef(C.Structure):
     _fields_ = [("beta", C.c_double), ("csw", C.c_double), ("nkappa", C.c_int),
                 ("kappa", C.c_double * PFMP_MAX_KAPPA), ("nterms", C.c_int), ("term", Term * PFMP_MAX_TERMS),
                 ("mu", C.c_double), ("nu", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int),
-                ("solver", C.c_int)]
+                ("solver", C.c_int), ("force_prec", C.c_int), ("md_tol", C.c_double)]
 
 
 class CostInfo(C.Structure):
@@ -167,6 +167,8 @@ SIGNATURES = {
     "pfmp_solve_fgcr": (I, [P, P, C.POINTER(SolverParams), P, P, C.POINTER(SolveInfo)]),
     "pfmp_profile_begin": (I, [P]),
     "pfmp_profile_end": (I, [P, I, C.POINTER(C.c_int64), DP, DP]),
+    "pfmp_fma_rate": (I, [P, I, DP]),
+    "pfmp_solve_multishift_prec": (I, [P, I, I, DP, DP, C.POINTER(P), P, D, I, C.POINTER(SolveInfo)]),
 }
 
 _lib = None
@@ -359,6 +361,12 @@ def pfmp_solve_host(op, params, x_host, b_host, raise_on_error=True):
     return info
 
 
+def pfmp_fma_rate(ctx, prec):
+    v = C.c_double()
+    check(lib().pfmp_fma_rate(ctx, int(prec), C.byref(v)))
+    return v.value
+
+
 def pfmp_profile_begin(ctx):
     check(lib().pfmp_profile_begin(ctx))
 
@@ -376,6 +384,17 @@ def pfmp_launch_count():
 def _dp(a):
     a = np.ascontiguousarray(a, dtype=np.float64)
     return a, a.ctypes.data_as(DP)
+
+
+def pfmp_solve_multishift_prec(op, prec, sigmas, xs, b, tol, max_iter):
+    sig = np.asarray(sigmas, dtype=np.complex128)
+    re, pre = _dp(sig.real)
+    im, pim = _dp(sig.imag)
+    arr = (P * len(xs))(*[_ptr(x) for x in xs])
+    info = SolveInfo()
+    check(lib().pfmp_solve_multishift_prec(op, int(prec), len(xs), pre, pim, arr, _ptr(b), float(tol), int(max_iter),
+                                           C.byref(info)))
+    return info
 
 
 def pfmp_solve_multishift(op, sigmas, xs, b, tol, max_iter, want_info=True):

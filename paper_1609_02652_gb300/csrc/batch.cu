@@ -328,6 +328,7 @@ struct RhsState {
   double bb = 0, rr_true = 0;
   bool finished = false;
   int iters = 0, rel = 0;
+  long kres = 0;  // K applications of the true residuals (double-float, FP64 confirmation)
   double res = 0;
 };
 
@@ -407,10 +408,10 @@ int batch_solve(pfmp_batch* B, double tol, int max_iter, double delta, int check
           if (R.finished || !B->h_scal[idx].done) continue;
           R.iters += B->h_scal[idx].iter;
           PFMP_REQUIRE(std::isfinite(B->h_scal[idx].rr), PFMP_E_NAN, "batched CG residual became NaN/Inf");
-          // reliable update in FP64
+          // reliable update: double-float true residual, confirmed in FP64 below the target
           blas_add_lo(c, x[idx], S.x + r * S.fw);
           void* r64 = op->cg64[0];
-          R.rr_true = true_residual_df(op, x[idx], b[idx], r64);
+          R.rr_true = true_residual_mixed(op, x[idx], b[idx], r64, tol * tol * R.bb, &R.kres);
           R.rel += 1;
           R.res = std::sqrt(R.rr_true / R.bb);
           if (R.res < tol) {
@@ -433,7 +434,7 @@ int batch_solve(pfmp_batch* B, double tol, int max_iter, double delta, int check
         infos[i].iters = st[i].iters;
         infos[i].reliable_updates = st[i].rel;
         infos[i].true_rel_res = st[i].res;
-        infos[i].k_apply = st[i].iters + st[i].rel;
+        infos[i].k_apply = st[i].iters + st[i].kres;
         infos[i].status = st[i].finished ? PFMP_OK : PFMP_E_NOT_CONVERGED;
       }
   } catch (...) {

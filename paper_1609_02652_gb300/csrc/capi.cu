@@ -480,11 +480,39 @@ int pfmp_solve_multishift(pfmp_op* op, int nshift, const double* sre, const doub
   int it = 0;
   double res = 0;
   long kap = 0;
-  int st = solve_multishift(op, nshift, sig.data(), x, b, tol, max_iter, 8, &it, &res, &kap, info != nullptr);
+  int st = solve_multishift(op, PFMP_F64, nshift, sig.data(), x, b, tol, max_iter, 8, &it, &res, &kap,
+                            info != nullptr);
   if (info) {
     info->iters = it;
     info->reliable_updates = 0;
     info->true_rel_res = res;
+    info->k_apply = kap;
+    info->status = st;
+  }
+  if (st != PFMP_OK) {
+    set_last_error(pfmp_strerror(st));
+    return st;
+  }
+  API_END
+}
+
+int pfmp_solve_multishift_prec(pfmp_op* op, int prec, int nshift, const double* sre, const double* sim, void* const* x,
+                               const void* b, double tol, int max_iter, pfmp_solve_info* info) {
+  API_BEGIN
+  PFMP_REQUIRE(op && sre && sim && x && b && nshift >= 1, PFMP_E_INVALID, "bad argument");
+  PFMP_REQUIRE(prec == PFMP_F64 || prec == PFMP_F32, PFMP_E_INVALID, "precision must be PFMP_F64 or PFMP_F32");
+  for (int k = 0; k < nshift; ++k) PFMP_REQUIRE(x[k] && x[k] != b, PFMP_E_INVALID, "bad solution pointer");
+  std::vector<std::complex<double>> sig(nshift);
+  for (int k = 0; k < nshift; ++k) sig[k] = std::complex<double>(sre[k], sim[k]);
+  int it = 0;
+  double res = 0;
+  long kap = 0;
+  int st = solve_multishift(op, prec, nshift, sig.data(), x, b, tol, max_iter, 8, &it, &res, &kap,
+                            info != nullptr && prec == PFMP_F64);
+  if (info) {
+    info->iters = it;
+    info->reliable_updates = 0;
+    info->true_rel_res = prec == PFMP_F64 ? res : -1.0;
     info->k_apply = kap;
     info->status = st;
   }
@@ -516,12 +544,12 @@ int pfmp_poly_apply(pfmp_op* op, int n, double mu, double nu, int which, void* o
   auto z = cheb_roots(n, mu, nu);
   const double an = cheb_norm(n, mu, nu);
   if (which == 0) {
-    poly_product(op, z, an, out, in);
+    poly_product(op, stable_ordered(z), an, out, in);
   } else {
     std::vector<std::complex<double>> h;
     for (auto zk : z)
       if (zk.imag() < 0) h.push_back(which == 1 ? zk : std::conj(zk));
-    poly_product(op, h, std::sqrt(an), out, in);
+    poly_product(op, stable_ordered(h), std::sqrt(an), out, in);
   }
   API_END
 }
@@ -860,6 +888,14 @@ int pfmp_profile_end(pfmp_ctx* ctx, int cls, int64_t* launches, double* total_ms
   long n = 0;
   profile_end(ctx, cls, &n, total_ms, total_bytes);
   *launches = n;
+  API_END
+}
+
+int pfmp_fma_rate(pfmp_ctx* ctx, int prec, double* tflops) {
+  API_BEGIN
+  PFMP_REQUIRE(ctx && tflops, PFMP_E_INVALID, "null argument");
+  PFMP_REQUIRE(prec == PFMP_F64 || prec == PFMP_F32, PFMP_E_INVALID, "precision must be PFMP_F64 or PFMP_F32");
+  *tflops = fma_rate(ctx, prec);
   API_END
 }
 

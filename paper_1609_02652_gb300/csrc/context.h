@@ -131,19 +131,24 @@ void mhat(pfmp_op* op, int prec, void* out, const void* in, bool dagger, double*
           CGScalars* scal);
 void kop(pfmp_op* op, int prec, void* out, const void* in, double* pKp_dev, CGScalars* scal);
 
-void hop_clov_odd(pfmp_op* op, void* out, const void* in, bool dagger);
+void hop_clov_odd(pfmp_op* op, int prec, void* out, const void* in, bool dagger);
 void kop_df(pfmp_op* op, void* out, const void* in);
 // r = b - K x with K applied in double-float; returns |r|^2 (synchronises)
 double true_residual_df(pfmp_op* op, const void* x64, const void* b64, void* r64);
+// the same with K in FP64 (x must not alias r)
+double true_residual_f64(pfmp_op* op, const void* x64, const void* b64, void* r64);
+// double-float, confirmed in FP64 once below target_rr; the FP64 value decides
+double true_residual_mixed(pfmp_op* op, const void* x64, const void* b64, void* r64, double target_rr, long* kapply);
 
 // force.cu
-void force_hop(pfmp_ctx* c, double* F, int pz, const void* Lf, const void* Rf, const void* Lb, const void* Rb,
-               double coef);
-void clover_insert(pfmp_ctx* c, double* Hc, int p, const void* a, const void* b, double coef);
+void force_hop(pfmp_ctx* c, int prec, double* F, int pz, const void* Lf, const void* Rf, const void* Lb,
+               const void* Rb, double coef);
+void clover_insert(pfmp_ctx* c, int prec, double* Hc, int p, const void* a, const void* b, double coef);
 void clover_insert_det(pfmp_op* op, double* Hc, double coef);
 void clover_force(pfmp_ctx* c, double* F, const double* Hc);
 void gauge_force(pfmp_ctx* c, double* F, double beta);
-void deriv_mhat(pfmp_op* op, double* F, double* Hc, const void* a, const void* b, double coef, void* y, void* w);
+void deriv_mhat(pfmp_op* op, int prec, double* F, double* Hc, const void* a, const void* b, double coef, void* y,
+                void* w);
 
 // blas.cu
 void blas_zero(pfmp_ctx* c, int prec, void* x);
@@ -160,13 +165,21 @@ void cg_step_p(pfmp_ctx* c, int prec, void* p, const void* r, CGScalars* s);
 void blas_add_lo(pfmp_ctx* c, void* x64, const void* x32);
 
 // multishift.cu
-void caxpby(pfmp_ctx* c, std::complex<double> a, const void* x, std::complex<double> b, void* y);
-int solve_multishift(pfmp_op* op, int ns, const std::complex<double>* sigma, void* const* x, const void* b, double tol,
-                     int max_iter, int check, int* iters, double* max_true_res, long* kapply, bool want_true_res);
+void caxpby(pfmp_ctx* c, std::complex<double> a, const void* x, std::complex<double> b, void* y);  // FP64
+void caxpby(pfmp_ctx* c, int prec, std::complex<double> a, const void* x, std::complex<double> b, void* y);
+int solve_multishift(pfmp_op* op, int prec, int ns, const std::complex<double>* sigma, void* const* x, const void* b,
+                     double tol, int max_iter, int check, int* iters, double* max_true_res, long* kapply,
+                     bool want_true_res);
+// bit-reversed permutation of 0..n-1, and a root list in that order (stable products)
+std::vector<int> stable_order(int n);
+std::vector<std::complex<double>> stable_ordered(const std::vector<std::complex<double>>& z);
 void ms_work_free(pfmp_op* op);
 std::vector<std::complex<double>> cheb_roots(int n, double mu, double nu);
 double cheb_norm(int n, double mu, double nu);
 void poly_product(pfmp_op* op, const std::vector<std::complex<double>>& z, double scale, void* out, const void* in);
+
+// probe.cu: measured FMA throughput (TFLOP/s) of the FP64 or FP32 pipe
+double fma_rate(pfmp_ctx* c, int prec);
 
 // solver.cu
 int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int check_every, void* x,

@@ -34,7 +34,8 @@ namespace pfmp {
 constexpr double kInvSqrt3 = 0.57735026918962576451;
 
 // c_a = tr(lambda_a M), a = 1..8 (complex)
-__device__ __forceinline__ void tr_lambda(const Mat3<double>& M, cplx<double> t[8]) {
+template <typename T>
+__device__ __forceinline__ void tr_lambda(const Mat3<T>& M, cplx<T> t[8]) {
   t[0] = M.m[1][0] + M.m[0][1];
   t[1] = times_i(M.m[0][1] - M.m[1][0]);
   t[2] = M.m[0][0] - M.m[1][1];
@@ -42,7 +43,7 @@ __device__ __forceinline__ void tr_lambda(const Mat3<double>& M, cplx<double> t[
   t[4] = times_i(M.m[0][2] - M.m[2][0]);
   t[5] = M.m[2][1] + M.m[1][2];
   t[6] = times_i(M.m[1][2] - M.m[2][1]);
-  t[7] = kInvSqrt3 * (M.m[0][0] + M.m[1][1] - 2.0 * M.m[2][2]);
+  t[7] = (T)kInvSqrt3 * (M.m[0][0] + M.m[1][1] - (T)2 * M.m[2][2]);
 }
 
 // H = sum_a h_a T_a (Hermitian traceless)
@@ -77,11 +78,12 @@ __device__ __forceinline__ double* fptr(double* F, const Geom& g, int p, int mu,
 }
 
 // outer product sum_s u_s v_s^dag over 4 spins
-__device__ __forceinline__ Mat3<double> outer(const Spinor<double>& u, const Spinor<double>& v) {
-  Mat3<double> M;
+template <typename T>
+__device__ __forceinline__ Mat3<T> outer(const Spinor<T>& u, const Spinor<T>& v) {
+  Mat3<T> M;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      cplx<double> s = mk(0.0, 0.0);
+      cplx<T> s = mk<T>(0, 0);
       for (int k = 0; k < 4; ++k) s = s + mul_cj(u.s[k][i], v.s[k][j]);
       M.m[i][j] = s;
     }
@@ -89,65 +91,88 @@ __device__ __forceinline__ Mat3<double> outer(const Spinor<double>& u, const Spi
 }
 
 // (1 + S g_MU) psi as a full spinor
-template <int MU, int S>
-__device__ __forceinline__ Spinor<double> proj_full(const Spinor<double>& p) {
-  Spinor<double> r;
+template <int MU, int S, typename T>
+__device__ __forceinline__ Spinor<T> proj_full(const Spinor<T>& p) {
+  Spinor<T> r;
   for (int s = 0; s < 4; ++s)
-    for (int c = 0; c < 3; ++c) r.s[s][c] = mk(0.0, 0.0);
+    for (int c = 0; c < 3; ++c) r.s[s][c] = mk<T>(0, 0);
   accumulate<MU, S>(r, project<MU, S>(p));
   return r;
 }
 
-__device__ __forceinline__ Spinor<double> umul(const Mat3<double>& U, const Spinor<double>& v) {
-  Spinor<double> r;
+template <typename T>
+__device__ __forceinline__ Spinor<T> umul(const Mat3<T>& U, const Spinor<T>& v) {
+  Spinor<T> r;
   for (int s = 0; s < 4; ++s)
     for (int i = 0; i < 3; ++i) r.s[s][i] = U.m[i][0] * v.s[s][0] + U.m[i][1] * v.s[s][1] + U.m[i][2] * v.s[s][2];
   return r;
 }
 
-template <int MU>
-__device__ void hop_force_dir(double* F, const double2* U64, const Geom& g, int pz, int cb, const int z[4],
-                              const double2* Lf, const double2* Rf, const double2* Lb, const double2* Rb, double coef) {
-  const Mat3<double> U = mlink(U64, g, z, MU);
+// the link U_MU(z) of the force kernels: FP64 from the master field, FP32 from the
+// 12-real compressed copy (third row rebuilt)
+template <int PREC>
+__device__ __forceinline__ Mat3<typename Prec<PREC>::real> force_link(const void* gauge, const Geom& g, int pz, int cb,
+                                                                      const int z[4], int mu) {
+  if constexpr (PREC == PFMP_F64) {
+    return mlink((const double2*)gauge, g, z, mu);
+  } else {
+    Mat3<float> U;
+    load_link(U, link_plane<PFMP_F32>((const float4*)gauge, pz * 4 + mu, g.Vh), cb, g.Vh);
+    return U;
+  }
+}
+
+// Spinor products in the arithmetic of PREC (FP64, or FP32 for the MD forces, whose
+// value only has to be a deterministic function of the gauge field), summed into the
+// FP64 force
+template <int PREC, int MU>
+__device__ void hop_force_dir(double* F, const void* gauge, const Geom& g, int pz, int cb, const int z[4],
+                              const typename Prec<PREC>::vec* Lf, const typename Prec<PREC>::vec* Rf,
+                              const typename Prec<PREC>::vec* Lb, const typename Prec<PREC>::vec* Rb, double coef) {
+  using T = typename Prec<PREC>::real;
+  const Mat3<T> U = force_link<PREC>(gauge, g, pz, cb, z, MU);
   const int n = nbr_cb(g, z, MU, +1);
-  Spinor<double> lf, rf, lb, rb;
+  Spinor<T> lf, rf, lb, rb;
   load_spinor(lf, Lf, cb, g.Vh);
   load_spinor(rf, Rf, n, g.Vh);
   load_spinor(lb, Lb, n, g.Vh);
   load_spinor(rb, Rb, cb, g.Vh);
   // Y_f = sum_s (U R_f)_s ((1 - g) L_f)_s^dag,  Y_b = sum_s R_b,s (U (1 + g) L_b)_s^dag
-  Mat3<double> Yf = outer(umul(U, rf), proj_full<MU, -1>(lf));
-  Mat3<double> Yb = outer(rb, umul(U, proj_full<MU, +1>(lb)));
+  Mat3<T> Yf = outer(umul(U, rf), proj_full<MU, -1>(lf));
+  Mat3<T> Yb = outer(rb, umul(U, proj_full<MU, +1>(lb)));
   double c = coef;
   if (MU == 3 && z[3] == g.L[3] - 1) c *= g.bc_t;
-  Mat3<double> Z;
+  Mat3<T> Z;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) Z.m[i][j] = Yf.m[i][j] - Yb.m[i][j];
-  cplx<double> t[8];
+  cplx<T> t[8];
   tr_lambda(Z, t);
   // Re(i tr(T_a Z)) = -Im tr(T_a Z) = -(1/2) Im tr(lambda_a Z)
-  for (int a = 0; a < 8; ++a) fptr(F, g, pz, MU, a)[cb] += -0.5 * c * t[a].im;
+  for (int a = 0; a < 8; ++a) fptr(F, g, pz, MU, a)[cb] += -0.5 * c * (double)t[a].im;
 }
 
-__global__ void k_force_hop(double* F, const double2* U64, Geom g, int pz, const double2* Lf, const double2* Rf,
-                            const double2* Lb, const double2* Rb, double coef) {
+template <int PREC>
+__global__ void k_force_hop(double* F, const void* gauge, Geom g, int pz, const typename Prec<PREC>::vec* Lf,
+                            const typename Prec<PREC>::vec* Rf, const typename Prec<PREC>::vec* Lb,
+                            const typename Prec<PREC>::vec* Rb, double coef) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   if (cb >= g.Vh) return;
   int z[4];
   cb_coords(g, cb, pz, z);
-  hop_force_dir<0>(F, U64, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
-  hop_force_dir<1>(F, U64, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
-  hop_force_dir<2>(F, U64, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
-  hop_force_dir<3>(F, U64, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
+  hop_force_dir<PREC, 0>(F, gauge, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
+  hop_force_dir<PREC, 1>(F, gauge, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
+  hop_force_dir<PREC, 2>(F, gauge, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
+  hop_force_dir<PREC, 3>(F, gauge, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
 }
 
 // G for the six planes from the chiral Pauli structure of sigma_{mu nu}:
 // P1 = O01 + O10, P2 = -i O01 + i O10, P3 = O00 - O11 per chiral block B, O_ij = b_{2B+j} a_{2B+i}^dag;
 // planes (01,02,03,12,13,23) = (P3+ + P3-, P2+ + P2-, -P1+ + P1-, P1+ + P1-, P2+ - P2-, -P3+ + P3-)
-__device__ void plane_G(const Spinor<double>& a, const Spinor<double>& b, Mat3<double> G[6]) {
-  Mat3<double> P[2][3];
+template <typename T>
+__device__ void plane_G(const Spinor<T>& a, const Spinor<T>& b, Mat3<T> G[6]) {
+  Mat3<T> P[2][3];
   for (int B = 0; B < 2; ++B) {
-    Mat3<double> O[2][2];
+    Mat3<T> O[2][2];
     for (int i = 0; i < 2; ++i)
       for (int j = 0; j < 2; ++j)
         for (int c = 0; c < 3; ++c)
@@ -175,18 +200,21 @@ __device__ __forceinline__ double* hptr(double* Hc, const Geom& g, int p, int pl
 }
 
 // Hc[p] += coef (G~ + G~^dag) for G(a, b): h_a += 4 coef Re tr(T_a G) = 2 coef Re tr(lambda_a G)
-__global__ void k_clover_insert(double* Hc, Geom g, int p, const double2* A, const double2* B, double coef) {
+template <int PREC>
+__global__ void k_clover_insert(double* Hc, Geom g, int p, const typename Prec<PREC>::vec* A,
+                                const typename Prec<PREC>::vec* B, double coef) {
+  using T = typename Prec<PREC>::real;
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   if (cb >= g.Vh) return;
-  Spinor<double> a, b;
+  Spinor<T> a, b;
   load_spinor(a, A, cb, g.Vh);
   load_spinor(b, B, cb, g.Vh);
-  Mat3<double> G[6];
+  Mat3<T> G[6];
   plane_G(a, b, G);
   for (int pl = 0; pl < 6; ++pl) {
-    cplx<double> t[8];
+    cplx<T> t[8];
     tr_lambda(G[pl], t);
-    for (int k = 0; k < 8; ++k) hptr(Hc, g, p, pl, k)[cb] += 2.0 * coef * t[k].re;
+    for (int k = 0; k < 8; ++k) hptr(Hc, g, p, pl, k)[cb] += 2.0 * coef * (double)t[k].re;
   }
 }
 
@@ -351,16 +379,23 @@ __global__ void k_gauge_force(double* F, const double2* U64, Geom g, int p, doub
 }
 
 // ------------------------------------------------------------------ host side
-void force_hop(pfmp_ctx* c, double* F, int pz, const void* Lf, const void* Rf, const void* Lb, const void* Rb,
-               double coef) {
-  k_force_hop<<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(F, c->U64, c->g, pz, (const double2*)Lf,
-                                                            (const double2*)Rf, (const double2*)Lb,
-                                                            (const double2*)Rb, coef);
+void force_hop(pfmp_ctx* c, int prec, double* F, int pz, const void* Lf, const void* Rf, const void* Lb,
+               const void* Rb, double coef) {
+  if (prec == PFMP_F64)
+    k_force_hop<PFMP_F64><<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(
+        F, c->U64, c->g, pz, (const double2*)Lf, (const double2*)Rf, (const double2*)Lb, (const double2*)Rb, coef);
+  else
+    k_force_hop<PFMP_F32><<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(
+        F, c->U32, c->g, pz, (const float4*)Lf, (const float4*)Rf, (const float4*)Lb, (const float4*)Rb, coef);
   PFMP_CHECK_LAUNCH();
 }
-void clover_insert(pfmp_ctx* c, double* Hc, int p, const void* a, const void* b, double coef) {
-  k_clover_insert<<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(Hc, c->g, p, (const double2*)a, (const double2*)b,
-                                                                coef);
+void clover_insert(pfmp_ctx* c, int prec, double* Hc, int p, const void* a, const void* b, double coef) {
+  if (prec == PFMP_F64)
+    k_clover_insert<PFMP_F64><<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(Hc, c->g, p, (const double2*)a,
+                                                                            (const double2*)b, coef);
+  else
+    k_clover_insert<PFMP_F32><<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(Hc, c->g, p, (const float4*)a,
+                                                                            (const float4*)b, coef);
   PFMP_CHECK_LAUNCH();
 }
 void clover_insert_det(pfmp_op* op, double* Hc, double coef) {
@@ -382,20 +417,21 @@ void gauge_force(pfmp_ctx* c, double* F, double beta) {
   }
 }
 
-// Re[a^dag dM-hat b] * coef  ->  F (hop terms) and Hc (clover terms); a, b even FP64
-void deriv_mhat(pfmp_op* op, double* F, double* Hc, const void* a, const void* b, double coef, void* y, void* w) {
+// Re[a^dag dM-hat b] * coef  ->  F (hop terms) and Hc (clover terms); a, b even fields
+// of precision prec (PFMP_F64 or PFMP_F32), y and w odd temporaries of that precision
+void deriv_mhat(pfmp_op* op, int prec, double* F, double* Hc, const void* a, const void* b, double coef, void* y,
+                void* w) {
   pfmp_ctx* c = op->ctx;
   const double k2 = op->kappa * op->kappa;
   const double kc = op->kappa * op->csw;
   // y = A_oo^{-1} H_oe b, w = A_oo^{-1} H^dag_oe a (odd)
-  hop_clov_odd(op, y, b, false);
-  hop_clov_odd(op, w, a, true);
-  (void)c;
-  force_hop(c, F, 0, a, y, w, b, -k2 * coef);
-  force_hop(c, F, 1, w, b, a, y, -k2 * coef);
+  hop_clov_odd(op, prec, y, b, false);
+  hop_clov_odd(op, prec, w, a, true);
+  force_hop(c, prec, F, 0, a, y, w, b, -k2 * coef);
+  force_hop(c, prec, F, 1, w, b, a, y, -k2 * coef);
   if (op->csw != 0.0) {
-    clover_insert(c, Hc, 0, a, b, -kc * coef);
-    clover_insert(c, Hc, 1, w, y, k2 * (-kc) * coef);
+    clover_insert(c, prec, Hc, 0, a, b, -kc * coef);
+    clover_insert(c, prec, Hc, 1, w, y, k2 * (-kc) * coef);
   }
 }
 

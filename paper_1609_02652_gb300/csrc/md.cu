@@ -160,6 +160,11 @@ struct pfmp_action {
   std::vector<double2*> ev;  // even FP64 temporaries
   std::vector<double2*> xs;  // multi-shift solutions
   double2* od[2] = {nullptr, nullptr};  // odd FP64 temporaries
+  // FP32 force path (force_prec = PFMP_F32): even and odd temporaries, solutions and
+  // filter chains
+  std::vector<float4*> ev32;
+  std::vector<float4*> xs32;
+  float4* od32[2] = {nullptr, nullptr};
   int force_evals = 0;
 };
 
@@ -181,38 +186,59 @@ cd cdot(pfmp_ctx* c, const void* x, const void* y) {
   return cd(v[0], v[1]);
 }
 
+bool f32_forces(pfmp_action* A) { return A->def.force_prec == PFMP_F32; }
+// relative residual of the solves inside the MD forces
+double md_tol(pfmp_action* A) { return A->def.md_tol > 0 ? A->def.md_tol : A->def.tol; }
+float4* E32(pfmp_action* A, int i) {
+  while ((int)A->ev32.size() <= i) A->ev32.push_back((float4*)dev_alloc(spinor_bytes(A->ctx->g, PFMP_F32)));
+  return A->ev32[i];
+}
+
 // the action's CG: FP64, or mixed (FP32 iterations with reliable updates, FP64-accurate
 // true residual) when the action was created with PFMP_SOLVER_CG_MIXED
-void cg64(pfmp_action* A, pfmp_op* op, void* x, const void* b) {
+void cg_tol(pfmp_action* A, pfmp_op* op, void* x, const void* b, double tol) {
   int it, rel;
   double res;
   long kap;
   const bool mixed = A->def.solver == PFMP_SOLVER_CG_MIXED;
-  int st = solve(op, mixed ? PFMP_SOLVER_CG_MIXED : PFMP_SOLVER_CG64, A->def.tol, A->def.max_iter, mixed ? 1e-4 : 0.1,
-                 8, x, b, &it, &rel, &res, &kap);
+  int st = solve(op, mixed ? PFMP_SOLVER_CG_MIXED : PFMP_SOLVER_CG64, tol, A->def.max_iter, mixed ? 1e-4 : 0.1, 8, x,
+                 b, &it, &rel, &res, &kap);
   PFMP_REQUIRE(st == PFMP_OK, st, "CG inside the action did not converge");
 }
+void cg64(pfmp_action* A, pfmp_op* op, void* x, const void* b) { cg_tol(A, op, x, b, A->def.tol); }
 
-void multishift(pfmp_action* A, pfmp_op* op, const std::vector<cd>& sig, const void* b) {
-  while (A->xs.size() < sig.size()) A->xs.push_back((double2*)dev_alloc(spb(A)));
+// multi-shift solutions into A->xs (FP64, at the action's tolerance) or A->xs32 (FP32,
+// at the MD tolerance: the solves of the FP32 forces)
+void multishift(pfmp_action* A, pfmp_op* op, const std::vector<cd>& sig, const void* b, int prec = PFMP_F64) {
   std::vector<void*> x(sig.size());
-  for (size_t k = 0; k < sig.size(); ++k) x[k] = A->xs[k];
+  if (prec == PFMP_F64) {
+    while (A->xs.size() < sig.size()) A->xs.push_back((double2*)dev_alloc(spb(A)));
+    for (size_t k = 0; k < sig.size(); ++k) x[k] = A->xs[k];
+  } else {
+    while (A->xs32.size() < sig.size()) A->xs32.push_back((float4*)dev_alloc(spinor_bytes(A->ctx->g, PFMP_F32)));
+    for (size_t k = 0; k < sig.size(); ++k) x[k] = A->xs32[k];
+  }
   int it;
   double res;
   long kap;
-  int st = solve_multishift(op, (int)sig.size(), sig.data(), x.data(), b, A->def.tol, A->def.max_iter, 8, &it, &res,
+  const double tol = prec == PFMP_F64 ? A->def.tol : md_tol(A);
+  int st = solve_multishift(op, prec, (int)sig.size(), sig.data(), x.data(), b, tol, A->def.max_iter, 8, &it, &res,
                             &kap, false);
   PFMP_REQUIRE(st == PFMP_OK, st, "multi-shift CG inside the action did not converge");
 }
 
-// Re eta^dag dK chi (coef) -> F, Hc for the operator op (K or J)
-void deriv_K(pfmp_action* A, pfmp_op* op, const void* eta, const void* chi, double coef) {
-  void* Mchi = E(A, 6);
-  void* Meta = E(A, 7);
-  mhat(op, PFMP_F64, Mchi, chi, false, nullptr, nullptr);
-  mhat(op, PFMP_F64, Meta, eta, false, nullptr, nullptr);
-  deriv_mhat(op, A->F, A->Hc, Mchi, eta, coef, A->od[0], A->od[1]);
-  deriv_mhat(op, A->F, A->Hc, Meta, chi, coef, A->od[0], A->od[1]);
+// Re eta^dag dK chi (coef) -> F, Hc for the operator op (K or J); eta, chi even fields of
+// precision prec
+void deriv_K(pfmp_action* A, pfmp_op* op, const void* eta, const void* chi, double coef, int prec = PFMP_F64) {
+  const bool f64 = prec == PFMP_F64;
+  void* Mchi = f64 ? E(A, 6) : (void*)E32(A, 6);
+  void* Meta = f64 ? E(A, 7) : (void*)E32(A, 7);
+  void* y = f64 ? (void*)A->od[0] : (void*)A->od32[0];
+  void* w = f64 ? (void*)A->od[1] : (void*)A->od32[1];
+  mhat(op, prec, Mchi, chi, false, nullptr, nullptr);
+  mhat(op, prec, Meta, eta, false, nullptr, nullptr);
+  deriv_mhat(op, prec, A->F, A->Hc, Mchi, eta, coef, y, w);
+  deriv_mhat(op, prec, A->F, A->Hc, Meta, chi, coef, y, w);
 }
 
 void refresh_ops(pfmp_action* A) {
@@ -264,6 +290,7 @@ void setup_term(Term& T, const pfmp_action_def& d) {
     for (auto qk : T.q)
       if (qk.imag() < 0) T.qh.push_back(qk);
     T.sh = product_residues(T.qh);
+    T.q = stable_ordered(T.q);  // the order of the product's factors (action and force)
   } else if (x.kind == PFMP_KIND_FILTERCORR) {
     PFMP_REQUIRE(x.p2 >= 2 && x.p2 % 2 == 0, PFMP_E_UNSUPPORTED, "filter orders must be even");
     std::vector<cd> z = cheb_roots(x.p2, d.mu, d.nu);
@@ -301,6 +328,9 @@ void action_destroy(pfmp_action* A) {
   for (auto p : A->ev) dev_free(p);
   for (auto p : A->xs) dev_free(p);
   for (auto p : A->od) dev_free(p);
+  for (auto p : A->ev32) dev_free(p);
+  for (auto p : A->xs32) dev_free(p);
+  for (auto p : A->od32) dev_free(p);
   for (auto op : A->ops) op_delete(op);
   delete A;
 }
@@ -358,6 +388,9 @@ pfmp_action* action_create_def(pfmp_ctx* c, const pfmp_action_def* d) {
   PFMP_REQUIRE(d->tol > 0 && d->max_iter > 0, PFMP_E_INVALID, "bad solver tolerance / iteration cap");
   PFMP_REQUIRE(d->solver == PFMP_SOLVER_CG64 || d->solver == PFMP_SOLVER_CG_MIXED, PFMP_E_INVALID,
                "action solver must be CG64 or CG_MIXED");
+  PFMP_REQUIRE(d->force_prec == PFMP_F64 || d->force_prec == PFMP_F32, PFMP_E_INVALID,
+               "force precision must be PFMP_F64 or PFMP_F32");
+  PFMP_REQUIRE(d->md_tol >= 0 && d->md_tol < 1, PFMP_E_INVALID, "md_tol must be in [0, 1)");
   for (int i = 0; i < d->nkappa; ++i) PFMP_REQUIRE(d->kappa[i] > 0, PFMP_E_INVALID, "kappa must be positive");
   for (int i = 0; i < d->nterms; ++i) {
     const pfmp_term& x = d->term[i];
@@ -386,6 +419,8 @@ pfmp_action* action_create_def(pfmp_ctx* c, const pfmp_action_def* d) {
     A->U0 = (double2*)dev_alloc((size_t)g.Vh * 72 * sizeof(double2));
     for (int i = 0; i < 8; ++i) A->ev.push_back((double2*)dev_alloc(spb(A)));
     for (auto& p : A->od) p = (double2*)dev_alloc(spb(A));
+    if (d->force_prec == PFMP_F32)
+      for (auto& p : A->od32) p = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
   } catch (...) {
     action_destroy(A);
     throw;
@@ -432,7 +467,7 @@ void action_heatbath(pfmp_action* A, const void* const* xi) {
       mhat(W, PFMP_F64, E(A, 0), x, true, nullptr, nullptr);
       std::vector<cd> zc;
       for (auto zk : T.zh) zc.push_back(std::conj(zk));
-      poly_product(W, zc, std::sqrt(T.a_p), phi, E(A, 0));
+      poly_product(W, stable_ordered(zc), std::sqrt(T.a_p), phi, E(A, 0));
     } else if (T.d.kind == PFMP_KIND_RATIO) {
       // phi = W_a J_a^{-1} M_b^dag xi
       mhat(A->ops[T.d.b], PFMP_F64, E(A, 0), x, true, nullptr, nullptr);
@@ -479,6 +514,61 @@ void action_eval(pfmp_action* A, double* S) {
   for (int i = 0; i < (int)A->t.size(); ++i) S[i] = action_term(A, i);
 }
 
+// The fermion forces with FP32 arithmetic (force_prec = PFMP_F32): the spinor products,
+// the K chains of the filter force and the multi-shift solve of the correction force in
+// FP32 (solves at the MD tolerance), the CG of the ratio and inverse terms mixed, every
+// contraction summed into the FP64 force.  The MD only needs each force to be a fixed
+// function of the gauge field (then every momentum update is a shear of phase space and
+// the MD map stays reversible and area-preserving), so the trajectory is still exact;
+// the actions at its ends are evaluated as before.
+static void force_f32(pfmp_action* A, Term& T, pfmp_op* W, const void* phi) {
+  pfmp_ctx* c = A->ctx;
+  const size_t b32 = spinor_bytes(c->g, PFMP_F32);
+  float4* phi32 = E32(A, 0);
+  blas_copy(c, phi32, PFMP_F32, phi, PFMP_F64);
+  if (T.d.kind == PFMP_KIND_FILTER) {
+    const int m = (int)T.q.size();
+    while ((int)A->xs32.size() < m) A->xs32.push_back((float4*)dev_alloc(b32));
+    // chi_{m-1} = c phi, chi_k = (J - q_{k+1}) chi_{k+1}
+    caxpby(c, PFMP_F32, T.c, phi32, 0.0, A->xs32[m - 1]);
+    for (int k = m - 2; k >= 0; --k) {
+      kop(W, PFMP_F32, A->xs32[k], A->xs32[k + 1], nullptr, nullptr);
+      caxpby(c, PFMP_F32, -T.q[k + 1], A->xs32[k + 1], 1.0, A->xs32[k]);
+    }
+    // eta_0 = phi, eta_k = (J - q_{k-1}^*) eta_{k-1}
+    float4* eta = E32(A, 2);
+    float4* tmp = E32(A, 3);
+    PFMP_CUDA(cudaMemcpyAsync(eta, phi32, b32, cudaMemcpyDeviceToDevice, c->stream));
+    for (int k = 0; k < m; ++k) {
+      if (k > 0) {
+        kop(W, PFMP_F32, tmp, eta, nullptr, nullptr);
+        caxpby(c, PFMP_F32, 1.0, tmp, -std::conj(T.q[k - 1]), eta);
+      }
+      deriv_K(A, W, eta, A->xs32[k], 1.0, PFMP_F32);
+    }
+  } else if (T.d.kind == PFMP_KIND_FILTERCORR) {
+    multishift(A, W, T.sig, phi32, PFMP_F32);
+    float4* chib = E32(A, 2);
+    for (size_t k = 0; k < T.sig.size(); ++k) {
+      caxpby(c, PFMP_F32, T.r[k], A->xs32[k], 0.0, chib);
+      deriv_K(A, W, A->xs32[T.conj_of[k]], chib, -1.0, PFMP_F32);
+    }
+  } else if (T.d.kind == PFMP_KIND_RATIO) {
+    pfmp_op* Mb = A->ops[T.d.b];
+    mhat(W, PFMP_F64, E(A, 0), phi, true, nullptr, nullptr);
+    cg_tol(A, Mb, E(A, 1), E(A, 0), md_tol(A));
+    float4* chi32 = E32(A, 1);
+    blas_copy(c, chi32, PFMP_F32, E(A, 1), PFMP_F64);
+    deriv_mhat(W, PFMP_F32, A->F, A->Hc, phi32, chi32, 2.0, A->od32[0], A->od32[1]);
+    deriv_K(A, Mb, chi32, chi32, -1.0, PFMP_F32);
+  } else {  // INV
+    cg_tol(A, W, E(A, 1), phi, md_tol(A));
+    float4* chi32 = E32(A, 1);
+    blas_copy(c, chi32, PFMP_F32, E(A, 1), PFMP_F64);
+    deriv_K(A, W, chi32, chi32, -1.0, PFMP_F32);
+  }
+}
+
 // F += dS_i/d omega (F must be zeroed by the caller for a fresh force)
 void action_force(pfmp_action* A, int i) {
   pfmp_ctx* c = A->ctx;
@@ -494,7 +584,9 @@ void action_force(pfmp_action* A, int i) {
   if (T.d.kind == PFMP_KIND_DET && !clover) return;
   PFMP_CUDA(cudaMemsetAsync(A->Hc, 0, (size_t)g.Vh * 96 * sizeof(double), c->stream));
   void* phi = T.pf >= 0 ? A->phi[T.pf] : nullptr;
-  if (T.d.kind == PFMP_KIND_DET) {
+  if (T.d.kind != PFMP_KIND_DET && f32_forces(A)) {
+    force_f32(A, T, W, phi);
+  } else if (T.d.kind == PFMP_KIND_DET) {
     clover_insert_det(W, A->Hc, 2.0 * W->kappa * W->csw);
   } else if (T.d.kind == PFMP_KIND_FILTER) {
     const int m = (int)T.q.size();
@@ -529,7 +621,7 @@ void action_force(pfmp_action* A, int i) {
     void* chi = E(A, 1);
     cg64(A, Mb, chi, E(A, 0));
     // 2 Re chi^dag dW^dag phi = 2 Re phi^dag dW chi
-    deriv_mhat(W, A->F, A->Hc, phi, chi, 2.0, A->od[0], A->od[1]);
+    deriv_mhat(W, PFMP_F64, A->F, A->Hc, phi, chi, 2.0, A->od[0], A->od[1]);
     deriv_K(A, Mb, chi, chi, -1.0);
   } else {  // INV
     void* chi = E(A, 1);
@@ -688,17 +780,33 @@ void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double
   for (auto op : A->ops) stale = stale || op->built_version != c->gauge_version;
   if (stale) refresh_ops(A);
   alg_pack(c, A->mom, mom, where);
-  action_heatbath(A, xi);
   std::vector<double> S0(nt, 0.0), S1(nt, 0.0);
-  double H0 = kinetic(A);
-  for (int t = 0; t < nt; ++t)
-    if (term_level[t] >= 0) H0 += (S0[t] = action_term(A, t));
-  md_steps(A, len, T, nlev, S, term_level, info);
-  double H1 = kinetic(A);
-  for (int t = 0; t < nt; ++t)
-    if (term_level[t] >= 0) H1 += (S1[t] = action_term(A, t));
+  double H0 = 0, H1 = 0;
+  // a trajectory that fails (a NaN, a solve that does not converge) leaves the gauge
+  // field as it found it
+  auto restore = [&]() {
+    cudaMemcpyAsync(c->U64, A->U0, (size_t)g.Vh * 72 * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream);
+    gauge_refresh_compressed(c);
+    refresh_ops(A);
+  };
+  try {
+    action_heatbath(A, xi);
+    H0 = kinetic(A);
+    for (int t = 0; t < nt; ++t)
+      if (term_level[t] >= 0) H0 += (S0[t] = action_term(A, t));
+    md_steps(A, len, T, nlev, S, term_level, info);
+    H1 = kinetic(A);
+    for (int t = 0; t < nt; ++t)
+      if (term_level[t] >= 0) H1 += (S1[t] = action_term(A, t));
+    PFMP_REQUIRE(std::isfinite(H1 - H0), PFMP_E_NAN, "dH is not finite");
+  } catch (const Err&) {
+    try {
+      restore();
+    } catch (const Err&) {
+    }
+    throw;
+  }
   const double dH = H1 - H0;
-  PFMP_REQUIRE(std::isfinite(dH), PFMP_E_NAN, "dH is not finite");
   const bool acc = u < std::exp(-dH);
   info->H0 = H0;
   info->H1 = H1;
@@ -711,11 +819,7 @@ void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double
   }
   info->k_apply = kapply_total(A) - k0;
   info->force_evals = A->force_evals;
-  if (!acc) {
-    PFMP_CUDA(cudaMemcpyAsync(c->U64, A->U0, (size_t)g.Vh * 72 * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-    gauge_refresh_compressed(c);
-    refresh_ops(A);
-  }
+  if (!acc) restore();
   info->plaquette = plaquette(c);
 }
 

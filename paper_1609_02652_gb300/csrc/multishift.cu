@@ -8,14 +8,27 @@
 //   alpha_s = a zeta_s' / zeta_s,  beta_s = b (zeta_s' / zeta_s)^2,
 //   x_s += alpha_s p_s,  p_s = zeta_s' r + beta_s p_s,
 // where a, b are the seed CG's alpha, beta and ^- marks the previous iteration.  All
-// scalars live on the device: one CUDA graph-free loop of 6 kernels per iteration with
-// no host round trip except a convergence check every `check` iterations.  FP64.
+// scalars live on the device (FP64); one iteration is K (the reduction finisher writes
+// a), the per-shift scalars, the seed residual (whose finisher writes b, the per-shift
+// coefficients and which shifts have converged), and ONE pass that updates x_s and p_s
+// of every shift still running and the seed direction.  A shift whose residual
+// |zeta_s| |r| is below tol |b| takes this iteration's x update and then stops: the
+// large shifts of a Chebyshev filter converge in a fraction of the seed's iterations,
+// and their vectors leave the memory traffic.  The loop ends when every shift has
+// converged (the seed system itself need not be one of them).
+//
+// Vectors (solutions, directions, seed residual) are FP64, or FP32 for the solves inside
+// the MD forces (K on the FP32 stencil, FP64 global sums and scalars): a deterministic
+// force needs no FP64 solve, and the trajectory's end actions stay FP64.
 //
 // Polynomial (App. A): P_n(K) v = a_n prod_{k=1}^{n} (K - z_k) v, roots
 // z_k = mu (1 - cos t_k) - i sqrt(mu^2 - nu^2) sin t_k, t_k = 2 pi k/(n+1),
 // a_n = 1/(mu prod_k (mu - z_k)); each factor is one K application and a complex axpby.
 // R(K) = sqrt(a_n) prod_{Im z_k < 0} (K - z_k) (P = R^dag R for even n), R^dag with the
-// conjugate roots.
+// conjugate roots.  The factors commute; they are applied in bit-reversed index order
+// (stable_order), which keeps every partial product within a few orders of magnitude of
+// the final one (in index order the partial products of P_64 reach 1e11 times it, and
+// the rounding of each factor is amplified accordingly).
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -28,10 +41,14 @@ namespace pfmp {
 struct MSShift {
   double2 sigma;
   double2 zeta_prev, zeta, zeta_next;
-  double2 alpha, beta;
+  double2 alpha;   // x_s += alpha p_s
+  double2 beta;    // p_s = zeta_next r + beta p_s
+  int active;      // takes part in this iteration
+  int keep;        // still running after it (its direction is updated)
 };
 struct MSSeed {
   double alpha_prev, beta_prev;
+  int nact;        // shifts active this iteration, listed in act[]
 };
 
 __device__ __forceinline__ double2 cm(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -43,12 +60,39 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 cs(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
 
-// zeta_next and alpha_s of every shift from the seed's alpha (just computed) and the
-// previous alpha, beta
+// complex words of a vector field: double2 = one complex number, float4 = two
+__device__ __forceinline__ double2 axpy_c(double2 a, double2 x, double2 y) { return cadd(y, cm(a, x)); }
+__device__ __forceinline__ float4 axpy_c(double2 a, float4 x, float4 y) {
+  const float ar = (float)a.x, ai = (float)a.y;
+  return make_float4(y.x + ar * x.x - ai * x.y, y.y + ar * x.y + ai * x.x, y.z + ar * x.z - ai * x.w,
+                     y.w + ar * x.w + ai * x.z);
+}
+// a x + b y
+__device__ __forceinline__ double2 axpby_c(double2 a, double2 x, double2 b, double2 y) { return cadd(cm(a, x), cm(b, y)); }
+__device__ __forceinline__ float4 axpby_c(double2 a, float4 x, double2 b, float4 y) {
+  const float ar = (float)a.x, ai = (float)a.y, br = (float)b.x, bi = (float)b.y;
+  return make_float4(ar * x.x - ai * x.y + br * y.x - bi * y.y, ar * x.y + ai * x.x + br * y.y + bi * y.x,
+                     ar * x.z - ai * x.w + br * y.z - bi * y.w, ar * x.w + ai * x.z + br * y.w + bi * y.z);
+}
+__device__ __forceinline__ double2 sub_real(double2 r, double a, double2 q) { return make_double2(r.x - a * q.x, r.y - a * q.y); }
+__device__ __forceinline__ float4 sub_real(float4 r, double ad, float4 q) {
+  const float a = (float)ad;
+  return make_float4(r.x - a * q.x, r.y - a * q.y, r.z - a * q.z, r.w - a * q.w);
+}
+__device__ __forceinline__ double nrm(double2 v) { return v.x * v.x + v.y * v.y; }
+__device__ __forceinline__ double nrm(float4 v) { return (double)(v.x * v.x + v.y * v.y) + (double)(v.z * v.z + v.w * v.w); }
+__device__ __forceinline__ double2 xpby_real(double2 r, double b, double2 p) { return make_double2(r.x + b * p.x, r.y + b * p.y); }
+__device__ __forceinline__ float4 xpby_real(float4 r, double bd, float4 p) {
+  const float b = (float)bd;
+  return make_float4(r.x + b * p.x, r.y + b * p.y, r.z + b * p.z, r.w + b * p.w);
+}
+
+// zeta_next and alpha_s of every active shift from the seed's alpha (just computed) and
+// the previous alpha, beta
 __global__ void k_ms_alpha(MSShift* sh, int ns, const CGScalars* s, const MSSeed* sd) {
   if (s->done) return;
   const int i = threadIdx.x + blockIdx.x * blockDim.x;
-  if (i >= ns) return;
+  if (i >= ns || !sh[i].active) return;
   MSShift v = sh[i];
   const double a = s->alpha, ap = sd->alpha_prev, bp = sd->beta_prev;
   const double2 one_as = make_double2(1.0 + a * v.sigma.x, a * v.sigma.y);
@@ -59,32 +103,18 @@ __global__ void k_ms_alpha(MSShift* sh, int ns, const CGScalars* s, const MSSeed
   sh[i].alpha = v.alpha;
 }
 
-// x_s += alpha_s p_s for all shifts
-__global__ void k_ms_x(double2** x, double2* const* p, const MSShift* sh, int ns, long n, const CGScalars* s) {
-  if (s->done) return;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    for (int k = 0; k < ns; ++k) {
-      const double2 a = sh[k].alpha;
-      double2 xx = x[k][i];
-      const double2 pp = p[k][i];
-      x[k][i] = cadd(xx, cm(a, pp));
-    }
-}
-
-// seed residual r -= alpha Ap, |r|^2; finisher: beta, rr, iter, convergence (seed and all
-// shifted residuals |zeta_s| |r| below stop), previous alpha/beta
-__global__ void k_ms_r(double2* __restrict__ r, const double2* __restrict__ Ap, long n, ReduceBuf rb, CGScalars* s,
-                       MSSeed* sd, const MSShift* sh, int ns) {
+// seed residual r -= alpha Ap, |r|^2; finisher: beta, rr, iter, the shifts' direction
+// coefficients, which shifts keep running (|zeta_s'|^2 |r|^2 >= stop), done when none
+template <typename V>
+__global__ void k_ms_r(V* __restrict__ r, const V* __restrict__ Ap, long n, ReduceBuf rb, CGScalars* s, MSSeed* sd,
+                       MSShift* sh, int ns) {
   if (s->done) return;
   const double al = s->alpha;
   double v[1] = {0.0};
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    double2 rr = r[i];
-    const double2 aa = Ap[i];
-    rr.x -= al * aa.x;
-    rr.y -= al * aa.y;
+    const V rr = sub_real(r[i], al, Ap[i]);
     r[i] = rr;
-    v[0] += rr.x * rr.x + rr.y * rr.y;
+    v[0] += nrm(rr);
   }
   double t[1];
   if (grid_sum<1>(v, rb, t)) {
@@ -94,65 +124,88 @@ __global__ void k_ms_r(double2* __restrict__ r, const double2* __restrict__ Ap, 
     s->iter += 1;
     sd->alpha_prev = al;
     sd->beta_prev = beta;
-    bool conv = t[0] < s->stop_rr;
-    for (int k = 0; k < ns && conv; ++k) {
-      const double z2 = sh[k].zeta_next.x * sh[k].zeta_next.x + sh[k].zeta_next.y * sh[k].zeta_next.y;
-      conv = z2 * t[0] < s->stop_rr;
+    bool any = false;
+    for (int k = 0; k < ns; ++k) {
+      if (!sh[k].active) continue;
+      const double2 q = cdiv(sh[k].zeta_next, sh[k].zeta);
+      sh[k].beta = cs(beta, cm(q, q));
+      const int keep = nrm(sh[k].zeta_next) * t[0] >= s->stop_rr;
+      sh[k].keep = keep;
+      any = any || keep;
     }
-    if (conv || !(t[0] == t[0])) s->done_next = 1;
+    if (!any || !(t[0] == t[0])) s->done_next = 1;
   }
 }
 
-// p_s = zeta_s' r + beta_s p_s, seed p = r + beta p; finisher rotates the zetas
-__global__ void k_ms_p(double2* const* p, double2* pseed, const double2* __restrict__ r, MSShift* sh, int ns, long n,
-                       ReduceBuf rb, CGScalars* s) {
+// x_s += alpha_s p_s and p_s = zeta_s' r + beta_s p_s for the active shifts (the
+// direction only for those that keep running), the seed p = r + beta p; the finisher
+// rotates the zetas and the active set
+template <typename V>
+__global__ void k_ms_xp(V* const* x, V* const* p, V* __restrict__ pseed, const V* __restrict__ r, MSShift* sh,
+                        int ns, const int* act, MSSeed* sd, long n, ReduceBuf rb, CGScalars* s) {
   if (s->done) return;
   const double be = s->beta;
+  const int na = sd->nact;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const double2 rr = r[i];
-    for (int k = 0; k < ns; ++k) {
-      const double2 q = cdiv(sh[k].zeta_next, sh[k].zeta);
-      const double2 bs = cs(be, cm(q, q));
-      p[k][i] = cadd(cm(sh[k].zeta_next, rr), cm(bs, p[k][i]));
+    const V rr = r[i];
+    for (int j = 0; j < na; ++j) {
+      const int k = act[j];
+      const V pk = p[k][i];
+      x[k][i] = axpy_c(sh[k].alpha, pk, x[k][i]);
+      if (sh[k].keep) p[k][i] = axpby_c(sh[k].zeta_next, rr, sh[k].beta, pk);
     }
-    const double2 ps = pseed[i];
-    pseed[i] = make_double2(rr.x + be * ps.x, rr.y + be * ps.y);
+    pseed[i] = xpby_real(rr, be, pseed[i]);
   }
   double v[1] = {0.0}, t[1];
   if (grid_sum<1>(v, rb, t)) {
+    int m = 0;
+    int* a = const_cast<int*>(act);
     for (int k = 0; k < ns; ++k) {
+      if (!sh[k].active) continue;
       sh[k].zeta_prev = sh[k].zeta;
       sh[k].zeta = sh[k].zeta_next;
+      sh[k].active = sh[k].keep;
+      if (sh[k].keep) a[m++] = k;
     }
+    sd->nact = m;
     s->done = s->done_next;
   }
 }
 
-// y = a x + b y (complex a, b), FP64
-__global__ void k_caxpby(double2 a, const double2* __restrict__ x, double2 b, double2* __restrict__ y, long n) {
+// y = a x + b y (complex a, b) on FP64 or FP32 even fields
+template <typename V>
+__global__ void k_caxpby(double2 a, const V* __restrict__ x, double2 b, V* __restrict__ y, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    y[i] = cadd(cm(a, x[i]), cm(b, y[i]));
+    y[i] = axpby_c(a, x[i], b, y[i]);
 }
 
 static int ms_grid(long n) {
   long b = (n + kBlock - 1) / kBlock;
   return (int)(b < 152 * 8 ? b : 152 * 8);
 }
+static long words(const Geom& g, int prec) { return (prec == PFMP_F64 ? 12L : 6L) * g.Vh; }
 
-void caxpby(pfmp_ctx* c, std::complex<double> a, const void* x, std::complex<double> b, void* y) {
-  const long n = 12L * c->g.Vh;
-  k_caxpby<<<ms_grid(n), kBlock, 0, c->stream>>>(make_double2(a.real(), a.imag()), (const double2*)x,
-                                                  make_double2(b.real(), b.imag()), (double2*)y, n);
+void caxpby(pfmp_ctx* c, int prec, std::complex<double> a, const void* x, std::complex<double> b, void* y) {
+  const long n = words(c->g, prec);
+  const double2 da = make_double2(a.real(), a.imag()), db = make_double2(b.real(), b.imag());
+  if (prec == PFMP_F64)
+    k_caxpby<double2><<<ms_grid(n), kBlock, 0, c->stream>>>(da, (const double2*)x, db, (double2*)y, n);
+  else
+    k_caxpby<float4><<<ms_grid(n), kBlock, 0, c->stream>>>(da, (const float4*)x, db, (float4*)y, n);
   PFMP_CHECK_LAUNCH();
+}
+void caxpby(pfmp_ctx* c, std::complex<double> a, const void* x, std::complex<double> b, void* y) {
+  caxpby(c, PFMP_F64, a, x, b, y);
 }
 
 // per-operator workspace for the shifted search directions and device scalar arrays
 struct MSWork {
   std::vector<double2*> p;
-  double2** d_x = nullptr;
-  double2** d_p = nullptr;
+  void** d_x = nullptr;
+  void** d_p = nullptr;
   MSShift* d_sh = nullptr;
   MSSeed* d_seed = nullptr;
+  int* d_act = nullptr;
   int cap = 0;
   ~MSWork() {
     for (auto q : p) dev_free(q);
@@ -160,6 +213,7 @@ struct MSWork {
     dev_free(d_p);
     dev_free(d_sh);
     dev_free(d_seed);
+    dev_free(d_act);
   }
 };
 
@@ -171,9 +225,11 @@ static MSWork& ms_work(pfmp_op* op, int ns) {
     dev_free(w.d_x);
     dev_free(w.d_p);
     dev_free(w.d_sh);
-    w.d_x = (double2**)dev_alloc(ns * sizeof(double2*));
-    w.d_p = (double2**)dev_alloc(ns * sizeof(double2*));
+    dev_free(w.d_act);
+    w.d_x = (void**)dev_alloc(ns * sizeof(void*));
+    w.d_p = (void**)dev_alloc(ns * sizeof(void*));
     w.d_sh = (MSShift*)dev_alloc(ns * sizeof(MSShift));
+    w.d_act = (int*)dev_alloc(ns * sizeof(int));
     if (!w.d_seed) w.d_seed = (MSSeed*)dev_alloc(sizeof(MSSeed));
     w.cap = ns;
   }
@@ -185,46 +241,74 @@ void ms_work_free(pfmp_op* op) {
   op->ms = nullptr;
 }
 
-// x[k] = (K + sigma_k)^{-1} b, FP64.  Returns iterations; true residuals optional.
-int solve_multishift(pfmp_op* op, int ns, const std::complex<double>* sigma, void* const* x, const void* b, double tol,
-                     int max_iter, int check, int* iters, double* max_true_res, long* kapply, bool want_true_res) {
+template <typename V>
+static void ms_iteration(pfmp_op* op, int prec, MSWork& w, int ns, void* r, void* pseed, void* Ap, long n) {
   pfmp_ctx* c = op->ctx;
+  kop(op, prec, Ap, pseed, &op->scal->pAp, op->scal);
+  k_ms_alpha<<<(ns + 127) / 128, 128, 0, c->stream>>>(w.d_sh, ns, op->scal, w.d_seed);
+  PFMP_CHECK_LAUNCH();
+  k_ms_r<V><<<ms_grid(n), kBlock, 0, c->stream>>>((V*)r, (const V*)Ap, n, c->rb, op->scal, w.d_seed, w.d_sh, ns);
+  PFMP_CHECK_LAUNCH();
+  k_ms_xp<V><<<ms_grid(n), kBlock, 0, c->stream>>>((V* const*)w.d_x, (V* const*)w.d_p, (V*)pseed, (const V*)r,
+                                                   w.d_sh, ns, w.d_act, w.d_seed, n, c->rb, op->scal);
+  PFMP_CHECK_LAUNCH();
+}
+
+// x[k] = (K + sigma_k)^{-1} b in FP64 or FP32 (x, b of precision prec).  Returns the
+// status; iterations, K applications and (FP64, on request) the largest true residual.
+int solve_multishift(pfmp_op* op, int prec, int ns, const std::complex<double>* sigma, void* const* x, const void* b,
+                     double tol, int max_iter, int check, int* iters, double* max_true_res, long* kapply,
+                     bool want_true_res) {
+  pfmp_ctx* c = op->ctx;
+  PFMP_REQUIRE(prec == PFMP_F64 || prec == PFMP_F32, PFMP_E_INVALID, "multi-shift CG: precision must be F64 or F32");
   PFMP_REQUIRE(ns >= 1 && ns <= 1024, PFMP_E_INVALID, "number of shifts must be in [1, 1024]");
   PFMP_REQUIRE(tol > 0 && max_iter > 0, PFMP_E_INVALID, "tol and max_iter must be positive");
+  // K is Hermitian positive definite, so K + sigma is singular only for real sigma < 0
+  // (at sigma = -lambda for an eigenvalue lambda of K); such shifts are refused
+  for (int k = 0; k < ns; ++k) {
+    PFMP_REQUIRE(std::isfinite(sigma[k].real()) && std::isfinite(sigma[k].imag()), PFMP_E_INVALID,
+                 "multi-shift CG: a shift is not finite");
+    PFMP_REQUIRE(!(sigma[k].imag() == 0.0 && sigma[k].real() < 0.0), PFMP_E_INVALID,
+                 "multi-shift CG: a real negative shift can make K + sigma singular");
+  }
   if (check <= 0) check = 8;
   MSWork& w = ms_work(op, ns);
-  const size_t bytes = spinor_bytes(c->g, PFMP_F64);
-  const long n = 12L * c->g.Vh;
-  // |b|^2
-  blas_norm2(c, PFMP_F64, b, c->d_sums);
+  const size_t bytes = spinor_bytes(c->g, prec);
+  const long n = words(c->g, prec);
+  blas_norm2(c, prec, b, c->d_sums);
   PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PFMP_CUDA(cudaStreamSynchronize(c->stream));
   const double bb = c->h_sums[0];
   *iters = 0;
   *kapply = 0;
   *max_true_res = 0;
-  for (int k = 0; k < ns; ++k) blas_zero(c, PFMP_F64, x[k]);
+  for (int k = 0; k < ns; ++k) blas_zero(c, prec, x[k]);
   if (bb == 0.0) return PFMP_OK;
   PFMP_REQUIRE(std::isfinite(bb), PFMP_E_NAN, "right-hand side is not finite");
-  void* r = op->cg64[0];
-  void* pseed = op->cg64[1];
-  void* Ap = op->cg64[2];
+  void* r = prec == PFMP_F64 ? (void*)op->cg64[0] : (void*)op->cg32[0];
+  void* pseed = prec == PFMP_F64 ? (void*)op->cg64[1] : (void*)op->cg32[1];
+  void* Ap = prec == PFMP_F64 ? (void*)op->cg64[2] : (void*)op->cg32[2];
   PFMP_CUDA(cudaMemcpyAsync(r, b, bytes, cudaMemcpyDeviceToDevice, c->stream));
   PFMP_CUDA(cudaMemcpyAsync(pseed, b, bytes, cudaMemcpyDeviceToDevice, c->stream));
-  std::vector<double2*> hx(ns);
+  std::vector<void*> hx(ns), hp(ns);
   std::vector<MSShift> hs(ns);
+  std::vector<int> act(ns);
   for (int k = 0; k < ns; ++k) {
-    hx[k] = (double2*)x[k];
+    hx[k] = x[k];
+    hp[k] = w.p[k];
+    act[k] = k;
     PFMP_CUDA(cudaMemcpyAsync(w.p[k], b, bytes, cudaMemcpyDeviceToDevice, c->stream));
     MSShift s{};
     s.sigma = make_double2(sigma[k].real(), sigma[k].imag());
     s.zeta_prev = s.zeta = s.zeta_next = make_double2(1.0, 0.0);
+    s.active = s.keep = 1;
     hs[k] = s;
   }
-  PFMP_CUDA(cudaMemcpyAsync(w.d_x, hx.data(), ns * sizeof(double2*), cudaMemcpyHostToDevice, c->stream));
-  PFMP_CUDA(cudaMemcpyAsync(w.d_p, w.p.data(), ns * sizeof(double2*), cudaMemcpyHostToDevice, c->stream));
+  PFMP_CUDA(cudaMemcpyAsync(w.d_x, hx.data(), ns * sizeof(void*), cudaMemcpyHostToDevice, c->stream));
+  PFMP_CUDA(cudaMemcpyAsync(w.d_p, hp.data(), ns * sizeof(void*), cudaMemcpyHostToDevice, c->stream));
   PFMP_CUDA(cudaMemcpyAsync(w.d_sh, hs.data(), ns * sizeof(MSShift), cudaMemcpyHostToDevice, c->stream));
-  MSSeed sd{1.0, 0.0};
+  PFMP_CUDA(cudaMemcpyAsync(w.d_act, act.data(), ns * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  MSSeed sd{1.0, 0.0, ns};
   PFMP_CUDA(cudaMemcpyAsync(w.d_seed, &sd, sizeof(MSSeed), cudaMemcpyHostToDevice, c->stream));
   CGScalars* h = op->h_scal;
   *h = CGScalars{};
@@ -236,17 +320,10 @@ int solve_multishift(pfmp_op* op, int ns, const std::complex<double>* sigma, voi
   while (done < max_iter) {
     const int chunk = check < max_iter - done ? check : max_iter - done;
     for (int k = 0; k < chunk; ++k) {
-      kop(op, PFMP_F64, Ap, pseed, &op->scal->pAp, op->scal);
-      k_ms_alpha<<<(ns + 127) / 128, 128, 0, c->stream>>>(w.d_sh, ns, op->scal, w.d_seed);
-      PFMP_CHECK_LAUNCH();
-      k_ms_x<<<ms_grid(n), kBlock, 0, c->stream>>>(w.d_x, w.d_p, w.d_sh, ns, n, op->scal);
-      PFMP_CHECK_LAUNCH();
-      k_ms_r<<<ms_grid(n), kBlock, 0, c->stream>>>((double2*)r, (const double2*)Ap, n, c->rb, op->scal, w.d_seed,
-                                                    w.d_sh, ns);
-      PFMP_CHECK_LAUNCH();
-      k_ms_p<<<ms_grid(n), kBlock, 0, c->stream>>>(w.d_p, (double2*)pseed, (const double2*)r, w.d_sh, ns, n, c->rb,
-                                                    op->scal);
-      PFMP_CHECK_LAUNCH();
+      if (prec == PFMP_F64)
+        ms_iteration<double2>(op, prec, w, ns, r, pseed, Ap, n);
+      else
+        ms_iteration<float4>(op, prec, w, ns, r, pseed, Ap, n);
     }
     PFMP_CUDA(cudaMemcpyAsync(h, op->scal, sizeof(CGScalars), cudaMemcpyDeviceToHost, c->stream));
     PFMP_CUDA(cudaStreamSynchronize(c->stream));
@@ -257,7 +334,7 @@ int solve_multishift(pfmp_op* op, int ns, const std::complex<double>* sigma, voi
   *iters = done;
   *kapply = done;
   op->kapply = kapply0 + done;
-  if (want_true_res) {
+  if (want_true_res && prec == PFMP_F64) {
     // || b - (K + sigma) x || / ||b|| for every shift, FP64
     for (int k = 0; k < ns; ++k) {
       kop(op, PFMP_F64, Ap, x[k], nullptr, nullptr);
@@ -271,6 +348,28 @@ int solve_multishift(pfmp_op* op, int ns, const std::complex<double>* sigma, voi
     }
   }
   return h->done ? PFMP_OK : PFMP_E_NOT_CONVERGED;
+}
+
+// bit-reversed order of 0..n-1 (indices >= n skipped): a permutation that interleaves
+// roots from all around the ellipse, so that no partial product is dominated by one
+// side of it
+std::vector<int> stable_order(int n) {
+  int b = 0;
+  while ((1 << b) < n) ++b;
+  std::vector<int> o;
+  for (int i = 0; i < (1 << b); ++i) {
+    int r = 0;
+    for (int k = 0; k < b; ++k)
+      if (i & (1 << k)) r |= 1 << (b - 1 - k);
+    if (r < n) o.push_back(r);
+  }
+  return o;
+}
+
+std::vector<std::complex<double>> stable_ordered(const std::vector<std::complex<double>>& z) {
+  std::vector<std::complex<double>> o;
+  for (int k : stable_order((int)z.size())) o.push_back(z[k]);
+  return o;
 }
 
 // ------------------------------------------------------------------ polynomial
@@ -290,7 +389,8 @@ double cheb_norm(int n, double mu, double nu) {
   return (1.0 / p).real();
 }
 
-// out = scale * prod_k (K - z_k) in, factors applied in the given order; FP64
+// out = scale * prod_k (K - z_k) in, factors applied in the given order (callers pass
+// stable_ordered lists); FP64
 void poly_product(pfmp_op* op, const std::vector<std::complex<double>>& z, double scale, void* out, const void* in) {
   pfmp_ctx* c = op->ctx;
   const size_t bytes = spinor_bytes(c->g, PFMP_F64);

@@ -1102,9 +1102,8 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
     *kapply += done_it;
     // outer correction in FP64 storage, true residual in double-float
     blas_add_lo(c, x, wk.e);
-    *kapply += 1;
     *outer += 1;
-    res = std::sqrt(true_residual_df(op, x, b, r64) / bb);
+    res = std::sqrt(true_residual_mixed(op, x, b, r64, tol * tol * bb, kapply) / bb);
     PFMP_REQUIRE(std::isfinite(res), PFMP_E_NAN, "FGCR residual is not finite");
     if (res < tol) break;
     stall = res > 0.9 * prev ? stall + 1 : 0;
@@ -1121,7 +1120,7 @@ int solve_fgcr(pfmp_op* op, pfmp_nn* nn, double tol, int max_iter, int restart, 
       *fallback_iters = it;
       *kapply += kap;
       caxpby(c, 1.0, ec, 1.0, x);
-      res = std::sqrt(true_residual_df(op, x, b, r64) / bb);
+      res = std::sqrt(true_residual_mixed(op, x, b, r64, tol * tol * bb, kapply) / bb);
       break;
     }
   }

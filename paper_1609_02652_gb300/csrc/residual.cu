@@ -1,8 +1,11 @@
 // The true residual r = b - K x of the mixed solvers with K applied in double-float on
 // the FP32 pipe (dfloat.cuh): x is split once into FP32 pairs, K runs through the same
 // stencil templates as the FP32 and FP64 paths, and only the final b - (hi + lo) and
-// |r|^2 use FP64.  About 48 significant bits: the residual is accurate to ~1e-13
-// relative to |K| |x|, far below the 1e-10 stopping tolerance.
+// |r|^2 use FP64.  About 48 significant bits: the rounding error of the residual is
+// ~2^-48 |K| |x|, which near a critical kappa (|K| |x| / |b| up to the condition number
+// of K) can come within a factor of ten of a 1e-10 target.  So the solvers' stopping
+// test (true_residual_mixed) confirms a double-float residual below the target once
+// with K in FP64, and that FP64 value decides and is the one reported.
 #include "context.h"
 #include "dfloat.cuh"
 
@@ -31,6 +34,19 @@ static int rgrid(long n) {
   return (int)(b < 152 * 8 ? b : 152 * 8);
 }
 
+// r = b - r, |r|^2 -> *out
+__global__ void k_b_minus_r(const double2* __restrict__ b, double2* __restrict__ r, long n, ReduceBuf rb, double* out) {
+  double v[1] = {0.0};
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double2 bb = b[i], kx = r[i];
+    const double2 d = make_double2(bb.x - kx.x, bb.y - kx.y);
+    r[i] = d;
+    v[0] += d.x * d.x + d.y * d.y;
+  }
+  double t[1];
+  if (grid_sum<1>(v, rb, t)) *out = t[0];
+}
+
 double true_residual_df(pfmp_op* op, const void* x64, const void* b64, void* r64) {
   pfmp_ctx* c = op->ctx;
   const long n = 12L * c->g.Vh;
@@ -42,6 +58,30 @@ double true_residual_df(pfmp_op* op, const void* x64, const void* b64, void* r64
   PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PFMP_CUDA(cudaStreamSynchronize(c->stream));
   return c->h_sums[0];
+}
+
+// r = b - K x with K in FP64 (x must not alias r); returns |r|^2 (synchronises)
+double true_residual_f64(pfmp_op* op, const void* x64, const void* b64, void* r64) {
+  pfmp_ctx* c = op->ctx;
+  const long n = 12L * c->g.Vh;
+  kop(op, PFMP_F64, r64, x64, nullptr, nullptr);
+  k_b_minus_r<<<rgrid(n), kBlock, 0, c->stream>>>((const double2*)b64, (double2*)r64, n, c->rb, c->d_sums);
+  PFMP_CHECK_LAUNCH();
+  PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PFMP_CUDA(cudaStreamSynchronize(c->stream));
+  return c->h_sums[0];
+}
+
+// The mixed solvers' true residual: double-float, and once that is below target_rr the
+// FP64 recomputation, which decides (returns |r|^2; adds the K applications to *kapply)
+double true_residual_mixed(pfmp_op* op, const void* x64, const void* b64, void* r64, double target_rr, long* kapply) {
+  double rr = true_residual_df(op, x64, b64, r64);
+  *kapply += 1;
+  if (rr < target_rr) {
+    rr = true_residual_f64(op, x64, b64, r64);
+    *kapply += 1;
+  }
+  return rr;
 }
 
 }  // namespace pfmp

@@ -4,8 +4,10 @@
 //    scales) and FP32 arithmetic; x and r stay FP32.
 //  * mixed: FP32 CG ("sloppy") with FP64 reliable updates: every time the sloppy residual
 //    has fallen by `delta` (or reached the target) the accumulated FP32 solution is
-//    added to the FP64 solution and the true residual b - K x is recomputed in FP64;
-//    the sloppy residual restarts from it while the search direction is kept.
+//    added to the FP64 solution and the true residual b - K x is recomputed (in
+//    double-float on the FP32 pipe, and in FP64 once it is below the target: the FP64
+//    value decides and is reported); the sloppy residual restarts from it while the
+//    search direction is kept.
 // The iteration runs on the device with no host round trip: alpha and beta come from
 // device scalars written by the reduction finishers, and a `done` flag makes every
 // queued kernel return at once after convergence.  The host looks at the scalars
@@ -190,10 +192,10 @@ int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int c
       total += it;
       *kapply += it;
       PFMP_REQUIRE(std::isfinite(op->h_scal->rr), PFMP_E_NAN, "sloppy CG residual became NaN/Inf");
-      // reliable update: the true residual in double-float (FP64 accuracy on the FP32 pipe)
+      // reliable update: the true residual in double-float (FP32 pipe), confirmed in FP64
+      // once it is below the target
       blas_add_lo(c, x, xs32);
-      rr_true = true_residual_df(op, x, b, r);
-      *kapply += 1;
+      rr_true = true_residual_mixed(op, x, b, r, tol * tol * bb, kapply);
       *rel_updates += 1;
       if (std::sqrt(rr_true / bb) < tol) break;
       blas_copy(c, r32, PFMP_F32, r, PFMP_F64);
