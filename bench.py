@@ -605,6 +605,129 @@ def learned(capi, stream, l2_flush, args, ctx, op, b, x):
     return out
 
 
+def learned_32x32x32x64(capi, stream, npairs=256, steps=300, ntherm=60):
+    """The learned preconditioner at scale.  Training field: 24^3 x 48 thermalised by
+    ntherm pure-gauge HMC trajectories at beta = 5.5 (seed 5), Wilson-clover c_sw = 1.6;
+    kappa: the lightest of 0.125 .. 0.135 (steps of 0.0025) at which the mixed CG reaches
+    1e-10 within 20000 iterations on it.  npairs (b, x = K^{-1} b) pairs from the mixed
+    solver (Gaussian b), a [1, 8, 8, 8, 1] network trained on them (residual loss, Adam,
+    batch 4).  Evaluation field: 32^3 x 64 thermalised the same way (seed 6), a Gaussian
+    right-hand side: FGCR with the network (tensor-core layers), GCR without it, the mixed
+    CG and the FP64 CG, all to a 1e-10 FP64 true residual; wall times by CUDA events."""
+    import torch
+
+    import pfmp_inputs as pin
+
+    csw, tol = 1.6, 1e-10
+    out = {"csw": csw, "beta": 5.5}
+    mixed = capi.SolverParams(method=capi.PFMP_SOLVER_CG_MIXED, tol=tol, max_iter=20000, delta=1e-4, check_every=16)
+    # ---- training field and the kappa scan
+    tdims = (24, 24, 24, 48)
+    tctx = capi.pfmp_ctx_create(tdims, -1, stream.cuda_stream)
+    out["train_thermalisation"] = thermalise(capi, tctx, tdims, ntherm, 5)
+    n64 = capi.pfmp_spinor_bytes(tctx, capi.PFMP_F64) // 8
+
+    def rhs(ctx, dims, seed, n):
+        bc = torch.tensor(np.ascontiguousarray(pin.spinor(dims, seed)).view(np.float64).reshape(-1), device="cuda")
+        bb = torch.zeros(n, dtype=torch.float64, device="cuda")
+        capi.pfmp_spinor_pack(ctx, bb, capi.PFMP_F64, bc, capi.PFMP_DEVICE, 0)
+        return bb
+
+    b0 = rhs(tctx, tdims, 7000, n64)
+    x0 = torch.zeros_like(b0)
+    scan, kappa = [], None
+    for kap in (0.125, 0.1275, 0.130, 0.1325, 0.135):
+        op = capi.pfmp_op_create(tctx, kap, csw)
+        t0 = time.perf_counter()
+        info = capi.pfmp_solve(op, mixed, x0, b0, raise_on_error=False)
+        scan.append({"kappa": kap, "iterations": info.iters, "status": info.status, "s": time.perf_counter() - t0,
+                     "true_rel_res": info.true_rel_res})
+        capi.pfmp_op_destroy(op)
+        if info.status == 0:
+            kappa = kap
+        else:
+            break
+    out["kappa_scan"] = scan
+    out["kappa"] = kappa
+    if kappa is None:
+        capi.pfmp_ctx_destroy(tctx)
+        return out
+    top = capi.pfmp_op_create(tctx, kappa, csw)
+    bs, xs = [], []
+    t0 = time.perf_counter()
+    for i in range(npairs):
+        bb = rhs(tctx, tdims, 8000 + i, n64)
+        xx = torch.zeros_like(bb)
+        capi.pfmp_solve(top, mixed, xx, bb)
+        bs.append(bb)
+        xs.append(xx)
+    torch.cuda.synchronize()
+    out["pairs"] = npairs
+    out["pairs_s"] = time.perf_counter() - t0
+    ch = [1, 8, 8, 8, 1]
+    net = capi.pfmp_nn_create(tctx, ch, capi.PFMP_F32)
+    capi.pfmp_nn_set_weights(net, pin.nn_weights(ch, 5))
+    t0 = time.perf_counter()
+    loss = capi.pfmp_nn_train(net, bs, xs, steps=steps, batch=4, lr=5e-3, op=top, kind=capi.PFMP_NN_LOSS_RESIDUAL)
+    torch.cuda.synchronize()
+    out.update({"train_steps": steps, "train_s": time.perf_counter() - t0, "final_train_loss": loss, "network": ch})
+    w = capi.pfmp_nn_get_weights(net, [(9, co, ci, 4, 4) for ci, co in zip(ch[:-1], ch[1:])])
+    capi.pfmp_nn_destroy(net)
+    del bs, xs
+    capi.pfmp_op_destroy(top)
+    capi.pfmp_ctx_destroy(tctx)
+    # ---- evaluation at 32^3 x 64
+    edims = (32, 32, 32, 64)
+    ctx = capi.pfmp_ctx_create(edims, -1, stream.cuda_stream)
+    try:
+        out["eval_thermalisation"] = thermalise(capi, ctx, edims, ntherm, 6)
+        op = capi.pfmp_op_create(ctx, kappa, csw)
+        n64 = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F64) // 8
+        b = rhs(ctx, edims, 9000, n64)
+        x = torch.zeros_like(b)
+        net = capi.pfmp_nn_create(ctx, ch, capi.PFMP_F32)
+        capi.pfmp_nn_set_weights(net, w)
+        capi.pfmp_nn_set_tensor_cores(net, 1)
+
+        def timed(fn):
+            fn()  # warm
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = fn()
+            e1.record(stream)
+            e1.synchronize()
+            return {"ms": e0.elapsed_time(e1), "iterations": info.iters, "true_rel_res": info.true_rel_res,
+                    "status": info.status}
+
+        prm = capi.SolverParams(method=0, tol=tol, max_iter=20000, delta=1e-3, check_every=8, restart=16)
+        plain = capi.SolverParams(method=capi.PFMP_SOLVER_CG64, tol=tol, max_iter=40000, delta=0.1, check_every=16)
+        res = {"fgcr_nn": timed(lambda: capi.pfmp_solve_fgcr(op, net, prm, x, b, raise_on_error=False)),
+               "gcr": timed(lambda: capi.pfmp_solve_fgcr(op, None, prm, x, b, raise_on_error=False)),
+               "mixed_cg": timed(lambda: capi.pfmp_solve(op, mixed, x, b, raise_on_error=False)),
+               "fp64_cg": timed(lambda: capi.pfmp_solve(op, plain, x, b, raise_on_error=False))}
+        n32 = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F32) // 4
+        vin = torch.randn(n32, dtype=torch.float32, device="cuda")
+        vout = torch.zeros_like(vin)
+        capi.pfmp_nn_apply(net, capi.PFMP_F32, vout, vin)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            capi.pfmp_nn_apply(net, capi.PFMP_F32, vout, vin)
+        e1.record(stream)
+        e1.synchronize()
+        res["network_apply_ms"] = e0.elapsed_time(e1) / 5
+        res["speedup_fgcr_nn_vs_fp64_cg"] = res["fp64_cg"]["ms"] / res["fgcr_nn"]["ms"]
+        res["speedup_mixed_cg_vs_fp64_cg"] = res["fp64_cg"]["ms"] / res["mixed_cg"]["ms"]
+        out["eval_32x32x32x64"] = res
+        capi.pfmp_nn_destroy(net)
+        capi.pfmp_op_destroy(op)
+    finally:
+        capi.pfmp_ctx_destroy(ctx)
+    return out
+
+
 def guarded(fn, *a):
     """A secondary measurement that must not take the headline line down with it."""
     try:
@@ -658,6 +781,45 @@ def trajectory_16x16x16x32(capi, stream, force_prec=0):
     return out
 
 
+def thermalise(capi, ctx, dims, ntherm, seed, beta=5.5):
+    """A random start (U = exp(i H), H from seed) thermalised by ntherm pure-gauge HMC
+    trajectories at beta (2MN, 10 steps over tau = 1; the first half accepted
+    unconditionally, the rest with the Metropolis test); returns the plaquette history
+    (thinned) and the acceptance of the second half."""
+    import torch
+
+    import pfmp_inputs as pin
+
+    lam = 0.1931833275037836
+    h = torch.tensor(np.ascontiguousarray(pin.gauge_algebra(dims, seed)).reshape(-1), device="cuda")
+    torch.cuda.synchronize()
+    capi.pfmp_gauge_from_algebra(ctx, h, 1.0, capi.PFMP_DEVICE)
+    del h
+    dq = capi.ActionDef()
+    dq.beta, dq.csw, dq.nkappa = beta, 0.0, 1   # no fermion term: no clover needed
+    dq.kappa[0] = 0.1
+    dq.mu, dq.nu, dq.tol, dq.max_iter = 1.2, 0.9, 1e-10, 20000
+    dq.nterms = 1
+    dq.term[0] = capi.Term(capi.PFMP_KIND_GAUGE, 0, 0, 0, 0)
+    Aq = capi.pfmp_action_create_def(ctx, dq)
+    Tq, Sq = capi.pfmp_schedule_merge([capi.pfmp_schedule_2mn(10, 1.0, lam)])
+    plaq, accq = [capi.pfmp_plaquette(ctx)], []
+    t0 = time.perf_counter()
+    try:
+        for k in range(ntherm):
+            u = 0.0 if k < ntherm // 2 else float(pin.uniform(1000 * seed + 31000 + k)[0])
+            mom = np.ascontiguousarray(pin.momenta(dims, 1000 * seed + 30000 + k)).reshape(-1)
+            info = capi.pfmp_trajectory(Aq, Tq, Sq, [0], mom, np.zeros(1), u)
+            plaq.append(info.plaquette)
+            if k >= ntherm // 2:
+                accq.append(int(info.accepted))
+    finally:
+        capi.pfmp_action_destroy(Aq)
+    return {"trajectories": ntherm, "s": time.perf_counter() - t0, "beta": beta,
+            "acceptance": float(np.mean(accq)) if accq else None,
+            "plaquette_history": plaq[:: max(1, len(plaq) // 25)] + [plaq[-1]]}
+
+
 PROD_DIMS = (24, 24, 24, 48)
 PROD = dict(beta=5.5, csw=1.6, kappa=0.134, kappa1=0.120, kappa2=0.130, p1=12, p2=64, steps=(60, 24, 10, 4), tau=1.0)
 
@@ -691,32 +853,7 @@ def production_24x24x24x48(capi, stream, ntraj=10, ntherm=100, reversibility=Tru
     ctx = capi.pfmp_ctx_create(dims, -1, stream.cuda_stream)
     out = {"lattice": "24x24x24x48", "params": dict(PROD, force_prec="f32" if fp == capi.PFMP_F32 else "f64")}
     try:
-        h = torch.tensor(np.ascontiguousarray(pin.gauge_algebra(dims, 3)).reshape(-1), device="cuda")
-        torch.cuda.synchronize()
-        capi.pfmp_gauge_from_algebra(ctx, h, 1.0, capi.PFMP_DEVICE)
-        del h
-        # pure-gauge HMC thermalisation
-        dq = capi.ActionDef()
-        dq.beta, dq.csw, dq.nkappa = PROD["beta"], 0.0, 1   # no fermion term: no clover needed
-        dq.kappa[0] = PROD["kappa"]
-        dq.mu, dq.nu, dq.tol, dq.max_iter = 1.2, 0.9, 1e-10, 20000
-        dq.nterms = 1
-        dq.term[0] = capi.Term(capi.PFMP_KIND_GAUGE, 0, 0, 0, 0)
-        Aq = capi.pfmp_action_create_def(ctx, dq)
-        Tq, Sq = capi.pfmp_schedule_merge([capi.pfmp_schedule_2mn(10, 1.0, lam)])
-        plaq, accq = [capi.pfmp_plaquette(ctx)], []
-        t0 = time.perf_counter()
-        for k in range(ntherm):
-            # the first half accepted unconditionally (u = 0), the rest with the Metropolis test
-            u = 0.0 if k < ntherm // 2 else float(pin.uniform(31000 + k)[0])
-            info = capi.pfmp_trajectory(Aq, Tq, Sq, [0], np.ascontiguousarray(pin.momenta(dims, 30000 + k)).reshape(-1),
-                                        np.zeros(1), u)
-            plaq.append(info.plaquette)
-            if k >= ntherm // 2:
-                accq.append(int(info.accepted))
-        out["thermalisation"] = {"trajectories": ntherm, "s": time.perf_counter() - t0, "acceptance": float(np.mean(accq)) if accq else None,
-                                 "plaquette_history": plaq[:: max(1, len(plaq) // 25)] + [plaq[-1]]}
-        capi.pfmp_action_destroy(Aq)
+        out["thermalisation"] = thermalise(capi, ctx, dims, ntherm, 3)
         # spectrum of J_1 and an estimate for K (Lanczos: lmax converges, lmin from above)
         nb = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F64) // 8
         v0 = torch.zeros(nb, dtype=torch.float64, device="cuda")
@@ -792,8 +929,10 @@ def production_24x24x24x48(capi, stream, ntraj=10, ntherm=100, reversibility=Tru
             ms = (time.perf_counter() - t0) * 1e3
             trajs.append({"ms": ms, "dH": info.dH, "accepted": bool(info.accepted), "plaquette": info.plaquette,
                           "k_apply": int(info.k_apply), "force_evals": int(info.force_evals),
+                          "ms_link_updates": info.ms_update,
                           "per_term": {n: {"k_apply": int(info.k_apply_term[t]), "forces": int(info.nforce[t]),
-                                           "fmax": info.fmax[t], "favg": info.favg[t]} for t, n in enumerate(names)}})
+                                           "fmax": info.fmax[t], "favg": info.favg[t], "ms": info.ms_force[t]}
+                                       for t, n in enumerate(names)}})
         out["trajectories"] = trajs
         if trajs:
             out["summary"] = {"ms_per_trajectory": statistics.mean(t["ms"] for t in trajs),
@@ -801,7 +940,9 @@ def production_24x24x24x48(capi, stream, ntraj=10, ntherm=100, reversibility=Tru
                               "dH": [t["dH"] for t in trajs],
                               "exp_minus_dH": float(np.mean([math.exp(-t["dH"]) for t in trajs])),
                               "n_mat_per_term": {n: float(np.mean([t["per_term"][n]["k_apply"] for t in trajs]))
-                                                 for n in names}}
+                                                 for n in names},
+                              "ms_per_term": {n: float(np.mean([t["per_term"][n]["ms"] for t in trajs])) for n in names},
+                              "ms_link_updates": float(np.mean([t["ms_link_updates"] for t in trajs]))}
         capi.pfmp_action_destroy(A)
     finally:
         capi.pfmp_ctx_destroy(ctx)
@@ -1048,6 +1189,9 @@ def main():
     ap.add_argument("--production", action="store_true",
                     help="only the 24^3x48 production PF-MP run (thermalisation, reversibility, trajectories)")
     ap.add_argument("--prod-traj", type=int, default=10)
+    ap.add_argument("--learned-scale", action="store_true",
+                    help="only the learned preconditioner at scale (train on 24^3x48, FGCR at 32^3x64)")
+    ap.add_argument("--pairs", type=int, default=256)
     ap.add_argument("--prod-therm", type=int, default=100)
     ap.add_argument("--cpu-full", action="store_true",
                     help="only the oracle's CPU timings: full solve on one thread and on all cores, 4^4 trajectory")
@@ -1070,6 +1214,14 @@ def main():
     args = ap.parse_args()
     if args.cpu_full:
         cpu_full()
+        return
+    if args.learned_scale:
+        import torch
+
+        from paper_1609_02652_gb300 import capi
+
+        stream = torch.cuda.Stream()
+        print(json.dumps(learned_32x32x32x64(capi, stream, args.pairs, args.nn_steps)), flush=True)
         return
     if args.production:
         import torch

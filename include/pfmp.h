@@ -345,6 +345,10 @@ typedef struct {
   int nforce[PFMP_MAX_TERMS];            /* force evaluations of each term                   */
   double fmax[PFMP_MAX_TERMS];  /* max over the trajectory of max_links |F|, |F| = sqrt(sum_a f_a^2) */
   double favg[PFMP_MAX_TERMS];  /* mean over the trajectory of the link average of |F|      */
+  double ms_force[PFMP_MAX_TERMS];  /* wall time of each term's force evaluations (ms)       */
+  double ms_update;                 /* wall time of the link updates with the rebuild of the
+                                       compressed copies and clover terms (ms)              */
+  double ms_total;                  /* wall time of the whole call (ms)                     */
 } pfmp_traj_info;
 /* Schemes compared in Sec. 3 (term lists; kappa[1], kappa[2] are the Hasenbusch kappas):
  *   1PF      GAUGE, DET, FILTER(0; p2), FILTERCORR(0; p2)              (eq. 1poly on K)

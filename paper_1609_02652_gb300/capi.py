@@ -87,7 +87,8 @@ class TrajInfo(C.Structure):
                 ("S0", C.c_double * PFMP_MAX_TERMS), ("S1", C.c_double * PFMP_MAX_TERMS),
                 ("plaquette", C.c_double), ("k_apply", C.c_int64), ("force_evals", C.c_int),
                 ("k_apply_term", C.c_int64 * PFMP_MAX_TERMS), ("nforce", C.c_int * PFMP_MAX_TERMS),
-                ("fmax", C.c_double * PFMP_MAX_TERMS), ("favg", C.c_double * PFMP_MAX_TERMS)]
+                ("fmax", C.c_double * PFMP_MAX_TERMS), ("favg", C.c_double * PFMP_MAX_TERMS),
+                ("ms_force", C.c_double * PFMP_MAX_TERMS), ("ms_update", C.c_double), ("ms_total", C.c_double)]
 
 P = C.c_void_p
 I = C.c_int

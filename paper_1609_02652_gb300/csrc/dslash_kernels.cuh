@@ -55,6 +55,8 @@ __global__ void __launch_bounds__(128, hop_min_blocks<PREC>()) k_hop(HopParams<P
     Spinor<typename Prec<PREC>::real> out;
     if constexpr (hop_rolled<PREC>())
       out = hop_site_rolled<PREC, DAG, EPI>(a, cb);
+    else if constexpr (PREC == PFMP_H16)
+      out = hop_site_h16<DAG, EPI>(a, cb);
     else
       out = hop_site<PREC, DAG, EPI>(a, cb);
     store_spinor(a.out, out, cb, a.g.Vh);

@@ -107,6 +107,179 @@ __device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site(const HopP
   return out;
 }
 
+// ---------------------------------------------------------------- FP16 storage, half2 arithmetic
+// The stencil on FP16 storage converts few values to FP32: each neighbour spinor
+// (stored as value / scale, |entries| <= 1) is spin-projected in packed half2 adds, the
+// FP16 link (never converted; its third row rebuilt in half2) multiplies the half
+// spinor with half2 FMAs, and only the 12 reals of each direction's product are
+// converted, multiplied by the neighbour's scale (and the boundary factor) and summed in
+// FP32, where the four-component rebuild and the clover epilogue happen.  Conversions per
+// site: 8 x 12 + 72 (clover) instead of 8 x (24 + 12) + 72.  Complex numbers are half2
+// (re, im); a x b = hi(a) (i b) + lo(a) b with lo, hi the broadcast real and imaginary
+// parts, and conj(a) x b = lo(a) b - hi(a) (i b).
+__device__ __forceinline__ __half2 u2h2(uint32_t u) {
+  __half2 h;
+  memcpy(&h, &u, 4);
+  return h;
+}
+__device__ __forceinline__ __half2 h2_times_i(__half2 v) {  // i v = (-im, re)
+  return __hmul2(__lowhigh2highlow(v), __floats2half2_rn(-1.f, 1.f));
+}
+__device__ __forceinline__ __half2 h2_cmul(__half2 a, __half2 b, __half2 ib) {  // a b
+  return __hfma2(__high2half2(a), ib, __hmul2(__low2half2(a), b));
+}
+__device__ __forceinline__ __half2 h2_cfma(__half2 a, __half2 b, __half2 ib, __half2 acc) {  // acc + a b
+  return __hfma2(__high2half2(a), ib, __hfma2(__low2half2(a), b, acc));
+}
+__device__ __forceinline__ __half2 h2_cjfma(__half2 a, __half2 b, __half2 ib, __half2 acc) {  // acc + conj(a) b
+  return __hfma2(__hneg2(__high2half2(a)), ib, __hfma2(__low2half2(a), b, acc));
+}
+__device__ __forceinline__ __half2 h2_conj(__half2 v) { return __hmul2(v, __floats2half2_rn(1.f, -1.f)); }
+
+// FP16 link as half2 [3][3], third row conj(row0 x row1) rebuilt in half2
+__device__ __forceinline__ void load_link_h2(__half2 U[3][3], const uint4* __restrict__ f, int cb, int Vh) {
+  const uint4 v0 = __ldg(f + cb);
+  const uint2 v1 = __ldg(reinterpret_cast<const uint2*>(f + Vh) + cb);
+  U[0][0] = u2h2(v0.x);
+  U[0][1] = u2h2(v0.y);
+  U[0][2] = u2h2(v0.z);
+  U[1][0] = u2h2(v0.w);
+  U[1][1] = u2h2(v1.x);
+  U[1][2] = u2h2(v1.y);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int k = (j + 1) % 3, l = (j + 2) % 3;
+    const __half2 b1 = U[1][l], b2 = U[1][k];
+    const __half2 t = h2_cmul(U[0][k], b1, h2_times_i(b1));
+    U[2][j] = h2_conj(__hsub2(t, h2_cmul(U[0][l], b2, h2_times_i(b2))));
+  }
+}
+
+// (1 + S g_MU) psi of a half2 spinor p[spin][colour]: the two components h[2][3]
+template <int MU, int S>
+__device__ __forceinline__ void project_h2(const __half2 p[4][3], __half2 h[2][3]) {
+  const __half2 pi = __floats2half2_rn(-1.f, 1.f), mi = __floats2half2_rn(1.f, -1.f);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (MU == 0) {  // p0 +- i p3, p1 +- i p2
+      h[0][c] = __hfma2(__lowhigh2highlow(p[3][c]), S > 0 ? pi : mi, p[0][c]);
+      h[1][c] = __hfma2(__lowhigh2highlow(p[2][c]), S > 0 ? pi : mi, p[1][c]);
+    } else if (MU == 1) {  // p0 -+ p3, p1 +- p2
+      h[0][c] = S > 0 ? __hsub2(p[0][c], p[3][c]) : __hadd2(p[0][c], p[3][c]);
+      h[1][c] = S > 0 ? __hadd2(p[1][c], p[2][c]) : __hsub2(p[1][c], p[2][c]);
+    } else if (MU == 2) {  // p0 +- i p2, p1 -+ i p3
+      h[0][c] = __hfma2(__lowhigh2highlow(p[2][c]), S > 0 ? pi : mi, p[0][c]);
+      h[1][c] = __hfma2(__lowhigh2highlow(p[3][c]), S > 0 ? mi : pi, p[1][c]);
+    } else {  // p0 +- p2, p1 +- p3
+      h[0][c] = S > 0 ? __hadd2(p[0][c], p[2][c]) : __hsub2(p[0][c], p[2][c]);
+      h[1][c] = S > 0 ? __hadd2(p[1][c], p[3][c]) : __hsub2(p[1][c], p[3][c]);
+    }
+  }
+}
+
+// one hop term on FP16 storage: load, project, transport in half2; the product times
+// `scale` (the neighbour's spinor scale and boundary factor) summed into acc in FP32
+template <int MU, int S, bool DAGU>
+__device__ __forceinline__ void hop_term_h16(Spinor<float>& acc, const uint4* __restrict__ in, const uint4* lf, int n,
+                                             int lcb, int Vh, float bcf) {
+  __half2 p[4][3];
+  const float sc = bcf * __ldg(reinterpret_cast<const float*>(in + (size_t)3 * Vh) + n);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint4 v = __ldg(in + (size_t)k * Vh + n);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) p[(4 * k + j) / 3][(4 * k + j) % 3] = u2h2(w[j]);
+  }
+  __half2 h[2][3], ih[2][3];
+  project_h2<MU, S>(p, h);
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ih[k][c] = h2_times_i(h[k][c]);
+  __half2 U[3][3];
+  load_link_h2(U, lf, lcb, Vh);
+  Half<float> r;
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      __half2 t;
+      if (DAGU) {  // sum_j conj(U[j][i]) h[k][j]
+        t = h2_cjfma(U[0][i], h[k][0], ih[k][0], __float2half2_rn(0.f));
+        t = h2_cjfma(U[1][i], h[k][1], ih[k][1], t);
+        t = h2_cjfma(U[2][i], h[k][2], ih[k][2], t);
+      } else {  // sum_j U[i][j] h[k][j]
+        t = h2_cmul(U[i][0], h[k][0], ih[k][0]);
+        t = h2_cfma(U[i][1], h[k][1], ih[k][1], t);
+        t = h2_cfma(U[i][2], h[k][2], ih[k][2], t);
+      }
+      const float2 f = __half22float2(t);
+      r.h[k][i] = mk(sc * f.x, sc * f.y);
+    }
+  accumulate<MU, S>(acc, r);
+}
+
+template <int MU, int SF>
+__device__ __forceinline__ void hop_dir_h16(Spinor<float>& acc, const HopParams<PFMP_H16>& a, const int x[4],
+                                            int cb) {
+  const Geom& g = a.g;
+  const int Vh = g.Vh;
+  {
+    const int n = nbr_cb(g, x, MU, +1);
+    const float f = (MU == 3 && x[3] == g.L[3] - 1) ? (float)g.bc_t : 1.0f;
+    hop_term_h16<MU, SF, false>(acc, a.in, link_plane<PFMP_H16>(a.gauge, a.p * 4 + MU, Vh), n, cb, Vh, f);
+  }
+  {
+    const int n = nbr_cb(g, x, MU, -1);
+    const float f = (MU == 3 && x[3] == 0) ? (float)g.bc_t : 1.0f;
+    hop_term_h16<MU, -SF, true>(acc, a.in, link_plane<PFMP_H16>(a.gauge, (1 - a.p) * 4 + MU, Vh), n, n, Vh, f);
+  }
+}
+
+template <bool DAG, int EPI>
+__device__ __forceinline__ Spinor<float> hop_site_h16(const HopParams<PFMP_H16>& a, int cb) {
+  int x[4];
+  cb_coords(a.g, cb, a.p, x);
+  Spinor<float> acc;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc.s[s][c] = mk(0.f, 0.f);
+  constexpr int SF = DAG ? +1 : -1;
+  hop_dir_h16<0, SF>(acc, a, x, cb);
+  hop_dir_h16<1, SF>(acc, a, x, cb);
+  hop_dir_h16<2, SF>(acc, a, x, cb);
+  hop_dir_h16<3, SF>(acc, a, x, cb);
+  Spinor<float> out;
+  const float cf = (float)a.coef;
+  if (EPI == EPI_PLAIN) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out.s[s][c] = cf * acc.s[s][c];
+  } else if (EPI == EPI_CLOV) {
+    HermBlock<float> B[2];
+    load_clover(B, a.clov, cb, a.g.Vh);
+    out = clover_apply(B, acc);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out.s[s][c] = cf * out.s[s][c];
+  } else {
+    HermBlock<float> B[2];
+    load_clover(B, a.clov, cb, a.g.Vh);
+    Spinor<float> xl;
+    load_spinor(xl, a.x, cb, a.g.Vh);
+    out = clover_apply(B, xl);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out.s[s][c] = out.s[s][c] + cf * acc.s[s][c];
+  }
+  return out;
+}
+
 // ---------------------------------------------------------------- rolled stencil
 // The same stencil with the 8 hop terms in a run-time loop and the two clover blocks in
 // another, so that the colour multiply and the 6x6 block product exist once in the code

@@ -25,6 +25,7 @@
 // Trajectory (Sec. 2.1, App. B): for each step of the merged schedule T-hat then the S-hat
 // of every level with a non-zero step; Metropolis accept iff u < exp(-dH).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -719,27 +720,38 @@ void force_norms(pfmp_action* A, double* sum, double* mx) {
 // the MD part of a trajectory (Sec. 2.1, App. B): for each step of the merged schedule
 // T-hat, then P -= eps F_t for every term t on each level with a non-zero step, one term
 // at a time so that each term's force is measured (sums of the link averages into favg)
+static double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 static void md_steps(pfmp_action* A, int len, const double* T, int nlev, const double* S, const int* term_level,
                      pfmp_traj_info* info) {
   const int nt = (int)A->t.size();
   const double nlinks = 4.0 * A->ctx->g.V;
   for (int i = 0; i < len; ++i) {
-    if (T[i] != 0.0) link_update(A, T[i]);
+    if (T[i] != 0.0) {
+      const auto t0 = std::chrono::steady_clock::now();
+      link_update(A, T[i]);
+      PFMP_CUDA(cudaStreamSynchronize(A->ctx->stream));
+      info->ms_update += ms_since(t0);
+    }
     for (int l = 0; l < nlev; ++l) {
       const double eps = S[(size_t)l * len + i];
       if (eps == 0.0) continue;
       for (int t = 0; t < nt; ++t) {
         if (term_level[t] != l) continue;
+        const auto t0 = std::chrono::steady_clock::now();
         const long long kt = kapply_total(A);
         action_zero_force(A);
         action_force(A, t);
         mom_update(A, eps);
         info->k_apply_term[t] += kapply_total(A) - kt;
         double fs, fm;
-        force_norms(A, &fs, &fm);
+        force_norms(A, &fs, &fm);  // synchronises
         info->nforce[t] += 1;
         info->fmax[t] = std::max(info->fmax[t], fm);
         info->favg[t] += fs / nlinks;
+        info->ms_force[t] += ms_since(t0);
       }
     }
   }
@@ -773,6 +785,7 @@ void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double
   for (int t = 0; t < nt; ++t)
     PFMP_REQUIRE(term_level[t] >= -1 && term_level[t] < nlev, PFMP_E_INVALID, "term level out of range");
   *info = pfmp_traj_info{};
+  const auto t_start = std::chrono::steady_clock::now();
   const long long k0 = kapply_total(A);
   A->force_evals = 0;
   PFMP_CUDA(cudaMemcpyAsync(A->U0, c->U64, (size_t)g.Vh * 72 * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
@@ -821,6 +834,7 @@ void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double
   info->force_evals = A->force_evals;
   if (!acc) restore();
   info->plaquette = plaquette(c);
+  info->ms_total = ms_since(t_start);
 }
 
 // ------------------------------------------------------------------ schedules (host)

@@ -30,6 +30,8 @@
 // waits (bounded) for the work it has in flight, frees its tensor memory and returns.
 #include <cuda_fp16.h>
 
+#include <cstdlib>
+
 #include "context.h"
 #include "fields.cuh"
 
@@ -196,15 +198,21 @@ __device__ __forceinline__ void make_hop(const Geom& g, const float4* __restrict
   h.sy = (size_t)lex_index(g, y);
 }
 
-__device__ __forceinline__ void load_channel(const __half2* __restrict__ in, size_t V, size_t sy, int ic,
-                                             cplx<float> v[4][3]) {
+// site-major activations act[site][C][12] (half2 complex, 48 C bytes per site): the 12
+// components of channel ic at site sy as three 16-byte words
+template <int C>
+__device__ __forceinline__ void load_channel(const __half2* __restrict__ in, size_t sy, int ic, cplx<float> v[4][3]) {
+  const uint4* p = reinterpret_cast<const uint4*>(in + (sy * C + ic) * 12);
 #pragma unroll
-  for (int sp = 0; sp < 4; ++sp)
+  for (int q = 0; q < 3; ++q) {
+    const uint4 w4 = __ldg(p + q);
+    const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float2 w = __half22float2(__ldg(in + ((size_t)ic * 12 + sp * 3 + c) * V + sy));
-      v[sp][c] = mk(w.x, w.y);
+    for (int j = 0; j < 4; ++j) {
+      const float2 f = h2_to_f2(w[j]);
+      v[(4 * q + j) / 3][(4 * q + j) % 3] = mk(f.x, f.y);
     }
+  }
 }
 
 // transport one channel and store it (FP16) at column col of the three colour tiles
@@ -257,7 +265,7 @@ __device__ __forceinline__ void gather_stage(const Geom& g, const float4* __rest
     cplx<float> v[4][3];
     if (on) {
       make_hop(g, U32, x, dir_of(di), h);
-      load_channel(in, V, h.sy, 0, v);
+      load_channel<1>(in, h.sy, 0, v);
     }
     store_channel<K>(h, v, on, A, row, part * 8, a_tile);
   } else {
@@ -266,8 +274,8 @@ __device__ __forceinline__ void gather_stage(const Geom& g, const float4* __rest
     const int ic0 = part, ic1 = part + 4;
     if (live) {
       make_hop(g, U32, x, dir_of(st), h);
-      load_channel(in, V, h.sy, ic0, v0);
-      load_channel(in, V, h.sy, ic1, v1);
+      load_channel<8>(in, h.sy, ic0, v0);
+      load_channel<8>(in, h.sy, ic1, v1);
     }
     store_channel<K>(h, v0, live, A, row, ic0 * 8, a_tile);
     store_channel<K>(h, v1, live, A, row, ic1 * 8, a_tile);
@@ -275,7 +283,7 @@ __device__ __forceinline__ void gather_stage(const Geom& g, const float4* __rest
 }
 
 // network input: sigma * (even FP32 field [6][Vh] float4) on even sites, 0 on odd sites,
-// as FP16 complex [12][V] (lexicographic sites)
+// as FP16 complex [V][12] (lexicographic sites, site-major)
 // rr (optional): |src|^2 already known to the caller (FGCR's residual norm); sigma is then
 // computed here, stored for the later kernels, and no separate reduction is needed
 __global__ void k_embed16(Geom g, const float4* __restrict__ src, float* __restrict__ sigma_p,
@@ -298,12 +306,16 @@ __global__ void k_embed16(Geom g, const float4* __restrict__ src, float* __restr
   const bool even = ((x[0] + x[1] + x[2] + x[3]) & 1) == 0;
   const float sg = rr ? (*rr > 0 ? (float)sqrt(24.0 * g.Vh / *rr) : 1.0f) : *sigma_p;
   const int cb = s >> 1;
+  uint32_t w[12];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     float4 v = even ? src[(size_t)k * g.Vh + cb] : make_float4(0.f, 0.f, 0.f, 0.f);
-    dst[(size_t)(2 * k) * g.V + s] = __floats2half2_rn(sg * v.x, sg * v.y);
-    dst[(size_t)(2 * k + 1) * g.V + s] = __floats2half2_rn(sg * v.z, sg * v.w);
+    w[2 * k] = pack_h2(sg * v.x, sg * v.y);
+    w[2 * k + 1] = pack_h2(sg * v.z, sg * v.w);
   }
+  uint4* d = reinterpret_cast<uint4*>(dst + (size_t)s * 12);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) d[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
 }
 
 // last layer, second half: out(x) = sum_d U_d(x) z_d(x + d) on even sites (the only ones
@@ -500,7 +512,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int r = col / S::N, n = col % S::N;
             const int o = n >> 3, a = (n >> 1) & 3;
             if (o < COUT) {
-              const size_t idx = ((size_t)o * 12 + a * 3 + r) * V + srow;
+              // COUT = 8: site-major activations [V][8][12]; the local mixing (COUT = 9)
+              // writes z as [9][12][V] for k_last_stencil
+              const size_t idx = S::LOCAL ? ((size_t)o * 12 + a * 3 + r) * V + srow
+                                          : ((size_t)srow * COUT + o) * 12 + a * 3 + r;
               if (OUT16)
                 reinterpret_cast<__half2*>(out)[idx] = __floats2half2_rn(v[j], v[j + 1]);
               else
@@ -518,6 +533,265 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int b = 0; b < 2; ++b)
       if (pending[b] >= 0) mbar_wait(smem_addr(&bar_a[b]), ((uint32_t)pending[b] >> 1) & 1);
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TMEM_COLS));
+}
+
+// ---------------------------------------------------------------- pipelined layer (C_out = 8)
+// The same contraction with the gather split in two: raw neighbour activations go
+// global -> shared by 16-byte cp.async copies (no registers held, so many bytes are in
+// flight), one stage ahead of the stage being transported; the links of the next stage
+// are prefetched into registers.  Per stage: issue the copies of stage u + 1, wait for
+// those of stage u, transport them from the staging buffer into the FP16 A tiles, one
+// thread issues the MMAs.  Staging rows are XOR-swizzled in 8-word groups (16-byte word j
+// of row r stored at j ^ (r & 7) within its group) so that the threads of a warp, one
+// row each, read different banks.  The A tiles are single-buffered: the transport of
+// stage u waits for the MMAs of stage u - 1 (a few hundred cycles, hidden behind the
+// staging wait).  Output: site-major FP16 [V][8][12], each thread writing two channels
+// of its site (96 contiguous bytes).
+template <int CIN>
+struct Pipe {
+  using S = Shape<CIN, 8>;
+  static constexpr int WORDS = CIN == 1 ? 16 : 24;  // 16-byte words per staging row (C_in = 1 padded)
+  static constexpr int ROWB = WORDS * 16;
+  static constexpr int STAGE_BYTES = kM * ROWB;
+  static constexpr int SMEM = S::B_ALL + S::A_BUF + 2 * STAGE_BYTES;
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+__device__ __forceinline__ uint32_t swz(int row, int word) { return (uint32_t)((word & ~7) | ((word & 7) ^ (row & 7))); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// the next stage's item of one thread: neighbour site, boundary factor, kind and the raw
+// 12-real link (rebuilt and daggered at transport time)
+struct HopRaw {
+  float4 l[3];
+  float f;
+  int kind;  // 0 site, 1 forward, 2 backward, -1 nothing (padding or a dead row)
+};
+
+__device__ __forceinline__ void hop_prefetch(const Geom& g, const float4* __restrict__ U32, const int x[4], int d,
+                                             HopRaw& h, size_t& sy) {
+  h.kind = d == 0 ? 0 : (d <= 4 ? 1 : 2);
+  const int mu = d == 0 ? 0 : (d - 1) & 3;
+  int y[4] = {x[0], x[1], x[2], x[3]};
+  h.f = 1.0f;
+  if (h.kind == 1) {
+    y[mu] = y[mu] + 1 == g.L[mu] ? 0 : y[mu] + 1;
+    if (mu == 3 && x[3] == g.L[3] - 1) h.f = (float)g.bc_t;
+    const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const float4* l = U32 + (size_t)((p * 4 + mu) * 3) * g.Vh + cb_index(g, x);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) h.l[k] = __ldg(l + (size_t)k * g.Vh);
+  } else if (h.kind == 2) {
+    y[mu] = y[mu] == 0 ? g.L[mu] - 1 : y[mu] - 1;
+    if (mu == 3 && x[3] == 0) h.f = (float)g.bc_t;
+    const int p = (y[0] + y[1] + y[2] + y[3]) & 1;
+    const float4* l = U32 + (size_t)((p * 4 + mu) * 3) * g.Vh + cb_index(g, y);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) h.l[k] = __ldg(l + (size_t)k * g.Vh);
+  }
+  sy = (size_t)lex_index(g, y);
+}
+
+__device__ __forceinline__ void site_coords(const Geom& g, int s, int x[4]) {
+  int r = s;
+  x[0] = r % g.L[0];
+  r /= g.L[0];
+  x[1] = r % g.L[1];
+  r /= g.L[1];
+  x[2] = r % g.L[2];
+  x[3] = r / g.L[2];
+}
+
+template <int CIN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_nn_layer_tc2(Geom g, const float4* __restrict__ U32, const __half* __restrict__ Bg, const __half2* __restrict__ in,
+                   __half2* __restrict__ out, int* __restrict__ err, const int* __restrict__ skip) {
+  using S = Shape<CIN, 8>;
+  using PP = Pipe<CIN>;
+  if (skip && *skip) return;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint32_t tmem_slot;
+  __shared__ __align__(8) uint64_t bar_w, bar_a;
+  unsigned char* sB = sm;
+  unsigned char* sA = sm + S::B_ALL;
+  unsigned char* sR = sm + S::B_ALL + S::A_BUF;  // two staging buffers
+  const int tid = threadIdx.x;
+  const int row = tid & (kM - 1);
+  const int part = tid >> 7;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_w)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_a)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(S::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar_w)), "r"(S::B_ALL)
+                 : "memory");
+    for (int st = 0; st < S::NST; ++st)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_addr(sB + st * S::B_ST)),
+          "l"(Bg + (size_t)st * (S::B_ST / 2)), "r"(S::B_ST), "r"(smem_addr(&bar_w))
+          : "memory");
+  }
+  bool fail = !mbar_wait(smem_addr(&bar_w), 0);
+  if (fail) atomicExch(err, 1);
+  bool aborted = __syncthreads_or(fail);
+
+  const int ntiles = (g.V + kM - 1) / kM;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nwork = my_tiles * S::NST;
+  const uint32_t id = idesc(kM, S::N);
+
+  // issue the copies (and link loads) of work item u into staging buffer u & 1
+  auto issue = [&](int u, HopRaw& h) {
+    h.kind = -1;
+    if (u >= nwork) return;
+    const int tile = blockIdx.x + (u / S::NST) * gridDim.x, st = u % S::NST;
+    const int s = tile * kM + row;
+    if (s >= g.V) return;
+    int x[4];
+    site_coords(g, s, x);
+    const int di = CIN == 1 ? 4 * st + part : st;
+    if (di >= 9) return;
+    size_t sy;
+    hop_prefetch(g, U32, x, dir_of(di), h, sy);
+    const uint32_t base = smem_addr(sR + (u & 1) * PP::STAGE_BYTES + row * PP::ROWB);
+    // C_in = 8: channels 2 part, 2 part + 1 (words 6 part .. + 5); C_in = 1: the part's
+    // direction slot (words 3 part .. + 2)
+    const int w0 = CIN == 1 ? 3 * part : 6 * part;
+    const int nw = CIN == 1 ? 3 : 6;
+    const uint4* src = reinterpret_cast<const uint4*>(in + sy * CIN * 12) + (CIN == 1 ? 0 : w0);
+#pragma unroll
+    for (int k = 0; k < nw; ++k) cp_async16(base + swz(row, w0 + k) * 16, src + k);
+  };
+
+  HopRaw cur, nxt;
+  if (!aborted) issue(0, cur);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  uint32_t commits = 0;  // MMA commits issued on bar_a
+  for (int u = 0; u < nwork && !aborted; ++u) {
+    const int tl = u / S::NST, st = u % S::NST;
+    const int tile = blockIdx.x + tl * gridDim.x;
+    issue(u + 1, nxt);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    // the MMAs of the previous stage read the A tiles: wait for them
+    fail = commits > 0 && !mbar_wait(smem_addr(&bar_a), (commits - 1) & 1);
+    if (fail) atomicExch(err, 2);
+    if (__syncthreads_or(fail)) {
+      aborted = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- transport the staged inputs into the three colour tiles
+    {
+      const unsigned char* R = sR + (u & 1) * PP::STAGE_BYTES + row * PP::ROWB;
+      Hop h;
+      h.kind = cur.kind < 0 ? 0 : cur.kind;
+      h.f = cur.f;
+      if (cur.kind > 0) {
+        Mat3<float> L;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          L.m[(2 * k) / 3][(2 * k) % 3] = mk(cur.l[k].x, cur.l[k].y);
+          L.m[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(cur.l[k].z, cur.l[k].w);
+        }
+        reconstruct_row2(L);
+        h.U = cur.kind == 1 ? L : dagger(L);
+      }
+      const bool live = cur.kind >= 0;
+      constexpr int NCH = CIN == 1 ? 1 : 2;
+#pragma unroll
+      for (int q = 0; q < NCH; ++q) {
+        const int w0 = CIN == 1 ? 3 * part : 6 * part + 3 * q;
+        cplx<float> v[4][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const uint4 w4 = live ? *reinterpret_cast<const uint4*>(R + swz(row, w0 + k) * 16) : make_uint4(0, 0, 0, 0);
+          const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float2 f = h2_to_f2(w[j]);
+            v[(4 * k + j) / 3][(4 * k + j) % 3] = mk(f.x, f.y);
+          }
+        }
+        const int col = CIN == 1 ? part * 8 : (2 * part + q) * 8;
+        store_channel<S::K>(h, v, live, sA, row, col, S::A_TILE);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int r = 0; r < 3; ++r) {
+        const uint32_t a0 = smem_addr(sA + r * S::A_TILE);
+        const uint32_t b0 = smem_addr(sB + st * S::B_ST);
+#pragma unroll 1
+        for (int kk = 0; kk < S::K / 16; ++kk)
+          mma_f16(tmem + r * S::N, sdesc(a0 + kk * 256, 128, S::SBO), sdesc(b0 + kk * 256, 128, S::SBO), id,
+                  (st > 0 || kk > 0) ? 1u : 0u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(&bar_a))
+                   : "memory");
+    }
+    ++commits;
+    cur = nxt;
+    if (st == S::NST - 1) {
+      // ---- epilogue of the tile: accumulators complete when the last commit arrived
+      fail = !mbar_wait(smem_addr(&bar_a), (commits - 1) & 1);
+      if (fail) atomicExch(err, 3);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (__syncthreads_or(fail)) {
+        aborted = true;
+        break;
+      }
+      // warp w: TMEM lanes 32 (w % 4) .. + 31 (sites), output channels 2 (w / 4), + 1
+      const int w = tid >> 5, qd = w & 3, grp = w >> 2;
+      const int srow = tile * kM + qd * 32 + (tid & 31);
+      float v[3][16];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + r * S::N + grp * 16, v[r]);
+      if (srow < g.V) {
+        uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)srow * 8 + 2 * grp) * 12);
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+          uint32_t hw[12];
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {  // complex k = spin a * 3 + colour r
+            const int a = k / 3, r = k % 3;
+            hw[k] = pack_h2(v[r][o * 8 + a * 2], v[r][o * 8 + a * 2 + 1]);
+          }
+#pragma unroll
+          for (int q = 0; q < 3; ++q) dst[o * 3 + q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+  }
+  // ---- teardown: no copy in flight, nothing of this CTA running on the tensor core
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (tid == 0 && commits > 0) mbar_wait(smem_addr(&bar_a), (commits - 1) & 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -578,11 +852,47 @@ static int layer_init() {
   return sms;
 }
 
+template <int CIN>
+static int layer2_init() {
+  static int sms = 0;
+  if (!sms) {
+    PFMP_CUDA(cudaFuncSetAttribute(tc::k_nn_layer_tc2<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   tc::Pipe<CIN>::SMEM));
+    int dev = 0;
+    PFMP_CUDA(cudaGetDevice(&dev));
+    PFMP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return sms;
+}
+
 // kernel attributes set outside any stream capture
 void nn_tc_init() {
   layer_init<1, 8, true>();
   layer_init<8, 8, true>();
   layer_init<8, 9, true>();
+  layer2_init<1>();
+  layer2_init<8>();
+}
+
+// the pipelined layers (C_out = 8); PFMP_NN_TC_PLAIN=1 in the environment selects the
+// original single-stage kernels (for comparison)
+static bool use_pipe() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("PFMP_NN_TC_PLAIN");
+    v = (e && e[0] == '1') ? 0 : 1;
+  }
+  return v == 1;
+}
+
+template <int CIN>
+static void layer2_t(pfmp_ctx* c, const void* Bp, const void* in, void* out, int* err, const int* skip) {
+  const int sms = layer2_init<CIN>();
+  const int ntiles = (c->g.V + tc::kM - 1) / tc::kM;
+  const int grid = ntiles < sms ? ntiles : sms;
+  tc::k_nn_layer_tc2<CIN><<<grid, tc::kThreads, tc::Pipe<CIN>::SMEM, c->stream>>>(
+      c->g, c->U32, (const __half*)Bp, (const __half2*)in, (__half2*)out, err, skip);
+  PFMP_CHECK_LAUNCH();
 }
 
 template <int CIN, int COUT, bool OUT16>
@@ -601,10 +911,16 @@ static void layer_t(pfmp_ctx* c, const void* Bp, const void* in, void* out, cons
 void nn_tc_layer(pfmp_ctx* c, int cin, int cout, bool last, const void* Bp, const void* in, void* out,
                  const float* sigma, int* err, const int* skip) {
   PFMP_REQUIRE(!last && cout == 8, PFMP_E_INVALID, "tensor-core layer sequence (the last layer: nn_tc_last)");
-  if (cin == 1)
+  if (use_pipe()) {
+    if (cin == 1)
+      layer2_t<1>(c, Bp, in, out, err, skip);
+    else
+      layer2_t<8>(c, Bp, in, out, err, skip);
+  } else if (cin == 1) {
     layer_t<1, 8, true>(c, Bp, in, out, sigma, err, skip);
-  else
+  } else {
     layer_t<8, 8, true>(c, Bp, in, out, sigma, err, skip);
+  }
 }
 
 // the last layer (8 -> 1) as local mixing on the tensor cores (z, FP16 [9][12][V]) and
