@@ -1097,7 +1097,7 @@ def roofline(capi, stream, l2_flush, reps=12):
     traffic = recorded_traffic()
     a16 = by16 / (ms16 * 1e-3) / 1e9
     h16 = {"bound": "hbm", "achieved": a16, "peak": hbm, "unit": "GB/s", "frac": a16 / hbm, "peak_source": src,
-           "kernel": "k_hop FP16 storage (FP32 arithmetic), 4 launches per K", "launches": n16,
+           "kernel": "k_hop FP16 storage (half2 projection and link multiply, FP32 sums), 4 launches per K", "launches": n16,
            "avg_us": ms16 * 1e3 / n16, "bytes_per_launch": by16 / n16,
            "k_time_ratio_f32_over_h16": (ms / n) / (ms16 / n16)}
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,

@@ -1,6 +1,8 @@
 // Clover term: field strength from the four plaquette leaves, the two chiral 6x6
 // blocks of A = 1 - kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}, and on odd sites
 // A^{-1} with log det A by Cholesky.  FP64 throughout; the FP32 copy is rounded last.
+// F_{mu nu} depends on the gauge field only: it is computed once per gauge-field version
+// (one thread per site and plane) and shared by every operator (kappa) of the context.
 //
 // In the chiral gamma basis sigma_{mu nu} = diag(s+, s-) with 2x2 Pauli blocks, so
 //   sum_{mu<nu} sigma F = sum_k s_k (x) X_k,
@@ -123,18 +125,57 @@ __device__ bool cholesky6(const cplx<double> A[6][6], cplx<double> L[6][6], doub
   return true;
 }
 
-__global__ void k_clover_build(Geom g, const double2* __restrict__ U, double kc, CloverOut out, ReduceBuf rb,
+// F_{mu nu} of every site and plane, one thread per (site, plane): the Hermitian matrix as
+// its three diagonal reals and the upper triangle (0,1), (0,2), (1,2), 9 reals per plane,
+// [2 parity][6 plane][9][Vh]
+__global__ void k_field_strength(Geom g, const double2* __restrict__ U, double* __restrict__ Fout) {
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y / 6, pl = blockIdx.y % 6;
+  if (cb >= g.Vh) return;
+  int x[4];
+  cb_coords(g, cb, p, x);
+  const int mu = pl < 3 ? 0 : (pl < 5 ? 1 : 2);
+  const int nu = pl < 3 ? pl + 1 : (pl < 5 ? pl - 1 : 3);
+  const Mat3<double> F = field_strength(U, g, x, mu, nu);
+  double* o = Fout + (size_t)((p * 6 + pl) * 9) * g.Vh + cb;
+  o[0] = F.m[0][0].re;
+  o[(size_t)g.Vh] = F.m[1][1].re;
+  o[2 * (size_t)g.Vh] = F.m[2][2].re;
+  o[3 * (size_t)g.Vh] = F.m[0][1].re;
+  o[4 * (size_t)g.Vh] = F.m[0][1].im;
+  o[5 * (size_t)g.Vh] = F.m[0][2].re;
+  o[6 * (size_t)g.Vh] = F.m[0][2].im;
+  o[7 * (size_t)g.Vh] = F.m[1][2].re;
+  o[8 * (size_t)g.Vh] = F.m[1][2].im;
+}
+
+__device__ __forceinline__ Mat3<double> load_fmunu(const double* __restrict__ Fin, const Geom& g, int p, int pl,
+                                                   int cb) {
+  const double* f = Fin + (size_t)((p * 6 + pl) * 9) * g.Vh + cb;
+  double v[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v[k] = __ldg(f + (size_t)k * g.Vh);
+  Mat3<double> F;
+  F.m[0][0] = mk(v[0], 0.0);
+  F.m[1][1] = mk(v[1], 0.0);
+  F.m[2][2] = mk(v[2], 0.0);
+  F.m[0][1] = mk(v[3], v[4]);
+  F.m[1][0] = mk(v[3], -v[4]);
+  F.m[0][2] = mk(v[5], v[6]);
+  F.m[2][0] = mk(v[5], -v[6]);
+  F.m[1][2] = mk(v[7], v[8]);
+  F.m[2][1] = mk(v[7], -v[8]);
+  return F;
+}
+
+__global__ void k_clover_build(Geom g, const double* __restrict__ Fin, double kc, CloverOut out, ReduceBuf rb,
                                double* logdet_out) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   double ld[1] = {0.0};
   if (cb < g.Vh) {
-    int x[4];
-    cb_coords(g, cb, p, x);
     Mat3<double> F[6];
-    int k = 0;
-    for (int mu = 0; mu < 4; ++mu)
-      for (int nu = mu + 1; nu < 4; ++nu) F[k++] = field_strength(U, g, x, mu, nu);
+    for (int k = 0; k < 6; ++k) F[k] = load_fmunu(Fin, g, p, k, cb);
     // F index: 0:(0,1) 1:(0,2) 2:(0,3) 3:(1,2) 4:(1,3) 5:(2,3)
     HermBlock<double> B[2];
     for (int blk = 0; blk < 2; ++blk) {
@@ -214,8 +255,18 @@ __global__ void k_clover_h16(const float4* __restrict__ src, uint4* __restrict__
   }
 }
 
+void field_strength_update(pfmp_ctx* c) {
+  if (c->fmunu_version == c->gauge_version && c->fmunu) return;
+  if (!c->fmunu) c->fmunu = (double*)dev_alloc((size_t)c->g.Vh * 2 * 6 * 9 * sizeof(double));
+  dim3 grid(nblocks(c->g.Vh, 128), 12);
+  k_field_strength<<<grid, 128, 0, c->stream>>>(c->g, c->U64, c->fmunu);
+  PFMP_CHECK_LAUNCH();
+  c->fmunu_version = c->gauge_version;
+}
+
 void clover_build(pfmp_op* op) {
   pfmp_ctx* c = op->ctx;
+  field_strength_update(c);
   CloverOut o;
   o.A64 = op->clov64[0];
   o.Ai64 = op->clov64[1];
@@ -226,7 +277,7 @@ void clover_build(pfmp_op* op) {
   o.bad = (int*)(c->d_sums + 8);
   PFMP_CUDA(cudaMemsetAsync(o.bad, 0, sizeof(int), c->stream));
   dim3 grid(nblocks(c->g.Vh, 128), 2);
-  k_clover_build<<<grid, 128, 0, c->stream>>>(c->g, c->U64, op->kappa * op->csw, o, c->rb, c->d_sums);
+  k_clover_build<<<grid, 128, 0, c->stream>>>(c->g, c->fmunu, op->kappa * op->csw, o, c->rb, c->d_sums);
   PFMP_CHECK_LAUNCH();
   PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, 9 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PFMP_CUDA(cudaStreamSynchronize(c->stream));

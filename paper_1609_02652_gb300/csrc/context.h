@@ -57,6 +57,8 @@ struct pfmp_ctx {
   double* h_sums = nullptr;  // pinned mirror [64]
   double* canon = nullptr;   // canonical full-lattice scratch (V*24 doubles)
   long gauge_version = 0;
+  double* fmunu = nullptr;   // clover field strength F_{mu nu}, [2][6][9][Vh] (built on demand)
+  long fmunu_version = -1;   // gauge_version it was computed for
 };
 
 struct pfmp_op {
@@ -117,6 +119,9 @@ void spinor_unpack(pfmp_ctx* c, double* dst_dev, const void* src, int prec, int 
 
 // clover.cu
 void clover_build(pfmp_op* op);
+// the field strength F_{mu nu} of the current gauge field in c->fmunu (computed once per
+// gauge-field version, shared by every operator of the context)
+void field_strength_update(pfmp_ctx* c);
 
 // profiling (core.cu): bracket one launch with events when profiling is on
 void prof_start(pfmp_ctx* c, cudaEvent_t* a);
@@ -145,8 +150,8 @@ void force_hop(pfmp_ctx* c, int prec, double* F, int pz, const void* Lf, const v
                const void* Rb, double coef);
 void clover_insert(pfmp_ctx* c, int prec, double* Hc, int p, const void* a, const void* b, double coef);
 void clover_insert_det(pfmp_op* op, double* Hc, double coef);
-void clover_force(pfmp_ctx* c, double* F, const double* Hc);
-void gauge_force(pfmp_ctx* c, double* F, double beta);
+void clover_force(pfmp_ctx* c, int prec, double* F, const double* Hc);
+void gauge_force(pfmp_ctx* c, int prec, double* F, double beta);
 void deriv_mhat(pfmp_op* op, int prec, double* F, double* Hc, const void* a, const void* b, double coef, void* y,
                 void* w);
 

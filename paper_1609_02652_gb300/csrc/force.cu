@@ -47,25 +47,42 @@ __device__ __forceinline__ void tr_lambda(const Mat3<T>& M, cplx<T> t[8]) {
 }
 
 // H = sum_a h_a T_a (Hermitian traceless)
-__device__ __forceinline__ Mat3<double> from_algebra(const double h[8]) {
-  Mat3<double> H;
+template <typename T>
+__device__ __forceinline__ Mat3<T> from_algebra(const double h[8]) {
+  Mat3<T> H;
   const double s = 0.5;
-  H.m[0][0] = mk(s * (h[2] + kInvSqrt3 * h[7]), 0.0);
-  H.m[1][1] = mk(s * (-h[2] + kInvSqrt3 * h[7]), 0.0);
-  H.m[2][2] = mk(s * (-2.0 * kInvSqrt3 * h[7]), 0.0);
-  H.m[0][1] = mk(s * h[0], -s * h[1]);
-  H.m[1][0] = mk(s * h[0], s * h[1]);
-  H.m[0][2] = mk(s * h[3], -s * h[4]);
-  H.m[2][0] = mk(s * h[3], s * h[4]);
-  H.m[1][2] = mk(s * h[5], -s * h[6]);
-  H.m[2][1] = mk(s * h[5], s * h[6]);
+  H.m[0][0] = mk<T>((T)(s * (h[2] + kInvSqrt3 * h[7])), 0);
+  H.m[1][1] = mk<T>((T)(s * (-h[2] + kInvSqrt3 * h[7])), 0);
+  H.m[2][2] = mk<T>((T)(s * (-2.0 * kInvSqrt3 * h[7])), 0);
+  H.m[0][1] = mk<T>((T)(s * h[0]), (T)(-s * h[1]));
+  H.m[1][0] = mk<T>((T)(s * h[0]), (T)(s * h[1]));
+  H.m[0][2] = mk<T>((T)(s * h[3]), (T)(-s * h[4]));
+  H.m[2][0] = mk<T>((T)(s * h[3]), (T)(s * h[4]));
+  H.m[1][2] = mk<T>((T)(s * h[5]), (T)(-s * h[6]));
+  H.m[2][1] = mk<T>((T)(s * h[5]), (T)(s * h[6]));
   return H;
 }
+
+// the link U_mu(x) at full coordinates: FP64 from the master field, FP32 from the
+// 12-real compressed copy (third row rebuilt)
+template <typename T>
+__device__ __forceinline__ Mat3<T> glink(const void* gauge, const Geom& g, const int x[4], int mu);
 
 __device__ __forceinline__ Mat3<double> mlink(const double2* U, const Geom& g, const int x[4], int mu) {
   const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
   Mat3<double> M;
   load_link18(M, U + (size_t)((p * 4 + mu) * 9) * g.Vh, cb_index(g, x), g.Vh);
+  return M;
+}
+template <>
+__device__ __forceinline__ Mat3<double> glink<double>(const void* gauge, const Geom& g, const int x[4], int mu) {
+  return mlink((const double2*)gauge, g, x, mu);
+}
+template <>
+__device__ __forceinline__ Mat3<float> glink<float>(const void* gauge, const Geom& g, const int x[4], int mu) {
+  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+  Mat3<float> M;
+  load_link(M, link_plane<PFMP_F32>((const float4*)gauge, p * 4 + mu, g.Vh), cb_index(g, x), g.Vh);
   return M;
 }
 __device__ __forceinline__ void shift(const Geom& g, const int x[4], int mu, int d, int y[4]) {
@@ -262,12 +279,13 @@ __global__ void k_clover_insert_det(double* Hc, Geom g, const double2* Ainv, dou
   }
 }
 
-__device__ __forceinline__ Mat3<double> load_H(const double* Hc, const Geom& g, const int x[4], int plane, double sgn) {
+template <typename T>
+__device__ __forceinline__ Mat3<T> load_H(const double* Hc, const Geom& g, const int x[4], int plane, double sgn) {
   const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
   const int cb = cb_index(g, x);
   double h[8];
   for (int a = 0; a < 8; ++a) h[a] = sgn * Hc[(size_t)((p * 6 + plane) * 8 + a) * g.Vh + cb];
-  return from_algebra(h);
+  return from_algebra<T>(h);
 }
 
 __device__ __forceinline__ int plane_index(int mu, int nu) {
@@ -286,14 +304,15 @@ __device__ __forceinline__ int plane_index(int mu, int nu) {
 // both summed Horner-fashion (U X from the left with the running prefix U V1 .. Vk,
 // Y U^dag from the right with the running suffix Wk .. W3 U^dag), which keeps three
 // 3x3 matrices live instead of a dozen.
-__global__ void k_clover_force(double* F, const double2* U64, const double* Hc, Geom g, int p) {
+template <typename T>
+__global__ void k_clover_force(double* F, const void* U64, const double* Hc, Geom g, int p) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   const int mu = blockIdx.y;
   if (cb >= g.Vh) return;
   int z[4];
   cb_coords(g, cb, p, z);
-  const Mat3<double> U = mlink(U64, g, z, mu);
-  Mat3<double> Zs = mat_zero<double>();
+  const Mat3<T> U = glink<T>(U64, g, z, mu);
+  Mat3<T> Zs = mat_zero<T>();
 #pragma unroll 1
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == mu) continue;
@@ -306,58 +325,59 @@ __global__ void k_clover_force(double* F, const double2* U64, const double* Hc, 
     shift(g, z, nu, -1, zmn);
     shift(g, zmn, mu, 1, zmnpm);
     // upper: R = sum over the four leaves, L = running prefix U V1 .. Vk
-    Mat3<double> L = U;
-    Mat3<double> R = matmul(L, load_H(Hc, g, zpm, pl, sg));
+    Mat3<T> L = U;
+    Mat3<T> R = matmul(L, load_H<T>(Hc, g, zpm, pl, sg));
     {
-      const Mat3<double> V1 = mlink(U64, g, zpm, nu);
+      const Mat3<T> V1 = glink<T>(U64, g, zpm, nu);
       L = matmul(L, V1);
-      R = mat_add(matmul(R, V1), matmul(L, load_H(Hc, g, zpmpn, pl, sg)));
+      R = mat_add(matmul(R, V1), matmul(L, load_H<T>(Hc, g, zpmpn, pl, sg)));
     }
     {
-      const Mat3<double> V2 = dagger(mlink(U64, g, zpn, mu));
+      const Mat3<T> V2 = dagger(glink<T>(U64, g, zpn, mu));
       L = matmul(L, V2);
-      R = mat_add(matmul(R, V2), matmul(L, load_H(Hc, g, zpn, pl, sg)));
+      R = mat_add(matmul(R, V2), matmul(L, load_H<T>(Hc, g, zpn, pl, sg)));
     }
     {
-      const Mat3<double> V3 = dagger(mlink(U64, g, z, nu));
+      const Mat3<T> V3 = dagger(glink<T>(U64, g, z, nu));
       L = matmul(L, V3);
-      R = mat_add(matmul(R, V3), matmul(L, load_H(Hc, g, z, pl, sg)));
+      R = mat_add(matmul(R, V3), matmul(L, load_H<T>(Hc, g, z, pl, sg)));
     }
     // lower: Q = sum over the four leaves, M = running suffix Wk .. W3 U^dag
-    Mat3<double> M = dagger(U);
-    Mat3<double> Q = matmul(load_H(Hc, g, zpm, pl, sg), M);
+    Mat3<T> M = dagger(U);
+    Mat3<T> Q = matmul(load_H<T>(Hc, g, zpm, pl, sg), M);
     {
-      const Mat3<double> W3 = mlink(U64, g, zmnpm, nu);
+      const Mat3<T> W3 = glink<T>(U64, g, zmnpm, nu);
       M = matmul(W3, M);
-      Q = mat_add(matmul(W3, Q), matmul(load_H(Hc, g, zmnpm, pl, sg), M));
+      Q = mat_add(matmul(W3, Q), matmul(load_H<T>(Hc, g, zmnpm, pl, sg), M));
     }
     {
-      const Mat3<double> W2 = mlink(U64, g, zmn, mu);
+      const Mat3<T> W2 = glink<T>(U64, g, zmn, mu);
       M = matmul(W2, M);
-      Q = mat_add(matmul(W2, Q), matmul(load_H(Hc, g, zmn, pl, sg), M));
+      Q = mat_add(matmul(W2, Q), matmul(load_H<T>(Hc, g, zmn, pl, sg), M));
     }
     {
-      const Mat3<double> W1 = dagger(mlink(U64, g, zmn, nu));
+      const Mat3<T> W1 = dagger(glink<T>(U64, g, zmn, nu));
       M = matmul(W1, M);
-      Q = mat_add(matmul(W1, Q), matmul(load_H(Hc, g, z, pl, sg), M));
+      Q = mat_add(matmul(W1, Q), matmul(load_H<T>(Hc, g, z, pl, sg), M));
     }
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) Zs.m[i][j] = Zs.m[i][j] + R.m[i][j] - Q.m[i][j];
   }
-  cplx<double> t[8];
+  cplx<T> t[8];
   tr_lambda(Zs, t);
   // (1/8) Re tr(T_a Z) = (1/16) Re tr(lambda_a Z)
-  for (int a = 0; a < 8; ++a) fptr(F, g, p, mu, a)[cb] += 0.0625 * t[a].re;
+  for (int a = 0; a < 8; ++a) fptr(F, g, p, mu, a)[cb] += 0.0625 * (double)t[a].re;
 }
 
 // F += (beta/3) Im tr(T_a U S) = (beta/6) Im tr(lambda_a U S)
-__global__ void k_gauge_force(double* F, const double2* U64, Geom g, int p, double beta) {
+template <typename T>
+__global__ void k_gauge_force(double* F, const void* U64, Geom g, int p, double beta) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   if (cb >= g.Vh) return;
   int z[4];
   cb_coords(g, cb, p, z);
   for (int mu = 0; mu < 4; ++mu) {
-    Mat3<double> S = mat_zero<double>();
+    Mat3<T> S = mat_zero<T>();
     int zpm[4];
     shift(g, z, mu, 1, zpm);
     for (int nu = 0; nu < 4; ++nu) {
@@ -367,14 +387,14 @@ __global__ void k_gauge_force(double* F, const double2* U64, Geom g, int p, doub
       shift(g, z, nu, -1, zmn);
       shift(g, zpm, nu, -1, zpmmn);
       // upper staple U_nu(z+mu) U_mu(z+nu)^dag U_nu(z)^dag
-      S = mat_add(S, matmul_nd(matmul_nd(mlink(U64, g, zpm, nu), mlink(U64, g, zpn, mu)), mlink(U64, g, z, nu)));
+      S = mat_add(S, matmul_nd(matmul_nd(glink<T>(U64, g, zpm, nu), glink<T>(U64, g, zpn, mu)), glink<T>(U64, g, z, nu)));
       // lower staple U_nu(z+mu-nu)^dag U_mu(z-nu)^dag U_nu(z-nu)
-      S = mat_add(S, matmul(matmul_dn(mlink(U64, g, zpmmn, nu), dagger(mlink(U64, g, zmn, mu))), mlink(U64, g, zmn, nu)));
+      S = mat_add(S, matmul(matmul_dn(glink<T>(U64, g, zpmmn, nu), dagger(glink<T>(U64, g, zmn, mu))), glink<T>(U64, g, zmn, nu)));
     }
-    const Mat3<double> US = matmul(mlink(U64, g, z, mu), S);
-    cplx<double> t[8];
+    const Mat3<T> US = matmul(glink<T>(U64, g, z, mu), S);
+    cplx<T> t[8];
     tr_lambda(US, t);
-    for (int a = 0; a < 8; ++a) fptr(F, g, p, mu, a)[cb] += beta / 6.0 * t[a].im;
+    for (int a = 0; a < 8; ++a) fptr(F, g, p, mu, a)[cb] += beta / 6.0 * (double)t[a].im;
   }
 }
 
@@ -403,16 +423,24 @@ void clover_insert_det(pfmp_op* op, double* Hc, double coef) {
   k_clover_insert_det<<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(Hc, c->g, op->clov64[1], coef);
   PFMP_CHECK_LAUNCH();
 }
-void clover_force(pfmp_ctx* c, double* F, const double* Hc) {
+// prec = PFMP_F64: FP64 arithmetic on the master links; PFMP_F32: FP32 arithmetic on the
+// compressed FP32 links (the forces of an MD with FP32 forces), FP64 accumulation
+void clover_force(pfmp_ctx* c, int prec, double* F, const double* Hc) {
   for (int p = 0; p < 2; ++p) {
     dim3 grid(nblocks(c->g.Vh, 64), 4);
-    k_clover_force<<<grid, 64, 0, c->stream>>>(F, c->U64, Hc, c->g, p);
+    if (prec == PFMP_F64)
+      k_clover_force<double><<<grid, 64, 0, c->stream>>>(F, c->U64, Hc, c->g, p);
+    else
+      k_clover_force<float><<<grid, 64, 0, c->stream>>>(F, c->U32, Hc, c->g, p);
     PFMP_CHECK_LAUNCH();
   }
 }
-void gauge_force(pfmp_ctx* c, double* F, double beta) {
+void gauge_force(pfmp_ctx* c, int prec, double* F, double beta) {
   for (int p = 0; p < 2; ++p) {
-    k_gauge_force<<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(F, c->U64, c->g, p, beta);
+    if (prec == PFMP_F64)
+      k_gauge_force<double><<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(F, c->U64, c->g, p, beta);
+    else
+      k_gauge_force<float><<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(F, c->U32, c->g, p, beta);
     PFMP_CHECK_LAUNCH();
   }
 }

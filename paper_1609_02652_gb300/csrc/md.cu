@@ -577,8 +577,9 @@ void action_force(pfmp_action* A, int i) {
   Term& T = A->t[i];
   pfmp_op* W = A->ops[T.d.a];
   A->force_evals++;
+  const int fprec = f32_forces(A) ? PFMP_F32 : PFMP_F64;
   if (T.d.kind == PFMP_KIND_GAUGE) {
-    gauge_force(c, A->F, A->def.beta);
+    gauge_force(c, fprec, A->F, A->def.beta);
     return;
   }
   const bool clover = A->def.csw != 0.0;
@@ -629,7 +630,7 @@ void action_force(pfmp_action* A, int i) {
     cg64(A, W, chi, phi);
     deriv_K(A, W, chi, chi, -1.0);
   }
-  if (clover) clover_force(c, A->F, A->Hc);
+  if (clover) clover_force(c, fprec, A->F, A->Hc);
 }
 
 void action_zero_force(pfmp_action* A) {

@@ -7,7 +7,8 @@
   oracle's FP64 forces.  Bars from the arithmetic: FP32 products carry ~1e-6 relative
   rounding (amplified ~1e2 by a 12-factor filter chain: 1e-4); a solve stopped at 1e-6
   leaves a solution error up to cond(K) x 1e-6 with cond(K) ~ 20 at kappa 0.12 here
-  (bar 5e-4).  The force of Q = P_64 / P_12 is the small remainder (4e-4 of the P_12
+  (bar 5e-4); the gauge and clover-determinant forces are products of a few FP32 links
+  (bar 1e-5).  The force of Q = P_64 / P_12 is the small remainder (4e-4 of the P_12
   force here) of 52 chain terms each ~1e4 times larger, so the FP32 rounding (6e-8) is
   amplified by that ratio (measured 2.5e-3 relative, 1e-6 of the P_12 force): bar 1e-2.
 * The config-1 trajectory (order-8 PF-MP, two-level 2MN 8 x 2, tau 0.5) with the mixed
@@ -98,8 +99,9 @@ def test_multishift_fp32(world, n):
 
 @pytest.mark.parametrize("kind,a,b,p1,p2,tol", [("filter", 1, 0, 0, 12, 1e-4), ("filter", 1, 0, 12, 64, 1e-2),
                                                ("filtercorr", 1, 0, 0, 8, 5e-4), ("ratio", 1, 0, 0, 0, 5e-4),
-                                               ("inv", 1, 0, 0, 0, 5e-4)],
-                         ids=["P12", "Q=P64/P12", "corr8", "ratio", "inv"])
+                                               ("inv", 1, 0, 0, 0, 5e-4), ("gauge", 0, 0, 0, 0, 1e-5),
+                                               ("det", 0, 0, 0, 0, 1e-5)],
+                         ids=["P12", "Q=P64/P12", "corr8", "ratio", "inv", "gauge", "det"])
 def test_fp32_forces(world, kind, a, b, p1, p2, tol):
     from oracle.action import Action, Term
 
@@ -109,10 +111,11 @@ def test_fp32_forces(world, kind, a, b, p1, p2, tol):
     A = capi.pfmp_action_create_def(g.ctx, _def(capi, [t], solver=1, force_prec=capi.PFMP_F32, md_tol=1e-6))
     try:
         phi = lat.even * torch.tensor(pin.spinor(DIMS, 61)).reshape(*lat.shape, 4, 3)
-        capi.pfmp_action_set_phi(A, 0, canon(phi))
+        if act.pf:
+            capi.pfmp_action_set_phi(A, 0, canon(phi))
         F = np.zeros(lat.V * 32)
         capi.pfmp_action_force(A, 0, F)
-        ref = act.F(U, 0, phi)
+        ref = act.F(U, 0, phi if act.pf else None)
         err = rel_l2(torch.tensor(F).reshape(*lat.shape, 4, 8), ref)
         assert err < tol, err
     finally:
