@@ -1035,7 +1035,7 @@ def kernel_source():
     """Bytes of the sources that define the FP32 stencil kernels (for the traffic record)."""
     csrc = os.path.join(ROOT, "paper_1609_02652_gb300", "csrc")
     return b"".join(open(os.path.join(csrc, f), "rb").read()
-                    for f in ("dslash.cu", "hop.cuh", "fields.cuh", "spin.cuh", "pfmp_internal.cuh"))
+                    for f in ("dslash_kernels.cuh", "hop.cuh", "fields.cuh", "spin.cuh", "pfmp_internal.cuh"))
 
 
 def recorded_traffic():
@@ -1152,10 +1152,11 @@ def kernel_only(dims, reps, prec="f32"):
     print(json.dumps({"kernel_only": list(dims), "reps": reps, "launches_per_rep": 4, "prec": prec}))
 
 
-def nn_only(reps):
+def nn_only(reps, timed=0):
     """Applications of a [1,8,8,8,1] network (weights pfmp_inputs.nn_weights(ch, 5)) on the
-    16^3x32 benchmark field through the tensor-core path (no timing): the case the ncu
-    captures of the network kernels run."""
+    16^3x32 benchmark field through the tensor-core path: the case the ncu captures of the
+    network kernels run; with timed > 0, that many more applications timed by CUDA events
+    on the default stream (not for runs under ncu)."""
     import torch
 
     import pfmp_inputs as pin
@@ -1175,9 +1176,18 @@ def nn_only(reps):
     for _ in range(reps):
         capi.pfmp_nn_apply(net, capi.PFMP_F32, o, a)
     torch.cuda.synchronize()
+    ms = None
+    if timed > 0:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(timed):
+            capi.pfmp_nn_apply(net, capi.PFMP_F32, o, a)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / timed
     capi.pfmp_nn_destroy(net)
     capi.pfmp_ctx_destroy(ctx)
-    print(json.dumps({"nn_only": list(DIMS), "reps": reps, "network": ch}))
+    print(json.dumps({"nn_only": list(DIMS), "reps": reps, "network": ch, "ms_per_application": ms}))
 
 
 def main():
@@ -1206,6 +1216,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=8, help="CG iterations per CUDA-graph chunk")
     ap.add_argument("--nn-only", action="store_true",
                     help="three applications of the [1,8,8,8,1] network at 16^3x32 (for ncu captures)")
+    ap.add_argument("--nn-timed", type=int, default=0, help="with --nn-only: applications timed by CUDA events")
     ap.add_argument("--kernel-prec", default="f32", choices=["f32", "h16", "f64", "df"])
     ap.add_argument("--kernel-only", action="store_true",
                     help="only apply K (FP32) --kernel-reps times on --kernel-dims: the small case for ncu")
@@ -1232,7 +1243,7 @@ def main():
         print(json.dumps(production_24x24x24x48(capi, stream, args.prod_traj, args.prod_therm)), flush=True)
         return
     if args.nn_only:
-        nn_only(3)
+        nn_only(3, args.nn_timed)
         return
     if args.kernel_only:
         kernel_only(tuple(int(v) for v in args.kernel_dims.split(",")), args.kernel_reps, args.kernel_prec)

@@ -28,8 +28,24 @@ __device__ __forceinline__ void shift(const Geom& g, const int x[4], int mu, int
   y[mu] = (y[mu] + d + g.L[mu]) % g.L[mu];
 }
 
+// the link U_mu(x): FP64 from the master field, FP32 from the 12-real compressed copy
+template <typename T>
+__device__ __forceinline__ Mat3<T> clink(const void* U, const Geom& g, const int x[4], int mu);
+template <>
+__device__ __forceinline__ Mat3<double> clink<double>(const void* U, const Geom& g, const int x[4], int mu) {
+  return mlink((const double2*)U, g, x, mu);
+}
+template <>
+__device__ __forceinline__ Mat3<float> clink<float>(const void* U, const Geom& g, const int x[4], int mu) {
+  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+  Mat3<float> M;
+  load_link(M, link_plane<PFMP_F32>((const float4*)U, p * 4 + mu, g.Vh), cb_index(g, x), g.Vh);
+  return M;
+}
+
 // F_{mu nu}(x): traceless part of (Q - Q^dag)/(8i), Q = sum of the four leaves at x
-__device__ Mat3<double> field_strength(const double2* U, const Geom& g, const int x[4], int mu, int nu) {
+template <typename T>
+__device__ Mat3<T> field_strength(const void* U, const Geom& g, const int x[4], int mu, int nu) {
   int xpm[4], xpn[4], xmm[4], xmn[4], xmmpn[4], xmmmn[4], xpmmn[4];
   shift(g, x, mu, 1, xpm);
   shift(g, x, nu, 1, xpn);
@@ -38,41 +54,41 @@ __device__ Mat3<double> field_strength(const double2* U, const Geom& g, const in
   shift(g, xmm, nu, 1, xmmpn);
   shift(g, xmm, nu, -1, xmmmn);
   shift(g, xpm, nu, -1, xpmmn);
-  const Mat3<double> Um = mlink(U, g, x, mu), Un = mlink(U, g, x, nu);
+  const Mat3<T> Um = clink<T>(U, g, x, mu), Un = clink<T>(U, g, x, nu);
   // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-  Mat3<double> Q = matmul_nd(matmul_nd(matmul(Um, mlink(U, g, xpm, nu)), mlink(U, g, xpn, mu)), Un);
+  Mat3<T> Q = matmul_nd(matmul_nd(matmul(Um, clink<T>(U, g, xpm, nu)), clink<T>(U, g, xpn, mu)), Un);
   // leaf 2: U_nu(x) U_mu(x-mu+nu)^dag U_nu(x-mu)^dag U_mu(x-mu)
-  const Mat3<double> Um_xmm = mlink(U, g, xmm, mu);
-  Mat3<double> L = matmul(matmul_nd(matmul_nd(Un, mlink(U, g, xmmpn, mu)), mlink(U, g, xmm, nu)), Um_xmm);
+  const Mat3<T> Um_xmm = clink<T>(U, g, xmm, mu);
+  Mat3<T> L = matmul(matmul_nd(matmul_nd(Un, clink<T>(U, g, xmmpn, mu)), clink<T>(U, g, xmm, nu)), Um_xmm);
   Q = mat_add(Q, L);
   // leaf 3: U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu)
   {
-    Mat3<double> A = dagger(Um_xmm);
-    A = matmul_nd(A, mlink(U, g, xmmmn, nu));
-    A = matmul(A, mlink(U, g, xmmmn, mu));
-    A = matmul(A, mlink(U, g, xmn, nu));
+    Mat3<T> A = dagger(Um_xmm);
+    A = matmul_nd(A, clink<T>(U, g, xmmmn, nu));
+    A = matmul(A, clink<T>(U, g, xmmmn, mu));
+    A = matmul(A, clink<T>(U, g, xmn, nu));
     L = A;
   }
   Q = mat_add(Q, L);
   // leaf 4: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x+mu-nu) U_mu(x)^dag
   {
-    Mat3<double> A = dagger(mlink(U, g, xmn, nu));
-    A = matmul(A, mlink(U, g, xmn, mu));
-    A = matmul(A, mlink(U, g, xpmmn, nu));
+    Mat3<T> A = dagger(clink<T>(U, g, xmn, nu));
+    A = matmul(A, clink<T>(U, g, xmn, mu));
+    A = matmul(A, clink<T>(U, g, xpmmn, nu));
     A = matmul_nd(A, Um);
     L = A;
   }
   Q = mat_add(Q, L);
-  Mat3<double> F;
+  Mat3<T> F;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      cplx<double> d = Q.m[i][j] - conj(Q.m[j][i]);
-      F.m[i][j] = 0.125 * times_mi(d);
+      cplx<T> d = Q.m[i][j] - conj(Q.m[j][i]);
+      F.m[i][j] = (T)0.125 * times_mi(d);
     }
-  const double tr = (F.m[0][0].re + F.m[1][1].re + F.m[2][2].re) / 3.0;
+  const T tr = (F.m[0][0].re + F.m[1][1].re + F.m[2][2].re) / (T)3;
   for (int i = 0; i < 3; ++i) {
     F.m[i][i].re -= tr;
-    F.m[i][i].im = 0.0;
+    F.m[i][i].im = 0;
   }
   return F;
 }
@@ -128,7 +144,8 @@ __device__ bool cholesky6(const cplx<double> A[6][6], cplx<double> L[6][6], doub
 // F_{mu nu} of every site and plane, one thread per (site, plane): the Hermitian matrix as
 // its three diagonal reals and the upper triangle (0,1), (0,2), (1,2), 9 reals per plane,
 // [2 parity][6 plane][9][Vh]
-__global__ void k_field_strength(Geom g, const double2* __restrict__ U, double* __restrict__ Fout) {
+template <typename T>
+__global__ void k_field_strength(Geom g, const void* __restrict__ U, double* __restrict__ Fout) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y / 6, pl = blockIdx.y % 6;
   if (cb >= g.Vh) return;
@@ -136,7 +153,7 @@ __global__ void k_field_strength(Geom g, const double2* __restrict__ U, double* 
   cb_coords(g, cb, p, x);
   const int mu = pl < 3 ? 0 : (pl < 5 ? 1 : 2);
   const int nu = pl < 3 ? pl + 1 : (pl < 5 ? pl - 1 : 3);
-  const Mat3<double> F = field_strength(U, g, x, mu, nu);
+  const Mat3<T> F = field_strength<T>(U, g, x, mu, nu);
   double* o = Fout + (size_t)((p * 6 + pl) * 9) * g.Vh + cb;
   o[0] = F.m[0][0].re;
   o[(size_t)g.Vh] = F.m[1][1].re;
@@ -255,18 +272,25 @@ __global__ void k_clover_h16(const float4* __restrict__ src, uint4* __restrict__
   }
 }
 
-void field_strength_update(pfmp_ctx* c) {
-  if (c->fmunu_version == c->gauge_version && c->fmunu) return;
+// prec = PFMP_F64: from the FP64 master links; PFMP_F32: FP32 arithmetic on the
+// compressed links (the clover terms an MD with FP32 forces uses between the trajectory
+// ends).  An FP64 result also serves an FP32 request.
+void field_strength_update(pfmp_ctx* c, int prec) {
+  if (c->fmunu && c->fmunu_version == c->gauge_version && (c->fmunu_prec == PFMP_F64 || prec == PFMP_F32)) return;
   if (!c->fmunu) c->fmunu = (double*)dev_alloc((size_t)c->g.Vh * 2 * 6 * 9 * sizeof(double));
   dim3 grid(nblocks(c->g.Vh, 128), 12);
-  k_field_strength<<<grid, 128, 0, c->stream>>>(c->g, c->U64, c->fmunu);
+  if (prec == PFMP_F64)
+    k_field_strength<double><<<grid, 128, 0, c->stream>>>(c->g, c->U64, c->fmunu);
+  else
+    k_field_strength<float><<<grid, 128, 0, c->stream>>>(c->g, c->U32, c->fmunu);
   PFMP_CHECK_LAUNCH();
   c->fmunu_version = c->gauge_version;
+  c->fmunu_prec = prec;
 }
 
-void clover_build(pfmp_op* op) {
+void clover_build(pfmp_op* op, int fprec) {
   pfmp_ctx* c = op->ctx;
-  field_strength_update(c);
+  field_strength_update(c, fprec);
   CloverOut o;
   o.A64 = op->clov64[0];
   o.Ai64 = op->clov64[1];
@@ -290,6 +314,7 @@ void clover_build(pfmp_op* op) {
     PFMP_CHECK_LAUNCH();
   }
   op->built_version = c->gauge_version;
+  op->built_prec = fprec;
 }
 
 }  // namespace pfmp

@@ -59,6 +59,7 @@ struct pfmp_ctx {
   long gauge_version = 0;
   double* fmunu = nullptr;   // clover field strength F_{mu nu}, [2][6][9][Vh] (built on demand)
   long fmunu_version = -1;   // gauge_version it was computed for
+  int fmunu_prec = PFMP_F64; // arithmetic it was computed in
 };
 
 struct pfmp_op {
@@ -73,6 +74,7 @@ struct pfmp_op {
   float4* kdf = nullptr;
   double logdet_oo = 0;
   long built_version = -1;
+  int built_prec = PFMP_F64;  // arithmetic of the field strength the clover blocks came from
   // workspace (odd temporaries and even scratch)
   double2* t64 = nullptr;
   float4* t32 = nullptr;
@@ -118,10 +120,11 @@ void spinor_pack(pfmp_ctx* c, void* dst, int prec, const double* src_dev, int pa
 void spinor_unpack(pfmp_ctx* c, double* dst_dev, const void* src, int prec, int parity);
 
 // clover.cu
-void clover_build(pfmp_op* op);
+// clover blocks from the field strength in FP64 (default) or FP32 arithmetic
+void clover_build(pfmp_op* op, int fprec = PFMP_F64);
 // the field strength F_{mu nu} of the current gauge field in c->fmunu (computed once per
-// gauge-field version, shared by every operator of the context)
-void field_strength_update(pfmp_ctx* c);
+// gauge-field version and precision, shared by every operator of the context)
+void field_strength_update(pfmp_ctx* c, int prec = PFMP_F64);
 
 // profiling (core.cu): bracket one launch with events when profiling is on
 void prof_start(pfmp_ctx* c, cudaEvent_t* a);

@@ -24,6 +24,9 @@
 #ifndef HOP_MINB_H16
 #define HOP_MINB_H16 7
 #endif
+#ifndef HOP_MINB_F64
+#define HOP_MINB_F64 1
+#endif
 
 namespace pfmp {
 
@@ -34,7 +37,7 @@ namespace pfmp {
 // double-float stencil 7-18% slower).
 template <int PREC>
 constexpr int hop_min_blocks() {
-  return PREC == PFMP_F32 ? HOP_MINB_F32 : PREC == PFMP_H16 ? HOP_MINB_H16 : 1;
+  return PREC == PFMP_F32 ? HOP_MINB_F32 : PREC == PFMP_H16 ? HOP_MINB_H16 : PREC == PFMP_F64 ? HOP_MINB_F64 : 1;
 }
 
 // Double-float arithmetic takes the rolled stencil: unrolled, its ~18k instructions per

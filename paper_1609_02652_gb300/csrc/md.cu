@@ -242,8 +242,10 @@ void deriv_K(pfmp_action* A, pfmp_op* op, const void* eta, const void* chi, doub
   deriv_mhat(op, prec, A->F, A->Hc, Meta, chi, coef, y, w);
 }
 
-void refresh_ops(pfmp_action* A) {
-  for (auto op : A->ops) clover_build(op);
+// clover terms of every operator after the gauge field changed; FP32 field strength
+// (fprec = PFMP_F32) for the link updates inside an MD with FP32 forces
+void refresh_ops(pfmp_action* A, int fprec = PFMP_F64) {
+  for (auto op : A->ops) clover_build(op, fprec);
 }
 
 long long kapply_total(pfmp_action* A) {
@@ -694,7 +696,7 @@ void link_update(pfmp_action* A, double eps) {
   k_link_update<<<grid, 128, 0, c->stream>>>(c->U64, A->mom, c->g, eps);
   PFMP_CHECK_LAUNCH();
   gauge_refresh_compressed(c);
-  refresh_ops(A);
+  refresh_ops(A, f32_forces(A) ? PFMP_F32 : PFMP_F64);
 }
 
 void mom_update(pfmp_action* A, double eps) {
@@ -721,6 +723,13 @@ void force_norms(pfmp_action* A, double* sum, double* mx) {
 // the MD part of a trajectory (Sec. 2.1, App. B): for each step of the merged schedule
 // T-hat, then P -= eps F_t for every term t on each level with a non-zero step, one term
 // at a time so that each term's force is measured (sums of the link averages into favg)
+// clover terms built from an FP32 field strength inside the MD are rebuilt in FP64
+static void fp64_clover(pfmp_action* A) {
+  bool f32 = false;
+  for (auto op : A->ops) f32 = f32 || op->built_prec != PFMP_F64;
+  if (f32) refresh_ops(A, PFMP_F64);
+}
+
 static double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -768,11 +777,12 @@ void action_md(pfmp_action* A, int len, const double* T, int nlev, const double*
   for (int t = 0; t < nt; ++t)
     PFMP_REQUIRE(term_level[t] >= -1 && term_level[t] < nlev, PFMP_E_INVALID, "term level out of range");
   bool stale = false;
-  for (auto op : A->ops) stale = stale || op->built_version != c->gauge_version;
+  for (auto op : A->ops) stale = stale || op->built_version != c->gauge_version || op->built_prec != PFMP_F64;
   if (stale) refresh_ops(A);
   alg_pack(c, A->mom, mom, where);
   pfmp_traj_info scratch{};
   md_steps(A, len, T, nlev, S, term_level, &scratch);
+  fp64_clover(A);
   alg_unpack(c, mom, where, A->mom);
   PFMP_CUDA(cudaStreamSynchronize(c->stream));
 }
@@ -791,7 +801,7 @@ void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double
   A->force_evals = 0;
   PFMP_CUDA(cudaMemcpyAsync(A->U0, c->U64, (size_t)g.Vh * 72 * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
   bool stale = false;
-  for (auto op : A->ops) stale = stale || op->built_version != c->gauge_version;
+  for (auto op : A->ops) stale = stale || op->built_version != c->gauge_version || op->built_prec != PFMP_F64;
   if (stale) refresh_ops(A);
   alg_pack(c, A->mom, mom, where);
   std::vector<double> S0(nt, 0.0), S1(nt, 0.0);
@@ -809,6 +819,7 @@ void trajectory(pfmp_action* A, int len, const double* T, int nlev, const double
     for (int t = 0; t < nt; ++t)
       if (term_level[t] >= 0) H0 += (S0[t] = action_term(A, t));
     md_steps(A, len, T, nlev, S, term_level, info);
+    fp64_clover(A);  // the final Hamiltonian with FP64 clover terms
     H1 = kinetic(A);
     for (int t = 0; t < nt; ++t)
       if (term_level[t] >= 0) H1 += (S1[t] = action_term(A, t));

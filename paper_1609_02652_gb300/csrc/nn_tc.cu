@@ -198,21 +198,18 @@ __device__ __forceinline__ void make_hop(const Geom& g, const float4* __restrict
   h.sy = (size_t)lex_index(g, y);
 }
 
-// site-major activations act[site][C][12] (half2 complex, 48 C bytes per site): the 12
-// components of channel ic at site sy as three 16-byte words
+// channel-major activations act[C][12][V] (half2 complex): component k of channel ic at
+// site sy; the threads of a warp (consecutive sites) read consecutive words
 template <int C>
-__device__ __forceinline__ void load_channel(const __half2* __restrict__ in, size_t sy, int ic, cplx<float> v[4][3]) {
-  const uint4* p = reinterpret_cast<const uint4*>(in + (sy * C + ic) * 12);
+__device__ __forceinline__ void load_channel(const __half2* __restrict__ in, size_t V, size_t sy, int ic,
+                                             cplx<float> v[4][3]) {
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const uint4 w4 = __ldg(p + q);
-    const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+  for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float2 f = h2_to_f2(w[j]);
-      v[(4 * q + j) / 3][(4 * q + j) % 3] = mk(f.x, f.y);
+    for (int c = 0; c < 3; ++c) {
+      const float2 w = __half22float2(__ldg(in + ((size_t)ic * 12 + sp * 3 + c) * V + sy));
+      v[sp][c] = mk(w.x, w.y);
     }
-  }
 }
 
 // transport one channel and store it (FP16) at column col of the three colour tiles
@@ -265,7 +262,7 @@ __device__ __forceinline__ void gather_stage(const Geom& g, const float4* __rest
     cplx<float> v[4][3];
     if (on) {
       make_hop(g, U32, x, dir_of(di), h);
-      load_channel<1>(in, h.sy, 0, v);
+      load_channel<1>(in, V, h.sy, 0, v);
     }
     store_channel<K>(h, v, on, A, row, part * 8, a_tile);
   } else {
@@ -274,8 +271,8 @@ __device__ __forceinline__ void gather_stage(const Geom& g, const float4* __rest
     const int ic0 = part, ic1 = part + 4;
     if (live) {
       make_hop(g, U32, x, dir_of(st), h);
-      load_channel<8>(in, h.sy, ic0, v0);
-      load_channel<8>(in, h.sy, ic1, v1);
+      load_channel<8>(in, V, h.sy, ic0, v0);
+      load_channel<8>(in, V, h.sy, ic1, v1);
     }
     store_channel<K>(h, v0, live, A, row, ic0 * 8, a_tile);
     store_channel<K>(h, v1, live, A, row, ic1 * 8, a_tile);
@@ -283,7 +280,7 @@ __device__ __forceinline__ void gather_stage(const Geom& g, const float4* __rest
 }
 
 // network input: sigma * (even FP32 field [6][Vh] float4) on even sites, 0 on odd sites,
-// as FP16 complex [V][12] (lexicographic sites, site-major)
+// as FP16 complex [12][V] (lexicographic sites)
 // rr (optional): |src|^2 already known to the caller (FGCR's residual norm); sigma is then
 // computed here, stored for the later kernels, and no separate reduction is needed
 __global__ void k_embed16(Geom g, const float4* __restrict__ src, float* __restrict__ sigma_p,
@@ -306,16 +303,12 @@ __global__ void k_embed16(Geom g, const float4* __restrict__ src, float* __restr
   const bool even = ((x[0] + x[1] + x[2] + x[3]) & 1) == 0;
   const float sg = rr ? (*rr > 0 ? (float)sqrt(24.0 * g.Vh / *rr) : 1.0f) : *sigma_p;
   const int cb = s >> 1;
-  uint32_t w[12];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     float4 v = even ? src[(size_t)k * g.Vh + cb] : make_float4(0.f, 0.f, 0.f, 0.f);
-    w[2 * k] = pack_h2(sg * v.x, sg * v.y);
-    w[2 * k + 1] = pack_h2(sg * v.z, sg * v.w);
+    dst[(size_t)(2 * k) * g.V + s] = __floats2half2_rn(sg * v.x, sg * v.y);
+    dst[(size_t)(2 * k + 1) * g.V + s] = __floats2half2_rn(sg * v.z, sg * v.w);
   }
-  uint4* d = reinterpret_cast<uint4*>(dst + (size_t)s * 12);
-#pragma unroll
-  for (int q = 0; q < 3; ++q) d[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
 }
 
 // last layer, second half: out(x) = sum_d U_d(x) z_d(x + d) on even sites (the only ones
@@ -512,10 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int r = col / S::N, n = col % S::N;
             const int o = n >> 3, a = (n >> 1) & 3;
             if (o < COUT) {
-              // COUT = 8: site-major activations [V][8][12]; the local mixing (COUT = 9)
-              // writes z as [9][12][V] for k_last_stencil
-              const size_t idx = S::LOCAL ? ((size_t)o * 12 + a * 3 + r) * V + srow
-                                          : ((size_t)srow * COUT + o) * 12 + a * 3 + r;
+              const size_t idx = ((size_t)o * 12 + a * 3 + r) * V + srow;
               if (OUT16)
                 reinterpret_cast<__half2*>(out)[idx] = __floats2half2_rn(v[j], v[j + 1]);
               else
@@ -540,32 +530,28 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---------------------------------------------------------------- pipelined layer (C_out = 8)
-// The same contraction with the gather split in two: raw neighbour activations go
-// global -> shared by 16-byte cp.async copies (no registers held, so many bytes are in
-// flight), one stage ahead of the stage being transported; the links of the next stage
-// are prefetched into registers.  Per stage: issue the copies of stage u + 1, wait for
-// those of stage u, transport them from the staging buffer into the FP16 A tiles, one
-// thread issues the MMAs.  Staging rows are XOR-swizzled in 8-word groups (16-byte word j
-// of row r stored at j ^ (r & 7) within its group) so that the threads of a warp, one
-// row each, read different banks.  The A tiles are single-buffered: the transport of
-// stage u waits for the MMAs of stage u - 1 (a few hundred cycles, hidden behind the
-// staging wait).  Output: site-major FP16 [V][8][12], each thread writing two channels
-// of its site (96 contiguous bytes).
+// The same contraction with the gather split in two: the raw neighbour activations go
+// global -> shared by 4-byte cp.async copies (no registers held; the threads of a warp,
+// consecutive sites, copy consecutive words), one stage ahead of the stage being
+// transported; the links of the next stage are prefetched into registers.  Per stage:
+// issue the copies of stage u + 1, wait for those of stage u, transport them from the
+// staging buffer into the FP16 A tiles, one thread issues the MMAs.  Staging layout
+// [slot][component][row] (slot: the input channel, or for C_in = 1 the direction of the
+// stage), so the warp's reads in the transport are conflict-free.  The A tiles are
+// single-buffered: the transport of stage u waits for the MMAs of stage u - 1.
 template <int CIN>
 struct Pipe {
   using S = Shape<CIN, 8>;
-  static constexpr int WORDS = CIN == 1 ? 16 : 24;  // 16-byte words per staging row (C_in = 1 padded)
-  static constexpr int ROWB = WORDS * 16;
-  static constexpr int STAGE_BYTES = kM * ROWB;
+  static constexpr int SLOTS = CIN == 1 ? 4 : 8;
+  static constexpr int STAGE_BYTES = SLOTS * 12 * kM * 4;
   static constexpr int SMEM = S::B_ALL + S::A_BUF + 2 * STAGE_BYTES;
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-__device__ __forceinline__ uint32_t swz(int row, int word) { return (uint32_t)((word & ~7) | ((word & 7) ^ (row & 7))); }
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
 }
+
 
 // the next stage's item of one thread: neighbour site, boundary factor, kind and the raw
 // 12-real link (rebuilt and daggered at transport time)
@@ -672,14 +658,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (di >= 9) return;
     size_t sy;
     hop_prefetch(g, U32, x, dir_of(di), h, sy);
-    const uint32_t base = smem_addr(sR + (u & 1) * PP::STAGE_BYTES + row * PP::ROWB);
-    // C_in = 8: channels 2 part, 2 part + 1 (words 6 part .. + 5); C_in = 1: the part's
-    // direction slot (words 3 part .. + 2)
-    const int w0 = CIN == 1 ? 3 * part : 6 * part;
-    const int nw = CIN == 1 ? 3 : 6;
-    const uint4* src = reinterpret_cast<const uint4*>(in + sy * CIN * 12) + (CIN == 1 ? 0 : w0);
+    const uint32_t base = smem_addr(sR + (u & 1) * PP::STAGE_BYTES) + row * 4;
+    const size_t V = (size_t)g.V;
+    // C_in = 8: channels 2 part, 2 part + 1; C_in = 1: the part's direction slot
 #pragma unroll
-    for (int k = 0; k < nw; ++k) cp_async16(base + swz(row, w0 + k) * 16, src + k);
+    for (int q = 0; q < (CIN == 1 ? 1 : 2); ++q) {
+      const int ic = CIN == 1 ? 0 : 2 * part + q;
+      const int slot = CIN == 1 ? part : ic;
+#pragma unroll
+      for (int k = 0; k < 12; ++k)
+        cp_async4(base + (uint32_t)((slot * 12 + k) * kM) * 4, in + ((size_t)ic * 12 + k) * V + sy);
+    }
   };
 
   HopRaw cur, nxt;
@@ -702,7 +691,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // ---- transport the staged inputs into the three colour tiles
     {
-      const unsigned char* R = sR + (u & 1) * PP::STAGE_BYTES + row * PP::ROWB;
+      const uint32_t* R = reinterpret_cast<const uint32_t*>(sR + (u & 1) * PP::STAGE_BYTES) + row;
       Hop h;
       h.kind = cur.kind < 0 ? 0 : cur.kind;
       h.f = cur.f;
@@ -720,17 +709,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       constexpr int NCH = CIN == 1 ? 1 : 2;
 #pragma unroll
       for (int q = 0; q < NCH; ++q) {
-        const int w0 = CIN == 1 ? 3 * part : 6 * part + 3 * q;
+        const int slot = CIN == 1 ? part : 2 * part + q;
         cplx<float> v[4][3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const uint4 w4 = live ? *reinterpret_cast<const uint4*>(R + swz(row, w0 + k) * 16) : make_uint4(0, 0, 0, 0);
-          const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float2 f = h2_to_f2(w[j]);
-            v[(4 * k + j) / 3][(4 * k + j) % 3] = mk(f.x, f.y);
-          }
+        for (int k = 0; k < 12; ++k) {
+          const float2 f = live ? h2_to_f2(R[(slot * 12 + k) * kM]) : make_float2(0.f, 0.f);
+          v[k / 3][k % 3] = mk(f.x, f.y);
         }
         const int col = CIN == 1 ? part * 8 : (2 * part + q) * 8;
         store_channel<S::K>(h, v, live, sA, row, col, S::A_TILE);
@@ -765,25 +749,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         aborted = true;
         break;
       }
-      // warp w: TMEM lanes 32 (w % 4) .. + 31 (sites), output channels 2 (w / 4), + 1
+      // warp w: TMEM lanes 32 (w % 4) .. + 31 (sites), output channels 2 (w / 4), + 1;
+      // channel-major output [8][12][V]: consecutive lanes write consecutive sites
       const int w = tid >> 5, qd = w & 3, grp = w >> 2;
       const int srow = tile * kM + qd * 32 + (tid & 31);
+      const size_t V = (size_t)g.V;
       float v[3][16];
 #pragma unroll
       for (int r = 0; r < 3; ++r) tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + r * S::N + grp * 16, v[r]);
       if (srow < g.V) {
-        uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)srow * 8 + 2 * grp) * 12);
 #pragma unroll
-        for (int o = 0; o < 2; ++o) {
-          uint32_t hw[12];
+        for (int o = 0; o < 2; ++o)
 #pragma unroll
           for (int k = 0; k < 12; ++k) {  // complex k = spin a * 3 + colour r
             const int a = k / 3, r = k % 3;
-            hw[k] = pack_h2(v[r][o * 8 + a * 2], v[r][o * 8 + a * 2 + 1]);
+            out[((size_t)(2 * grp + o) * 12 + k) * V + srow] =
+                __floats2half2_rn(v[r][o * 8 + a * 2], v[r][o * 8 + a * 2 + 1]);
           }
-#pragma unroll
-          for (int q = 0; q < 3; ++q) dst[o * 3 + q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
-        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
