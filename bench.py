@@ -1090,6 +1090,27 @@ def roofline(capi, stream, l2_flush, reps=12):
         l2_flush()
         capi.pfmp_kop(op, capi.PFMP_H16, oh, ah)
     n16, ms16, by16 = capi.pfmp_profile_end(ctx, capi.PFMP_KERNEL_HOP_H16)
+    # the solves on the same 32^3x64 system, where the stencil is HBM-bound: mixed CG on
+    # the FP32 stencil and on FP16 storage, the FP64 CG (a Gaussian rhs, 1e-10, L2 flushed)
+    n64 = capi.pfmp_spinor_bytes(ctx, capi.PFMP_F64) // 8
+    bcan = torch.tensor(np.ascontiguousarray(pin.spinor(ROOF_DIMS, RHS_SEED)).view(np.float64).reshape(-1), device="cuda")
+    b = torch.zeros(n64, dtype=torch.float64, device="cuda")
+    capi.pfmp_spinor_pack(ctx, b, capi.PFMP_F64, bcan, capi.PFMP_DEVICE, 0)
+    del bcan
+    x = torch.zeros_like(b)
+    solves = {}
+    for name, method, delta in (("mixed_cg", capi.PFMP_SOLVER_CG_MIXED, 1e-4), ("half_cg", capi.PFMP_SOLVER_CG_HALF, 0.03),
+                                ("fp64_cg", capi.PFMP_SOLVER_CG64, 0.1)):
+        prm = capi.SolverParams(method=method, tol=TOL, max_iter=20000, delta=delta, check_every=8)
+        capi.pfmp_solve(op, prm, x, b)
+        l2_flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = capi.pfmp_solve(op, prm, x, b)
+        e1.record(stream)
+        e1.synchronize()
+        solves[name] = {"ms": e0.elapsed_time(e1), "iterations": info.iters, "true_rel_res": info.true_rel_res}
+    solves["speedup_half_vs_mixed"] = solves["mixed_cg"]["ms"] / solves["half_cg"]["ms"]
     capi.pfmp_op_destroy(op)
     capi.pfmp_ctx_destroy(ctx)
     hbm, src = peaks()
@@ -1099,7 +1120,7 @@ def roofline(capi, stream, l2_flush, reps=12):
     h16 = {"bound": "hbm", "achieved": a16, "peak": hbm, "unit": "GB/s", "frac": a16 / hbm, "peak_source": src,
            "kernel": "k_hop FP16 storage (half2 projection and link multiply, FP32 sums), 4 launches per K", "launches": n16,
            "avg_us": ms16 * 1e3 / n16, "bytes_per_launch": by16 / n16,
-           "k_time_ratio_f32_over_h16": (ms / n) / (ms16 / n16)}
+           "k_time_ratio_f32_over_h16": (ms / n) / (ms16 / n16), "solves_32x32x32x64": solves}
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": traffic, "peak_source": src,
             "kernel": "k_hop FP32 (Wilson hop + fused clover epilogues), 4 launches per K",

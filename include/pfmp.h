@@ -83,8 +83,9 @@ int64_t pfmp_launch_count(void);
 /* ---- context: lattice geometry, stream, gauge field ---------------------------------
  * pfmp_ctx_create: dims = {Lx, Ly, Lz, Lt} (all even, >= 2); bc_t = +1 or -1 is the
  * fermion time boundary factor; stream is a cudaStream_t (NULL: the legacy default
- * stream) borrowed, not owned.  Allocates the gauge field (FP64 master copy plus FP64
- * and FP32 12-real compressed copies) and reduction scratch on the current device.
+ * stream) borrowed, not owned.  Allocates the gauge field (FP64 master copy, read in full
+ * by the FP64 stencil, plus FP32, FP16 and double-float copies, the FP32 and FP16 ones
+ * 12-real) and reduction scratch on the current device.
  * Errors: PFMP_E_INVALID (odd or non-positive extent, |bc_t| != 1), PFMP_E_NOMEM.   */
 int pfmp_ctx_create(pfmp_ctx** ctx, const int dims[4], int bc_t, void* stream);
 int pfmp_ctx_destroy(pfmp_ctx* ctx);
@@ -95,8 +96,8 @@ int64_t pfmp_half_volume(const pfmp_ctx* ctx);
 int64_t pfmp_spinor_bytes(const pfmp_ctx* ctx, int prec);
 
 /* Gauge field in the canonical layout ([V][4][3][3] complex double), from host or
- * device memory (where = PFMP_HOST / PFMP_DEVICE).  Links must be SU(3): the
- * compressed copies keep two rows and rebuild the third as conj(row0 x row1).
+ * device memory (where = PFMP_HOST / PFMP_DEVICE).  Links must be SU(3): the 12-real
+ * FP32 and FP16 copies keep two rows and rebuild the third as conj(row0 x row1).
  * Setting the gauge field invalidates every operator's clover term until
  * pfmp_op_update().                                                                  */
 int pfmp_gauge_set(pfmp_ctx* ctx, const double* U, int where);

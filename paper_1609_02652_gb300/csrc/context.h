@@ -48,7 +48,6 @@ struct pfmp_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
   double2* U64 = nullptr;    // master [2][4][9][Vh]
-  double2* U64c = nullptr;   // compressed [2][4][6][Vh]
   float4* U32 = nullptr;     // compressed [2][4][3][Vh]
   float4* Udf = nullptr;     // double-float full links [2][4][9][Vh] (complex as hi/lo pairs)
   uint4* U16 = nullptr;      // FP16 compressed, 24 bytes per link (planes: see link_plane)

@@ -77,16 +77,14 @@ __global__ void k_gauge_to_canonical(Geom g, const double2* __restrict__ U, doub
   }
 }
 
-__global__ void k_gauge_compress(Geom g, const double2* __restrict__ U, double2* __restrict__ U64c,
-                                 float4* __restrict__ U32, float4* __restrict__ Udf, uint4* __restrict__ U16) {
+__global__ void k_gauge_compress(Geom g, const double2* __restrict__ U, float4* __restrict__ U32,
+                                 float4* __restrict__ Udf, uint4* __restrict__ U16) {
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
   const int pm = blockIdx.y;  // parity*4 + mu
   if (cb >= g.Vh) return;
   const double2* src = U + (size_t)(pm * 9) * g.Vh;
   double2 v[6];
   for (int k = 0; k < 6; ++k) v[k] = src[(size_t)k * g.Vh + cb];
-  double2* d64 = U64c + (size_t)(pm * 6) * g.Vh;
-  for (int k = 0; k < 6; ++k) d64[(size_t)k * g.Vh + cb] = v[k];
   float4* ddf = Udf + (size_t)(pm * 9) * g.Vh;
   for (int k = 0; k < 9; ++k) ddf[(size_t)k * g.Vh + cb] = split2(src[(size_t)k * g.Vh + cb]);
   float4* d32 = U32 + (size_t)(pm * 3) * g.Vh;
@@ -177,7 +175,7 @@ static double* canon_scratch(pfmp_ctx* c, size_t doubles) {
 
 void gauge_refresh_compressed(pfmp_ctx* c) {
   dim3 grid(nblocks(c->g.Vh), 8);
-  k_gauge_compress<<<grid, kBlock, 0, c->stream>>>(c->g, c->U64, c->U64c, c->U32, c->Udf, c->U16);
+  k_gauge_compress<<<grid, kBlock, 0, c->stream>>>(c->g, c->U64, c->U32, c->Udf, c->U16);
   PFMP_CHECK_LAUNCH();
   c->gauge_version++;
 }
@@ -215,7 +213,6 @@ pfmp_ctx* ctx_create(const int dims[4], int bc_t, void* stream) {
     c->stream = (cudaStream_t)stream;
     PFMP_CUDA(cudaGetDevice(&c->device));
     c->U64 = (double2*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 9 * sizeof(double2));
-    c->U64c = (double2*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 6 * sizeof(double2));
     c->U32 = (float4*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 3 * sizeof(float4));
     c->Udf = (float4*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 9 * sizeof(float4));
     c->U16 = (uint4*)dev_alloc((size_t)c->g.Vh * 2 * 4 * 24);
@@ -226,7 +223,6 @@ pfmp_ctx* ctx_create(const int dims[4], int bc_t, void* stream) {
     PFMP_CUDA(cudaMallocHost(&c->h_sums, 64 * sizeof(double)));
   } catch (...) {
     dev_free(c->U64);
-    dev_free(c->U64c);
     dev_free(c->U32);
     dev_free(c->Udf);
     dev_free(c->U16);
@@ -292,7 +288,6 @@ void ctx_destroy(pfmp_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   dev_free(c->U64);
-  dev_free(c->U64c);
   dev_free(c->U32);
   dev_free(c->Udf);
   dev_free(c->U16);

@@ -85,7 +85,7 @@ HopParams<PREC> params(pfmp_op* op, int p, void* out, const void* in) {
   a.p = p;
   a.out = (vec*)out;
   a.in = (const vec*)in;
-  a.gauge = PREC == PFMP_F64   ? (const vec*)(const void*)op->ctx->U64c
+  a.gauge = PREC == PFMP_F64   ? (const vec*)(const void*)op->ctx->U64
             : PREC == PREC_DF  ? (const vec*)(const void*)op->ctx->Udf
             : PREC == PFMP_H16 ? (const vec*)(const void*)op->ctx->U16
                                : (const vec*)(const void*)op->ctx->U32;
@@ -107,7 +107,7 @@ double hop_bytes(int epi, int Vh) {
     const double b = 8 * 12 * 2 + 52 + 52 + (epi >= EPI_CLOV ? 72 * 2 : 0) + (epi == EPI_XPAY ? 52 : 0);
     return b * (double)Vh;
   }
-  const double link = PREC == PREC_DF ? 18 : 12;
+  const double link = (PREC == PREC_DF || PREC == PFMP_F64) ? 18 : 12;
   const double reals = 8 * link + 24 + 24 + (epi >= EPI_CLOV ? 72 : 0) + (epi == EPI_XPAY ? 24 : 0);
   return reals * (PREC == PFMP_F32 ? 4 : 8) * (double)Vh;
 }

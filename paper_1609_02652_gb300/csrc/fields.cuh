@@ -14,7 +14,7 @@ struct Prec<PFMP_F64> {
   using real = double;
   using vec = double2;
   static constexpr int spinor_vecs = 12;
-  static constexpr int link_vecs = 6;  // 12 reals
+  static constexpr int link_vecs = 9;  // 18 reals (the master field)
   static constexpr int clover_vecs = 36;
 };
 template <>
@@ -109,15 +109,17 @@ __device__ __forceinline__ void store_spinor(uint4* __restrict__ f, const Spinor
   reinterpret_cast<float*>(f + (size_t)3 * Vh)[cb] = m;
 }
 
-// ---------------------------------------------------------------- links (12-real)
-// link field of one (parity, mu): base pointer at [parity][mu], vectors strided by Vh
+// ---------------------------------------------------------------- links
+// link field of one (parity, mu): base pointer at [parity][mu], vectors strided by Vh.
+// FP64: the full 18-real link of the master field (the FP64 stencil is bound by the FP64
+// pipe, not by bytes, so it reads the third row instead of rebuilding it); FP32 and FP16:
+// 12 reals, the third row rebuilt as conj(row0 x row1)
 __device__ __forceinline__ void load_link(Mat3<double>& U, const double2* __restrict__ f, int cb, int Vh) {
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 9; ++k) {
     double2 v = __ldg(f + (size_t)k * Vh + cb);
     U.m[k / 3][k % 3] = mk(v.x, v.y);
   }
-  reconstruct_row2(U);
 }
 __device__ __forceinline__ void load_link(Mat3<float>& U, const float4* __restrict__ f, int cb, int Vh) {
 #pragma unroll

@@ -134,3 +134,36 @@ def test_fgcr_falls_back_to_cg():
     finally:
         capi.pfmp_nn_destroy(nn)
         g.close()
+
+
+def test_fma_rate_probe_and_trajectory_timings():
+    """pfmp_fma_rate measures the FP64 and FP32 FMA pipes (an FP32 rate many times the
+    FP64 rate on this part); a trajectory reports positive wall times per term's forces and
+    for the link updates, which add up to no more than the whole call."""
+    from oracle.integrator import LAMBDA_2MN
+    from paper_1609_02652_gb300 import capi
+
+    lat, U = oracle_gauge(DIMS, 0.3, 1)
+    g = Gpu(lat, U)
+    try:
+        r64 = capi.pfmp_fma_rate(g.ctx, capi.PFMP_F64)
+        r32 = capi.pfmp_fma_rate(g.ctx, capi.PFMP_F32)
+        assert 0.05 < r64 < 1e3 and 1.0 < r32 < 1e4 and r32 > 8 * r64, (r64, r32)
+        with pytest.raises(capi.PfmpError):
+            capi.pfmp_fma_rate(g.ctx, capi.PFMP_H16)
+        ap = capi.ActionParams(beta=5.5, kappa=0.12, kappa_h=0.11, csw=1.0, n=4, mu=1.2, nu=0.9, tol=1e-10,
+                               max_iter=2000)
+        A = capi.pfmp_action_create(g.ctx, ap)
+        try:
+            T, S = capi.pfmp_schedule_merge([capi.pfmp_schedule_2mn(2, 0.1, LAMBDA_2MN)])
+            xi = np.concatenate([canon(lat.even * torch.tensor(pin.spinor(DIMS, 10 + i)).reshape(*lat.shape, 4, 3))
+                                 for i in range(3)])
+            mom = np.ascontiguousarray(pin.momenta(DIMS, 5)).reshape(-1)
+            info = capi.pfmp_trajectory(A, T, S, [0, 0, 0, 0, 0], mom, xi, 0.5)
+            per_term = [info.ms_force[t] for t in range(5)]
+            assert all(v > 0 for v in per_term) and info.ms_update > 0
+            assert sum(per_term) + info.ms_update <= info.ms_total
+        finally:
+            capi.pfmp_action_destroy(A)
+    finally:
+        g.close()
