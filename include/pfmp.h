@@ -428,20 +428,31 @@ int pfmp_cost(int ntraj, const int* accepted, const double* nmat, const double* 
 
 /* ---- batched solves ------------------------------------------------------------------
  * Many independent systems K_s x = b (each operator on its own context: lattice, gauge
- * field, kappa; nrhs[s] right-hand sides each, 1..64) solved together by grouped kernels:
- * one launch per CG phase covers every (system, site block, rhs) tile, a chunk of
- * iterations is one CUDA graph, FP32 iterations with FP64 reliable updates per rhs as in
- * PFMP_SOLVER_CG_MIXED.  All contexts must live on the current device; the first
- * operator's stream is used for everything during a solve.  x and b are the
- * sum(nrhs) FP64 even device fields in system order.  pfmp_batch_tune times one graph
- * replay for block sizes 64/128/256 and keeps the fastest (call before a solve; it
- * overwrites the batch workspace).  infos (optional) receives one entry per rhs.       */
+ * field, kappa; nrhs[s] right-hand sides each, 1..64) solved together in ONE persistent
+ * cooperative launch: its blocks take (system, site block, rhs) tiles phase after phase
+ * with grid barriers in between, FP32 CG iterations per rhs with reliable updates on the
+ * device (x accumulated in FP64, r = b - K x with K in double-float), as in
+ * PFMP_SOLVER_CG_MIXED; a rhs whose double-float residual is below tol stops, and the
+ * host confirms it with K in FP64 afterwards (relaunching for any it does not confirm).
+ * Every barrier wait is bounded (2 s): a wait that runs out ends the launch with
+ * PFMP_E_TIMEOUT instead of hanging.  All contexts must live on the current device; the
+ * first operator's stream is used for everything during a solve; the operators' clover
+ * terms must be current and built in FP64 (pfmp_op_update).  x and b are the sum(nrhs)
+ * FP64 even device fields in system order (x overwritten).  check_every is not used.
+ * pfmp_batch_tune times one launch of `chunk` iterations for block sizes 64/128/256 and
+ * keeps the fastest (call before a solve; it overwrites the batch workspace).  infos
+ * (optional) receives one entry per rhs.  Memory: 12 FP32 half-lattice fields per rhs.
+ * pfmp_batch_barrier_check runs `rounds` grid barriers of the batch's launch shape with
+ * `missing` more blocks expected than launched (no paper counterpart; it tests the
+ * bounded wait): missing = 0 returns PFMP_OK, missing > 0 makes every wait run out after
+ * limit_s (0 < limit_s <= 10) and returns PFMP_E_TIMEOUT with the context still usable. */
 typedef struct pfmp_batch pfmp_batch;
 int pfmp_batch_create(int nsys, pfmp_op* const* ops, const int* nrhs, pfmp_batch** batch);
 int pfmp_batch_destroy(pfmp_batch* batch);
 int pfmp_batch_tune(pfmp_batch* batch, int chunk, int* block, double* ms_per_chunk);
 int pfmp_batch_solve(pfmp_batch* batch, const pfmp_solver_params* params, void* const* x, const void* const* b,
                      pfmp_solve_info* infos);
+int pfmp_batch_barrier_check(pfmp_batch* batch, int rounds, int missing, double limit_s);
 
 /* ---- learned preconditioner (no counterpart in the paper) ---------------------------
  * A gauge-covariant linear network N used as the preconditioner of FGCR: layer l maps

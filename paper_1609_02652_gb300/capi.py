@@ -156,6 +156,7 @@ SIGNATURES = {
     "pfmp_batch_destroy": (I, [P]),
     "pfmp_batch_tune": (I, [P, I, C.POINTER(I), DP]),
     "pfmp_batch_solve": (I, [P, C.POINTER(SolverParams), C.POINTER(P), C.POINTER(P), C.POINTER(SolveInfo)]),
+    "pfmp_batch_barrier_check": (I, [P, I, I, C.c_double]),
     "pfmp_nn_create": (I, [P, I, C.POINTER(I), I, C.POINTER(P)]),
     "pfmp_nn_destroy": (I, [P]),
     "pfmp_nn_num_weights": (C.c_int64, [P]),
@@ -564,6 +565,12 @@ def pfmp_batch_solve(b, params, xs, bs, raise_on_error=True):
     if raise_on_error:
         check(st)
     return list(infos)
+
+
+def pfmp_batch_barrier_check(b, rounds, missing, limit_s):
+    """Status of `rounds` grid barriers with `missing` more blocks expected than launched
+    (PFMP_OK, or PFMP_E_TIMEOUT once every wait ran out); returned, not raised."""
+    return lib().pfmp_batch_barrier_check(b, rounds, missing, float(limit_s))
 
 
 def pfmp_nn_create(ctx, channels, prec=PFMP_F32):

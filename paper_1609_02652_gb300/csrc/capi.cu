@@ -43,6 +43,7 @@ void batch_destroy(pfmp_batch* B);
 int batch_solve(pfmp_batch* B, double tol, int max_iter, double delta, int check, void* const* x, const void* const* b,
                 pfmp_solve_info* infos);
 int batch_tune(pfmp_batch* B, int chunk, double* best_ms);
+int batch_barrier_check(pfmp_batch* B, int rounds, int missing, double limit_s);
 pfmp_nn* nn_create(pfmp_ctx* c, int nl, const int* ch, int prec);
 void nn_destroy(pfmp_nn* N);
 long nn_num_weights(const pfmp_nn* N);
@@ -771,6 +772,13 @@ int pfmp_batch_tune(pfmp_batch* B, int chunk, int* block, double* ms) {
   PFMP_REQUIRE(B && chunk >= 1, PFMP_E_INVALID, "bad argument");
   int bl = batch_tune(B, chunk, ms);
   if (block) *block = bl;
+  API_END
+}
+
+int pfmp_batch_barrier_check(pfmp_batch* B, int rounds, int missing, double limit_s) {
+  API_BEGIN
+  PFMP_REQUIRE(B, PFMP_E_INVALID, "null argument");
+  batch_barrier_check(B, rounds, missing, limit_s);
   API_END
 }
 

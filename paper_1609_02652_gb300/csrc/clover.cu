@@ -103,42 +103,15 @@ struct CloverOut {
   int* bad;
 };
 
-__device__ void store_clover_df(float4* f, const HermBlock<double> b[2], int cb, int Vh) {
-  for (int blk = 0; blk < 2; ++blk) {
-    float4* g = f + (size_t)(18 * blk) * Vh;
-    for (int k = 0; k < 3; ++k) g[(size_t)k * Vh + cb] = split2(make_double2(b[blk].d[2 * k], b[blk].d[2 * k + 1]));
-    for (int k = 0; k < 15; ++k) g[(size_t)(3 + k) * Vh + cb] = split2(make_double2(b[blk].o[k].re, b[blk].o[k].im));
-  }
-}
-
-__device__ void store_block32(float4* f, const HermBlock<double>& b, int blk, int cb, int Vh) {
+template <typename T>
+__device__ __forceinline__ void store_block32(float4* f, const HermBlock<T>& b, int blk, int cb, int Vh) {
   float4* g = f + (size_t)(9 * blk) * Vh;
   g[cb] = make_float4((float)b.d[0], (float)b.d[1], (float)b.d[2], (float)b.d[3]);
   g[(size_t)Vh + cb] = make_float4((float)b.d[4], (float)b.d[5], (float)b.o[0].re, (float)b.o[0].im);
+#pragma unroll
   for (int k = 0; k < 7; ++k)
     g[(size_t)(2 + k) * Vh + cb] =
         make_float4((float)b.o[1 + 2 * k].re, (float)b.o[1 + 2 * k].im, (float)b.o[2 + 2 * k].re, (float)b.o[2 + 2 * k].im);
-}
-
-// Cholesky A = L L^dag (6x6 Hermitian positive definite); returns false if not PD.
-__device__ bool cholesky6(const cplx<double> A[6][6], cplx<double> L[6][6], double& logdet) {
-  logdet = 0.0;
-  for (int i = 0; i < 6; ++i)
-    for (int j = 0; j < 6; ++j) L[i][j] = mk(0.0, 0.0);
-  for (int j = 0; j < 6; ++j) {
-    double d = A[j][j].re;
-    for (int k = 0; k < j; ++k) d -= norm2(L[j][k]);
-    if (!(d > 0.0)) return false;
-    const double ljj = sqrt(d);
-    L[j][j] = mk(ljj, 0.0);
-    logdet += 2.0 * log(ljj);
-    for (int i = j + 1; i < 6; ++i) {
-      cplx<double> s = A[i][j];
-      for (int k = 0; k < j; ++k) s = s - mul_cj(L[i][k], L[j][k]);
-      L[i][j] = (1.0 / ljj) * s;
-    }
-  }
-  return true;
 }
 
 // F_{mu nu} of every site and plane, one thread per (site, plane): the Hermitian matrix as
@@ -166,16 +139,16 @@ __global__ void k_field_strength(Geom g, const void* __restrict__ U, double* __r
   o[8 * (size_t)g.Vh] = F.m[1][2].im;
 }
 
-__device__ __forceinline__ Mat3<double> load_fmunu(const double* __restrict__ Fin, const Geom& g, int p, int pl,
-                                                   int cb) {
+template <typename T>
+__device__ __forceinline__ Mat3<T> load_fmunu(const double* __restrict__ Fin, const Geom& g, int p, int pl, int cb) {
   const double* f = Fin + (size_t)((p * 6 + pl) * 9) * g.Vh + cb;
-  double v[9];
+  T v[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) v[k] = __ldg(f + (size_t)k * g.Vh);
-  Mat3<double> F;
-  F.m[0][0] = mk(v[0], 0.0);
-  F.m[1][1] = mk(v[1], 0.0);
-  F.m[2][2] = mk(v[2], 0.0);
+  for (int k = 0; k < 9; ++k) v[k] = (T)__ldg(f + (size_t)k * g.Vh);
+  Mat3<T> F;
+  F.m[0][0] = mk(v[0], T(0));
+  F.m[1][1] = mk(v[1], T(0));
+  F.m[2][2] = mk(v[2], T(0));
   F.m[0][1] = mk(v[3], v[4]);
   F.m[1][0] = mk(v[3], -v[4]);
   F.m[0][2] = mk(v[5], v[6]);
@@ -185,76 +158,163 @@ __device__ __forceinline__ Mat3<double> load_fmunu(const double* __restrict__ Fi
   return F;
 }
 
-__global__ void k_clover_build(Geom g, const double* __restrict__ Fin, double kc, CloverOut out, ReduceBuf rb,
-                               double* logdet_out) {
-  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+template <typename T>
+__device__ __forceinline__ void store_block64(double2* f, const HermBlock<T>& b, int blk, int cb, int Vh) {
+  double2* g = f + (size_t)(18 * blk) * Vh;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g[(size_t)k * Vh + cb] = make_double2(b.d[2 * k], b.d[2 * k + 1]);
+#pragma unroll
+  for (int k = 0; k < 15; ++k) g[(size_t)(3 + k) * Vh + cb] = make_double2(b.o[k].re, b.o[k].im);
+}
+template <typename T>
+__device__ __forceinline__ void store_block_df(float4* f, const HermBlock<T>& b, int blk, int cb, int Vh) {
+  float4* g = f + (size_t)(18 * blk) * Vh;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g[(size_t)k * Vh + cb] = split2(make_double2(b.d[2 * k], b.d[2 * k + 1]));
+#pragma unroll
+  for (int k = 0; k < 15; ++k) g[(size_t)(3 + k) * Vh + cb] = split2(make_double2(b.o[k].re, b.o[k].im));
+}
+
+// In place on a packed Hermitian block: the Cholesky factor L (A = L L^dag, lower
+// triangle, real diagonal), then L^{-1} (lower triangular), then A^{-1} = L^{-dag} L^{-1}.
+// Every loop runs over the full 0..5 range with the triangle selected by a condition, so
+// that after unrolling every index is a constant and the block stays in registers.
+// Returns false (and the identity) if A is not positive definite; logdet = log det A.
+template <typename T>
+__device__ __forceinline__ bool invert_block(HermBlock<T>& B, double& logdet) {
+  bool ok = true;
+  logdet = 0.0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    T d = B.d[j];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (k < j) d -= norm2(B.o[tri_index(j, k)]);
+    if (!(d > T(0))) {
+      ok = false;
+      d = T(1);
+    }
+    const T ljj = sqrt(d);
+    B.d[j] = ljj;
+    logdet += 2.0 * (double)log(ljj);
+    const T r = T(1) / ljj;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      if (i > j) {
+        cplx<T> s = B.o[tri_index(i, j)];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          if (k < j) s = s - mul_cj(B.o[tri_index(i, k)], B.o[tri_index(j, k)]);
+        B.o[tri_index(i, j)] = r * s;
+      }
+  }
+  if (!ok) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) B.d[i] = T(1);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) B.o[k] = mk(T(0), T(0));
+    logdet = 0.0;
+    return false;
+  }
+  // L^{-1}: diagonal 1 / L_ii; column by column, (L^{-1})_ij = -(1 / L_ii) sum_{j<=k<i} L_ik (L^{-1})_kj.
+  // Row i of column j reads L_ik for k >= j (not yet overwritten) and (L^{-1})_kj for k < i.
+#pragma unroll
+  for (int i = 0; i < 6; ++i) B.d[i] = T(1) / B.d[i];
+#pragma unroll
+  for (int j = 0; j < 6; ++j)
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      if (i > j) {
+        cplx<T> s = B.d[j] * B.o[tri_index(i, j)];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          if (k > j && k < i) s = s + B.o[tri_index(i, k)] * B.o[tri_index(k, j)];
+        B.o[tri_index(i, j)] = (-B.d[i]) * s;
+      }
+  // A^{-1}_ij = sum_{k >= max(i, j)} conj(Li_ki) Li_kj (lower triangle, i >= j)
+  HermBlock<T> R;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      if (j <= i) {
+        cplx<T> s = i == j ? mk(B.d[i] * B.d[i], T(0)) : B.d[i] * B.o[tri_index(i, j)];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          if (k > i) s = s + cj_mul(B.o[tri_index(k, i)], B.o[tri_index(k, j)]);
+        if (i == j)
+          R.d[i] = s.re;
+        else
+          R.o[tri_index(i, j)] = s;
+      }
+  B = R;
+  return true;
+}
+
+// One thread per (site, chiral block): lanes 2n and 2n + 1 take the two blocks of a site.
+// Block blk (spins 2 blk, 2 blk + 1) of A = 1 - kappa c_sw sigma.F / 2 from the six planes
+// (0,1) (0,2) (0,3) (1,2) (1,3) (2,3): with s = -1 (blk 0) or +1 (blk 1),
+// X1 = F_12 + s F_03, X2 = F_02 - s F_13, X3 = F_01 + s F_23 and
+// A = [[1 - kc X3, -kc (X1 - i X2)], [-kc (X1 + i X2), 1 + kc X3]].
+// Even sites store A_ee, odd sites A_oo^{-1} and their log det (grid-stride, so the grid
+// and the reduction's block count stay bounded at any volume).  T is the arithmetic:
+// double, or float for the clover terms built from an FP32 field strength inside an MD
+// with FP32 forces (FP32 is all the accuracy such a field strength carries).
+template <typename T>
+__global__ void __launch_bounds__(128, 3) k_clover_build(Geom g, const double* __restrict__ Fin, double kc_d,
+                                                         CloverOut out, ReduceBuf rb, double* logdet_out) {
+  const T kc = (T)kc_d;
   const int p = blockIdx.y;
   double ld[1] = {0.0};
-  if (cb < g.Vh) {
-    Mat3<double> F[6];
-    for (int k = 0; k < 6; ++k) F[k] = load_fmunu(Fin, g, p, k, cb);
-    // F index: 0:(0,1) 1:(0,2) 2:(0,3) 3:(1,2) 4:(1,3) 5:(2,3)
-    HermBlock<double> B[2];
-    for (int blk = 0; blk < 2; ++blk) {
-      const double s = blk == 0 ? -1.0 : 1.0;
-      cplx<double> A[6][6];
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < 2L * g.Vh; t += (long)gridDim.x * blockDim.x) {
+    const int cb = (int)(t >> 1), blk = (int)(t & 1);
+    const T s = blk == 0 ? T(-1) : T(1);
+    Mat3<T> X1, X2, X3;
+    {
+      const Mat3<T> F01 = load_fmunu<T>(Fin, g, p, 0, cb), F23 = load_fmunu<T>(Fin, g, p, 5, cb);
+#pragma unroll
       for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-          cplx<double> X1 = F[3].m[i][j] + s * F[2].m[i][j];
-          cplx<double> X2 = F[1].m[i][j] - s * F[4].m[i][j];
-          cplx<double> X3 = F[0].m[i][j] + s * F[5].m[i][j];
-          const double one = (i == j) ? 1.0 : 0.0;
-          A[i][j] = mk(one, 0.0) - kc * X3;
-          A[i + 3][j + 3] = mk(one, 0.0) + kc * X3;
-          A[i][j + 3] = -kc * (X1 - times_i(X2));
-          A[i + 3][j] = -kc * (X1 + times_i(X2));
-        }
-      if (p == 0) {
-        for (int i = 0; i < 6; ++i) B[blk].d[i] = A[i][i].re;
-        for (int i = 1; i < 6; ++i)
-          for (int j = 0; j < i; ++j) B[blk].o[tri_index(i, j)] = A[i][j];
-      } else {
-        cplx<double> L[6][6];
-        double l;
-        if (!cholesky6(A, L, l)) {
-          atomicExch(out.bad, 1);
-          l = 0.0;
-          for (int i = 0; i < 6; ++i) L[i][i] = mk(1.0, 0.0);
-        }
-        ld[0] += l;
-        // Linv = L^{-1} (lower triangular), A^{-1} = Linv^dag Linv
-        cplx<double> Li[6][6];
-        for (int i = 0; i < 6; ++i)
-          for (int j = 0; j < 6; ++j) Li[i][j] = mk(0.0, 0.0);
-        for (int j = 0; j < 6; ++j) {
-          Li[j][j] = mk(1.0 / L[j][j].re, 0.0);
-          for (int i = j + 1; i < 6; ++i) {
-            cplx<double> s2 = mk(0.0, 0.0);
-            for (int kk = j; kk < i; ++kk) s2 = s2 + L[i][kk] * Li[kk][j];
-            Li[i][j] = (-1.0 / L[i][i].re) * s2;
-          }
-        }
-        for (int i = 0; i < 6; ++i)
-          for (int j = 0; j <= i; ++j) {
-            cplx<double> s2 = mk(0.0, 0.0);
-            for (int kk = i; kk < 6; ++kk) s2 = s2 + cj_mul(Li[kk][i], Li[kk][j]);
-            if (i == j)
-              B[blk].d[i] = s2.re;
-            else
-              B[blk].o[tri_index(i, j)] = s2;
-          }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) X3.m[i][j] = F01.m[i][j] + s * F23.m[i][j];
+    }
+    {
+      const Mat3<T> F12 = load_fmunu<T>(Fin, g, p, 3, cb), F03 = load_fmunu<T>(Fin, g, p, 2, cb);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) X1.m[i][j] = F12.m[i][j] + s * F03.m[i][j];
+    }
+    {
+      const Mat3<T> F02 = load_fmunu<T>(Fin, g, p, 1, cb), F13 = load_fmunu<T>(Fin, g, p, 4, cb);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) X2.m[i][j] = F02.m[i][j] - s * F13.m[i][j];
+    }
+    HermBlock<T> B;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      B.d[i] = T(1) - kc * X3.m[i][i].re;
+      B.d[i + 3] = T(1) + kc * X3.m[i][i].re;
+#pragma unroll
+      for (int j = 0; j < i; ++j) {
+        B.o[tri_index(i, j)] = -kc * X3.m[i][j];
+        B.o[tri_index(i + 3, j + 3)] = kc * X3.m[i][j];
       }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) B.o[tri_index(i + 3, j)] = -kc * (X1.m[i][j] + times_i(X2.m[i][j]));
     }
     if (p == 0) {
-      store_clover(out.A64, B, cb, g.Vh);
-      store_clover_df(out.Adf, B, cb, g.Vh);
-      store_block32(out.A32, B[0], 0, cb, g.Vh);
-      store_block32(out.A32, B[1], 1, cb, g.Vh);
+      store_block64(out.A64, B, blk, cb, g.Vh);
+      store_block_df(out.Adf, B, blk, cb, g.Vh);
+      store_block32(out.A32, B, blk, cb, g.Vh);
     } else {
-      store_clover(out.Ai64, B, cb, g.Vh);
-      store_clover_df(out.Aidf, B, cb, g.Vh);
-      store_block32(out.Ai32, B[0], 0, cb, g.Vh);
-      store_block32(out.Ai32, B[1], 1, cb, g.Vh);
+      double l;
+      if (!invert_block(B, l)) atomicExch(out.bad, 1);
+      ld[0] += l;
+      store_block64(out.Ai64, B, blk, cb, g.Vh);
+      store_block_df(out.Aidf, B, blk, cb, g.Vh);
+      store_block32(out.Ai32, B, blk, cb, g.Vh);
     }
   }
   double tot[1];
@@ -300,8 +360,11 @@ void clover_build(pfmp_op* op, int fprec) {
   o.Aidf = op->clovdf[1];
   o.bad = (int*)(c->d_sums + 8);
   PFMP_CUDA(cudaMemsetAsync(o.bad, 0, sizeof(int), c->stream));
-  dim3 grid(nblocks(c->g.Vh, 128), 2);
-  k_clover_build<<<grid, 128, 0, c->stream>>>(c->g, c->fmunu, op->kappa * op->csw, o, c->rb, c->d_sums);
+  dim3 grid(std::min(nblocks(2L * c->g.Vh, 128), 152 * 24), 2);
+  if (fprec == PFMP_F64)
+    k_clover_build<double><<<grid, 128, 0, c->stream>>>(c->g, c->fmunu, op->kappa * op->csw, o, c->rb, c->d_sums);
+  else
+    k_clover_build<float><<<grid, 128, 0, c->stream>>>(c->g, c->fmunu, op->kappa * op->csw, o, c->rb, c->d_sums);
   PFMP_CHECK_LAUNCH();
   PFMP_CUDA(cudaMemcpyAsync(c->h_sums, c->d_sums, 9 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   PFMP_CUDA(cudaStreamSynchronize(c->stream));

@@ -59,6 +59,7 @@ struct pfmp_ctx {
   double* fmunu = nullptr;   // clover field strength F_{mu nu}, [2][6][9][Vh] (built on demand)
   long fmunu_version = -1;   // gauge_version it was computed for
   int fmunu_prec = PFMP_F64; // arithmetic it was computed in
+  float* hc32 = nullptr;     // FP32 copy of a clover insertion for the FP32 clover force (on demand)
 };
 
 struct pfmp_op {
@@ -148,14 +149,28 @@ double true_residual_f64(pfmp_op* op, const void* x64, const void* b64, void* r6
 double true_residual_mixed(pfmp_op* op, const void* x64, const void* b64, void* r64, double target_rr, long* kapply);
 
 // force.cu
-void force_hop(pfmp_ctx* c, int prec, double* F, int pz, const void* Lf, const void* Rf, const void* Lb,
-               const void* Rb, double coef);
-void clover_insert(pfmp_ctx* c, int prec, double* Hc, int p, const void* a, const void* b, double coef);
+// One contraction Re a^dag dM-hat b: the even fields a and b, the odd fields
+// y = A_oo^{-1} H_oe b and w = A_oo^{-1} H^dag_oe a (all of one precision), and the
+// coefficients of its hop part (-kappa^2 coef), its clover part on the even sites
+// (-kappa c_sw coef) and on the odd sites (kappa^2 kappa c_sw coef).
+struct DerivSet {
+  const void* a;
+  const void* b;
+  const void* y;
+  const void* w;
+  double c_hop, c_even, c_odd;
+};
+constexpr int kMaxDerivSets = 8;
+struct DerivBatch {
+  int n = 0;
+  DerivSet s[kMaxDerivSets];
+};
+// F and Hc += every contraction of the batch, one launch per force kernel: the
+// accumulators are read and written once per batch
+void deriv_mhat_batch(pfmp_ctx* c, int prec, double* F, double* Hc, const DerivBatch& B);
 void clover_insert_det(pfmp_op* op, double* Hc, double coef);
 void clover_force(pfmp_ctx* c, int prec, double* F, const double* Hc);
 void gauge_force(pfmp_ctx* c, int prec, double* F, double beta);
-void deriv_mhat(pfmp_op* op, int prec, double* F, double* Hc, const void* a, const void* b, double coef, void* y,
-                void* w);
 
 // blas.cu
 void blas_zero(pfmp_ctx* c, int prec, void* x);

@@ -296,6 +296,7 @@ void ctx_destroy(pfmp_ctx* c) {
   dev_free(c->d_sums);
   dev_free(c->canon);
   dev_free(c->fmunu);
+  dev_free(c->hc32);
   if (c->h_sums) cudaFreeHost(c->h_sums);
   delete c;
 }

@@ -68,9 +68,10 @@ constexpr int PREC_DF = 2;
 __device__ __forceinline__ cplx<df> c_of(float4 v) { return mk(df(v.x, v.y), df(v.z, v.w)); }
 __device__ __forceinline__ float4 v_of(cplx<df> c) { return make_float4(c.re.hi, c.re.lo, c.im.hi, c.im.lo); }
 
+template <bool CG = false>
 __device__ __forceinline__ void load_spinor(Spinor<df>& s, const float4* __restrict__ f, int cb, int Vh) {
 #pragma unroll
-  for (int k = 0; k < 12; ++k) s.s[k / 3][k % 3] = c_of(__ldg(f + (size_t)k * Vh + cb));
+  for (int k = 0; k < 12; ++k) s.s[k / 3][k % 3] = c_of(ldf<CG>(f + (size_t)k * Vh + cb));
 }
 __device__ __forceinline__ void store_spinor(float4* __restrict__ f, const Spinor<df>& s, int cb, int Vh) {
 #pragma unroll

@@ -48,10 +48,22 @@ __device__ __forceinline__ uint32_t f2_to_h2(float a, float b) {
 }
 
 // ---------------------------------------------------------------- spinors
+// A field read with CG = true goes through L2 only (ld.global.cg): a persistent kernel
+// reads fields that other blocks rewrote earlier in the same launch, and L1 is not
+// coherent across SMs.  The default is the read-only path (ld.global.nc).
+template <bool CG, typename V>
+__device__ __forceinline__ V ldf(const V* p) {
+  if constexpr (CG)
+    return __ldcg(p);
+  else
+    return __ldg(p);
+}
+
+template <bool CG = false>
 __device__ __forceinline__ void load_spinor(Spinor<double>& s, const double2* __restrict__ f, int cb, int Vh) {
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    double2 v = __ldg(f + (size_t)k * Vh + cb);
+    double2 v = ldf<CG>(f + (size_t)k * Vh + cb);
     s.s[k / 3][k % 3] = mk(v.x, v.y);
   }
 }
@@ -59,10 +71,11 @@ __device__ __forceinline__ void store_spinor(double2* __restrict__ f, const Spin
 #pragma unroll
   for (int k = 0; k < 12; ++k) f[(size_t)k * Vh + cb] = make_double2(s.s[k / 3][k % 3].re, s.s[k / 3][k % 3].im);
 }
+template <bool CG = false>
 __device__ __forceinline__ void load_spinor(Spinor<float>& s, const float4* __restrict__ f, int cb, int Vh) {
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    float4 v = __ldg(f + (size_t)k * Vh + cb);
+    float4 v = ldf<CG>(f + (size_t)k * Vh + cb);
     s.s[(2 * k) / 3][(2 * k) % 3] = mk(v.x, v.y);
     s.s[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(v.z, v.w);
   }
@@ -76,6 +89,7 @@ __device__ __forceinline__ void store_spinor(float4* __restrict__ f, const Spino
 }
 
 // FP16: [3][Vh] uint4 (complex 4k .. 4k+3 in word k) then FP32 scale[Vh]; value = scale * h
+template <bool CG = false>
 __device__ __forceinline__ void load_spinor(Spinor<float>& s, const uint4* __restrict__ f, int cb, int Vh) {
   const float sc = __ldg(reinterpret_cast<const float*>(f + (size_t)3 * Vh) + cb);
 #pragma unroll

@@ -23,6 +23,7 @@
 //   W1 = U_nu(z-nu)^dag, W2 = U_mu(z-nu), W3 = U_nu(z-nu+mu).
 // Gauge force (Wilson action, beta/3 normalisation): d/dw_a = (beta/3) Im tr(T_a U S),
 // S the sum of the six staples.
+#include <algorithm>
 #include <cmath>
 
 #include "context.h"
@@ -46,20 +47,20 @@ __device__ __forceinline__ void tr_lambda(const Mat3<T>& M, cplx<T> t[8]) {
   t[7] = (T)kInvSqrt3 * (M.m[0][0] + M.m[1][1] - (T)2 * M.m[2][2]);
 }
 
-// H = sum_a h_a T_a (Hermitian traceless)
+// H = sum_a h_a T_a (Hermitian traceless), in the arithmetic of T
 template <typename T>
-__device__ __forceinline__ Mat3<T> from_algebra(const double h[8]) {
+__device__ __forceinline__ Mat3<T> from_algebra(const T h[8]) {
   Mat3<T> H;
-  const double s = 0.5;
-  H.m[0][0] = mk<T>((T)(s * (h[2] + kInvSqrt3 * h[7])), 0);
-  H.m[1][1] = mk<T>((T)(s * (-h[2] + kInvSqrt3 * h[7])), 0);
-  H.m[2][2] = mk<T>((T)(s * (-2.0 * kInvSqrt3 * h[7])), 0);
-  H.m[0][1] = mk<T>((T)(s * h[0]), (T)(-s * h[1]));
-  H.m[1][0] = mk<T>((T)(s * h[0]), (T)(s * h[1]));
-  H.m[0][2] = mk<T>((T)(s * h[3]), (T)(-s * h[4]));
-  H.m[2][0] = mk<T>((T)(s * h[3]), (T)(s * h[4]));
-  H.m[1][2] = mk<T>((T)(s * h[5]), (T)(-s * h[6]));
-  H.m[2][1] = mk<T>((T)(s * h[5]), (T)(s * h[6]));
+  const T s = (T)0.5, r3 = (T)kInvSqrt3;
+  H.m[0][0] = mk<T>(s * (h[2] + r3 * h[7]), 0);
+  H.m[1][1] = mk<T>(s * (-h[2] + r3 * h[7]), 0);
+  H.m[2][2] = mk<T>(s * ((T)-2 * r3 * h[7]), 0);
+  H.m[0][1] = mk<T>(s * h[0], -s * h[1]);
+  H.m[1][0] = mk<T>(s * h[0], s * h[1]);
+  H.m[0][2] = mk<T>(s * h[3], -s * h[4]);
+  H.m[2][0] = mk<T>(s * h[3], s * h[4]);
+  H.m[1][2] = mk<T>(s * h[5], -s * h[6]);
+  H.m[2][1] = mk<T>(s * h[5], s * h[6]);
   return H;
 }
 
@@ -140,98 +141,169 @@ __device__ __forceinline__ Mat3<typename Prec<PREC>::real> force_link(const void
 }
 
 // Spinor products in the arithmetic of PREC (FP64, or FP32 for the MD forces, whose
-// value only has to be a deterministic function of the gauge field), summed into the
-// FP64 force
+// value only has to be a deterministic function of the gauge field).  On the sites of
+// parity pz the forward and backward fields of a contraction (a, b, y, w) are
+// (L_f, R_f, L_b, R_b) = (a, y, w, b) for pz = 0 and (w, b, a, y) for pz = 1.  The link
+// factors out of the batch's sum:
+//   sum_k c_k Z_k = U X_f - X_b U^dag,  X_f = sum_k c_k sum_s R_f,s ((1 - g) L_f)_s^dag,
+//                                       X_b = sum_k c_k sum_s R_b,s ((1 + g) L_b)_s^dag,
+// so each contraction costs two spin-summed outer products, accumulated in PREC, and the
+// FP64 force is read and written once per batch.
 template <int PREC, int MU>
 __device__ void hop_force_dir(double* F, const void* gauge, const Geom& g, int pz, int cb, const int z[4],
-                              const typename Prec<PREC>::vec* Lf, const typename Prec<PREC>::vec* Rf,
-                              const typename Prec<PREC>::vec* Lb, const typename Prec<PREC>::vec* Rb, double coef) {
+                              const DerivBatch& B) {
   using T = typename Prec<PREC>::real;
-  const Mat3<T> U = force_link<PREC>(gauge, g, pz, cb, z, MU);
+  using V = typename Prec<PREC>::vec;
   const int n = nbr_cb(g, z, MU, +1);
-  Spinor<T> lf, rf, lb, rb;
-  load_spinor(lf, Lf, cb, g.Vh);
-  load_spinor(rf, Rf, n, g.Vh);
-  load_spinor(lb, Lb, n, g.Vh);
-  load_spinor(rb, Rb, cb, g.Vh);
-  // Y_f = sum_s (U R_f)_s ((1 - g) L_f)_s^dag,  Y_b = sum_s R_b,s (U (1 + g) L_b)_s^dag
-  Mat3<T> Yf = outer(umul(U, rf), proj_full<MU, -1>(lf));
-  Mat3<T> Yb = outer(rb, umul(U, proj_full<MU, +1>(lb)));
-  double c = coef;
-  if (MU == 3 && z[3] == g.L[3] - 1) c *= g.bc_t;
+  Mat3<T> Xf = mat_zero<T>(), Xb = mat_zero<T>();
+#pragma unroll
+  for (int k = 0; k < kMaxDerivSets; ++k) {
+    if (k < B.n) {
+      const DerivSet& d = B.s[k];
+      const V* Lf = (const V*)(pz == 0 ? d.a : d.w);
+      const V* Rf = (const V*)(pz == 0 ? d.y : d.b);
+      const V* Lb = (const V*)(pz == 0 ? d.w : d.a);
+      const V* Rb = (const V*)(pz == 0 ? d.b : d.y);
+      Spinor<T> lf, rf, lb, rb;
+      load_spinor(lf, Lf, cb, g.Vh);
+      load_spinor(rf, Rf, n, g.Vh);
+      load_spinor(lb, Lb, n, g.Vh);
+      load_spinor(rb, Rb, cb, g.Vh);
+      const T c = (T)d.c_hop;
+      const Mat3<T> Of = outer(rf, proj_full<MU, -1>(lf));
+      const Mat3<T> Ob = outer(rb, proj_full<MU, +1>(lb));
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          Xf.m[i][j] = Xf.m[i][j] + c * Of.m[i][j];
+          Xb.m[i][j] = Xb.m[i][j] + c * Ob.m[i][j];
+        }
+    }
+  }
+  const Mat3<T> U = force_link<PREC>(gauge, g, pz, cb, z, MU);
+  const Mat3<T> A = matmul(U, Xf), Bm = matmul_nd(Xb, U);
   Mat3<T> Z;
+#pragma unroll
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) Z.m[i][j] = Yf.m[i][j] - Yb.m[i][j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Z.m[i][j] = A.m[i][j] - Bm.m[i][j];
   cplx<T> t[8];
   tr_lambda(Z, t);
   // Re(i tr(T_a Z)) = -Im tr(T_a Z) = -(1/2) Im tr(lambda_a Z)
-  for (int a = 0; a < 8; ++a) fptr(F, g, pz, MU, a)[cb] += -0.5 * c * (double)t[a].im;
+  const double c = (MU == 3 && z[3] == g.L[3] - 1) ? -0.5 * g.bc_t : -0.5;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) fptr(F, g, pz, MU, a)[cb] += c * (double)t[a].im;
 }
 
+// A block takes 32 sites of parity blockIdx.y; warp mu of the block takes direction mu,
+// so the four warps read the same local spinors close together (from L1 after the first)
 template <int PREC>
-__global__ void k_force_hop(double* F, const void* gauge, Geom g, int pz, const typename Prec<PREC>::vec* Lf,
-                            const typename Prec<PREC>::vec* Rf, const typename Prec<PREC>::vec* Lb,
-                            const typename Prec<PREC>::vec* Rb, double coef) {
-  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_force_hop(double* F, const void* gauge, Geom g, DerivBatch B) {
+  const int cb = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int mu = threadIdx.x >> 5;
+  const int pz = blockIdx.y;
   if (cb >= g.Vh) return;
   int z[4];
   cb_coords(g, cb, pz, z);
-  hop_force_dir<PREC, 0>(F, gauge, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
-  hop_force_dir<PREC, 1>(F, gauge, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
-  hop_force_dir<PREC, 2>(F, gauge, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
-  hop_force_dir<PREC, 3>(F, gauge, g, pz, cb, z, Lf, Rf, Lb, Rb, coef);
-}
-
-// G for the six planes from the chiral Pauli structure of sigma_{mu nu}:
-// P1 = O01 + O10, P2 = -i O01 + i O10, P3 = O00 - O11 per chiral block B, O_ij = b_{2B+j} a_{2B+i}^dag;
-// planes (01,02,03,12,13,23) = (P3+ + P3-, P2+ + P2-, -P1+ + P1-, P1+ + P1-, P2+ - P2-, -P3+ + P3-)
-template <typename T>
-__device__ void plane_G(const Spinor<T>& a, const Spinor<T>& b, Mat3<T> G[6]) {
-  Mat3<T> P[2][3];
-  for (int B = 0; B < 2; ++B) {
-    Mat3<T> O[2][2];
-    for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 2; ++j)
-        for (int c = 0; c < 3; ++c)
-          for (int d = 0; d < 3; ++d) O[i][j].m[c][d] = mul_cj(b.s[2 * B + j][c], a.s[2 * B + i][d]);
-    for (int c = 0; c < 3; ++c)
-      for (int d = 0; d < 3; ++d) {
-        P[B][0].m[c][d] = O[0][1].m[c][d] + O[1][0].m[c][d];
-        P[B][1].m[c][d] = times_i(O[1][0].m[c][d] - O[0][1].m[c][d]);
-        P[B][2].m[c][d] = O[0][0].m[c][d] - O[1][1].m[c][d];
-      }
+  switch (mu) {
+    case 0: hop_force_dir<PREC, 0>(F, gauge, g, pz, cb, z, B); break;
+    case 1: hop_force_dir<PREC, 1>(F, gauge, g, pz, cb, z, B); break;
+    case 2: hop_force_dir<PREC, 2>(F, gauge, g, pz, cb, z, B); break;
+    default: hop_force_dir<PREC, 3>(F, gauge, g, pz, cb, z, B); break;
   }
-  for (int c = 0; c < 3; ++c)
-    for (int d = 0; d < 3; ++d) {
-      G[0].m[c][d] = P[0][2].m[c][d] + P[1][2].m[c][d];
-      G[1].m[c][d] = P[0][1].m[c][d] + P[1][1].m[c][d];
-      G[2].m[c][d] = P[1][0].m[c][d] - P[0][0].m[c][d];
-      G[3].m[c][d] = P[0][0].m[c][d] + P[1][0].m[c][d];
-      G[4].m[c][d] = P[0][1].m[c][d] - P[1][1].m[c][d];
-      G[5].m[c][d] = P[1][2].m[c][d] - P[0][2].m[c][d];
-    }
 }
 
 __device__ __forceinline__ double* hptr(double* Hc, const Geom& g, int p, int plane, int a) {
   return Hc + (size_t)((p * 6 + plane) * 8 + a) * g.Vh;
 }
 
-// Hc[p] += coef (G~ + G~^dag) for G(a, b): h_a += 4 coef Re tr(T_a G) = 2 coef Re tr(lambda_a G)
-template <int PREC>
-__global__ void k_clover_insert(double* Hc, Geom g, int p, const typename Prec<PREC>::vec* A,
-                                const typename Prec<PREC>::vec* B, double coef) {
+// P_K of chiral block B (spins 2B, 2B + 1) from O_ij = b_{2B+j} a_{2B+i}^dag:
+// P_0 = O01 + O10, P_1 = -i O01 + i O10, P_2 = O00 - O11
+template <int K, typename T>
+__device__ __forceinline__ Mat3<T> pauli_P(const Spinor<T>& a, const Spinor<T>& b, int B) {
+  Mat3<T> P;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if constexpr (K == 0)
+        P.m[c][d] = mul_cj(b.s[2 * B + 1][c], a.s[2 * B][d]) + mul_cj(b.s[2 * B][c], a.s[2 * B + 1][d]);
+      else if constexpr (K == 1)
+        P.m[c][d] = times_i(mul_cj(b.s[2 * B][c], a.s[2 * B + 1][d]) - mul_cj(b.s[2 * B + 1][c], a.s[2 * B][d]));
+      else
+        P.m[c][d] = mul_cj(b.s[2 * B][c], a.s[2 * B][d]) - mul_cj(b.s[2 * B + 1][c], a.s[2 * B + 1][d]);
+    }
+  return P;
+}
+
+// The two planes built from the Pauli component K, summed over the contractions of a
+// batch: (planes, G) = K 2: (01, P+ + P-), (23, -P+ + P-); K 1: (02, P+ + P-),
+// (13, P+ - P-); K 0: (03, -P+ + P-), (12, P+ + P-), with P+ / P- the blocks 0 / 1.
+// P is linear in the contraction's fields: the batch's P+ and P- are accumulated in
+// PREC and reduced to algebra components once.
+template <int PREC, int K>
+__device__ __forceinline__ void clover_insert_pair(double* Hc, const Geom& g, int p, int cb, const DerivBatch& B) {
   using T = typename Prec<PREC>::real;
-  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cb >= g.Vh) return;
-  Spinor<T> a, b;
-  load_spinor(a, A, cb, g.Vh);
-  load_spinor(b, B, cb, g.Vh);
-  Mat3<T> G[6];
-  plane_G(a, b, G);
-  for (int pl = 0; pl < 6; ++pl) {
+  using V = typename Prec<PREC>::vec;
+  Mat3<T> P[2] = {mat_zero<T>(), mat_zero<T>()};
+#pragma unroll
+  for (int s = 0; s < kMaxDerivSets; ++s) {
+    if (s < B.n) {
+      const DerivSet& d = B.s[s];
+      const T coef = (T)(2.0 * (p == 0 ? d.c_even : d.c_odd));
+      Spinor<T> a, b;
+      load_spinor(a, (const V*)(p == 0 ? d.a : d.w), cb, g.Vh);
+      load_spinor(b, (const V*)(p == 0 ? d.b : d.y), cb, g.Vh);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const Mat3<T> Pq = pauli_P<K>(a, b, q);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) P[q].m[i][j] = P[q].m[i][j] + coef * Pq.m[i][j];
+      }
+    }
+  }
+  double r[2][8];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
     cplx<T> t[8];
-    tr_lambda(G[pl], t);
-    for (int k = 0; k < 8; ++k) hptr(Hc, g, p, pl, k)[cb] += 2.0 * coef * (double)t[k].re;
+    tr_lambda(P[q], t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r[q][k] = (double)t[k].re;
+  }
+  // plane index (0,1)=0 (0,2)=1 (0,3)=2 (1,2)=3 (1,3)=4 (2,3)=5
+  constexpr int plA = K == 2 ? 0 : (K == 1 ? 1 : 2);
+  constexpr int plB = K == 2 ? 5 : (K == 1 ? 4 : 3);
+  constexpr double sA = K == 0 ? -1.0 : 1.0;  // sign of P+ in plane plA
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    hptr(Hc, g, p, plA, k)[cb] += sA * r[0][k] + r[1][k];
+    if constexpr (K == 1)
+      hptr(Hc, g, p, plB, k)[cb] += r[0][k] - r[1][k];
+    else if constexpr (K == 2)
+      hptr(Hc, g, p, plB, k)[cb] += -r[0][k] + r[1][k];
+    else
+      hptr(Hc, g, p, plB, k)[cb] += r[0][k] + r[1][k];
+  }
+}
+
+// Hc[p] += coef (G~ + G~^dag) for G(a, b): h_a += 4 coef Re tr(T_a G) = 2 coef Re tr(lambda_a G),
+// summed over the contractions of a batch: on the even sites G(a, b) with c_even, on the
+// odd sites G(w, y) with c_odd.  A block takes 32 sites of parity blockIdx.y and warp K
+// the Pauli component K (two of the six planes), so the three warps read the same
+// spinors close together and each thread keeps 16 accumulators live instead of 48.
+template <int PREC>
+__global__ void __launch_bounds__(96) k_clover_insert(double* Hc, Geom g, DerivBatch B) {
+  const int cb = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int K = threadIdx.x >> 5;
+  const int p = blockIdx.y;
+  if (cb >= g.Vh) return;
+  switch (K) {
+    case 0: clover_insert_pair<PREC, 0>(Hc, g, p, cb, B); break;
+    case 1: clover_insert_pair<PREC, 1>(Hc, g, p, cb, B); break;
+    default: clover_insert_pair<PREC, 2>(Hc, g, p, cb, B); break;
   }
 }
 
@@ -279,13 +351,20 @@ __global__ void k_clover_insert_det(double* Hc, Geom g, const double2* Ainv, dou
   }
 }
 
+// the insertion H of a plane at full coordinates x, times sgn, from a copy of Hc in T
 template <typename T>
-__device__ __forceinline__ Mat3<T> load_H(const double* Hc, const Geom& g, const int x[4], int plane, double sgn) {
+__device__ __forceinline__ Mat3<T> load_H(const T* Hc, const Geom& g, const int x[4], int plane, T sgn) {
   const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
   const int cb = cb_index(g, x);
-  double h[8];
-  for (int a = 0; a < 8; ++a) h[a] = sgn * Hc[(size_t)((p * 6 + plane) * 8 + a) * g.Vh + cb];
+  T h[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) h[a] = sgn * __ldg(Hc + (size_t)((p * 6 + plane) * 8 + a) * g.Vh + cb);
   return from_algebra<T>(h);
+}
+
+__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
 }
 
 __device__ __forceinline__ int plane_index(int mu, int nu) {
@@ -304,10 +383,13 @@ __device__ __forceinline__ int plane_index(int mu, int nu) {
 // both summed Horner-fashion (U X from the left with the running prefix U V1 .. Vk,
 // Y U^dag from the right with the running suffix Wk .. W3 U^dag), which keeps three
 // 3x3 matrices live instead of a dozen.
+// A block takes 32 sites of parity blockIdx.y and warp mu the links U_mu of those sites,
+// so the four warps share the insertions and links they read through L1.
 template <typename T>
-__global__ void k_clover_force(double* F, const void* U64, const double* Hc, Geom g, int p) {
-  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-  const int mu = blockIdx.y;
+__global__ void __launch_bounds__(128) k_clover_force(double* F, const void* U64, const T* Hc, Geom g) {
+  const int cb = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int mu = threadIdx.x >> 5;
+  const int p = blockIdx.y;
   if (cb >= g.Vh) return;
   int z[4];
   cb_coords(g, cb, p, z);
@@ -317,7 +399,7 @@ __global__ void k_clover_force(double* F, const void* U64, const double* Hc, Geo
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == mu) continue;
     const int pl = plane_index(mu, nu);
-    const double sg = mu < nu ? 1.0 : -1.0;
+    const T sg = mu < nu ? (T)1 : (T)-1;
     int zpm[4], zpmpn[4], zpn[4], zmn[4], zmnpm[4];
     shift(g, z, mu, 1, zpm);
     shift(g, zpm, nu, 1, zpmpn);
@@ -399,23 +481,21 @@ __global__ void k_gauge_force(double* F, const void* U64, Geom g, int p, double 
 }
 
 // ------------------------------------------------------------------ host side
-void force_hop(pfmp_ctx* c, int prec, double* F, int pz, const void* Lf, const void* Rf, const void* Lb,
-               const void* Rb, double coef) {
-  if (prec == PFMP_F64)
-    k_force_hop<PFMP_F64><<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(
-        F, c->U64, c->g, pz, (const double2*)Lf, (const double2*)Rf, (const double2*)Lb, (const double2*)Rb, coef);
-  else
-    k_force_hop<PFMP_F32><<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(
-        F, c->U32, c->g, pz, (const float4*)Lf, (const float4*)Rf, (const float4*)Lb, (const float4*)Rb, coef);
-  PFMP_CHECK_LAUNCH();
-}
-void clover_insert(pfmp_ctx* c, int prec, double* Hc, int p, const void* a, const void* b, double coef) {
-  if (prec == PFMP_F64)
-    k_clover_insert<PFMP_F64><<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(Hc, c->g, p, (const double2*)a,
-                                                                            (const double2*)b, coef);
-  else
-    k_clover_insert<PFMP_F32><<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(Hc, c->g, p, (const float4*)a,
-                                                                            (const float4*)b, coef);
+void deriv_mhat_batch(pfmp_ctx* c, int prec, double* F, double* Hc, const DerivBatch& B) {
+  if (B.n == 0) return;
+  PFMP_REQUIRE(B.n <= kMaxDerivSets, PFMP_E_INVALID, "too many contractions in one force batch");
+  bool clover = false;
+  for (int k = 0; k < B.n; ++k) clover = clover || B.s[k].c_even != 0.0 || B.s[k].c_odd != 0.0;
+  const dim3 grid(nblocks(c->g.Vh, 32), 2);
+  if (prec == PFMP_F64) {
+    k_force_hop<PFMP_F64><<<grid, 128, 0, c->stream>>>(F, c->U64, c->g, B);
+    PFMP_CHECK_LAUNCH();
+    if (clover) k_clover_insert<PFMP_F64><<<grid, 96, 0, c->stream>>>(Hc, c->g, B);
+  } else {
+    k_force_hop<PFMP_F32><<<grid, 128, 0, c->stream>>>(F, c->U32, c->g, B);
+    PFMP_CHECK_LAUNCH();
+    if (clover) k_clover_insert<PFMP_F32><<<grid, 96, 0, c->stream>>>(Hc, c->g, B);
+  }
   PFMP_CHECK_LAUNCH();
 }
 void clover_insert_det(pfmp_op* op, double* Hc, double coef) {
@@ -425,15 +505,19 @@ void clover_insert_det(pfmp_op* op, double* Hc, double coef) {
 }
 // prec = PFMP_F64: FP64 arithmetic on the master links; PFMP_F32: FP32 arithmetic on the
 // compressed FP32 links (the forces of an MD with FP32 forces), FP64 accumulation
+// prec = PFMP_F32 reads an FP32 copy of Hc (converted once here, not per leaf)
 void clover_force(pfmp_ctx* c, int prec, double* F, const double* Hc) {
-  for (int p = 0; p < 2; ++p) {
-    dim3 grid(nblocks(c->g.Vh, 64), 4);
-    if (prec == PFMP_F64)
-      k_clover_force<double><<<grid, 64, 0, c->stream>>>(F, c->U64, Hc, c->g, p);
-    else
-      k_clover_force<float><<<grid, 64, 0, c->stream>>>(F, c->U32, Hc, c->g, p);
+  const dim3 grid(nblocks(c->g.Vh, 32), 2);
+  if (prec == PFMP_F64) {
+    k_clover_force<double><<<grid, 128, 0, c->stream>>>(F, c->U64, Hc, c->g);
+  } else {
+    const long n = 96L * c->g.Vh;
+    if (!c->hc32) c->hc32 = (float*)dev_alloc(n * sizeof(float));
+    k_to_f32<<<std::min(nblocks(n), 152 * 8), kBlock, 0, c->stream>>>(Hc, c->hc32, n);
     PFMP_CHECK_LAUNCH();
+    k_clover_force<float><<<grid, 128, 0, c->stream>>>(F, c->U32, c->hc32, c->g);
   }
+  PFMP_CHECK_LAUNCH();
 }
 void gauge_force(pfmp_ctx* c, int prec, double* F, double beta) {
   for (int p = 0; p < 2; ++p) {
@@ -442,24 +526,6 @@ void gauge_force(pfmp_ctx* c, int prec, double* F, double beta) {
     else
       k_gauge_force<float><<<nblocks(c->g.Vh, 128), 128, 0, c->stream>>>(F, c->U32, c->g, p, beta);
     PFMP_CHECK_LAUNCH();
-  }
-}
-
-// Re[a^dag dM-hat b] * coef  ->  F (hop terms) and Hc (clover terms); a, b even fields
-// of precision prec (PFMP_F64 or PFMP_F32), y and w odd temporaries of that precision
-void deriv_mhat(pfmp_op* op, int prec, double* F, double* Hc, const void* a, const void* b, double coef, void* y,
-                void* w) {
-  pfmp_ctx* c = op->ctx;
-  const double k2 = op->kappa * op->kappa;
-  const double kc = op->kappa * op->csw;
-  // y = A_oo^{-1} H_oe b, w = A_oo^{-1} H^dag_oe a (odd)
-  hop_clov_odd(op, prec, y, b, false);
-  hop_clov_odd(op, prec, w, a, true);
-  force_hop(c, prec, F, 0, a, y, w, b, -k2 * coef);
-  force_hop(c, prec, F, 1, w, b, a, y, -k2 * coef);
-  if (op->csw != 0.0) {
-    clover_insert(c, prec, Hc, 0, a, b, -kc * coef);
-    clover_insert(c, prec, Hc, 1, w, y, k2 * (-kc) * coef);
   }
 }
 

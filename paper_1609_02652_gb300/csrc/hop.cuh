@@ -32,7 +32,7 @@ struct HopParams {
 };
 
 // forward (x+mu, projector 1 + SF g) and backward (x-mu, projector 1 - SF g) terms
-template <int PREC, int MU, int SF>
+template <int PREC, int MU, int SF, bool CG = false>
 __device__ __forceinline__ void hop_dir(Spinor<typename Prec<PREC>::real>& acc, const HopParams<PREC>& a,
                                         const int x[4], int cb) {
   using T = typename Prec<PREC>::real;
@@ -41,7 +41,7 @@ __device__ __forceinline__ void hop_dir(Spinor<typename Prec<PREC>::real>& acc, 
   {
     const int n = nbr_cb(g, x, MU, +1);
     Spinor<T> psi;
-    load_spinor(psi, a.in, n, Vh);
+    load_spinor<CG>(psi, a.in, n, Vh);
     Half<T> h = project<MU, SF>(psi);
     Mat3<T> U;
     load_link(U, link_plane<PREC>(a.gauge, a.p * 4 + MU, Vh), cb, Vh);
@@ -52,7 +52,7 @@ __device__ __forceinline__ void hop_dir(Spinor<typename Prec<PREC>::real>& acc, 
   {
     const int n = nbr_cb(g, x, MU, -1);
     Spinor<T> psi;
-    load_spinor(psi, a.in, n, Vh);
+    load_spinor<CG>(psi, a.in, n, Vh);
     Half<T> h = project<MU, -SF>(psi);
     Mat3<T> U;
     load_link(U, link_plane<PREC>(a.gauge, (1 - a.p) * 4 + MU, Vh), n, Vh);
@@ -63,7 +63,7 @@ __device__ __forceinline__ void hop_dir(Spinor<typename Prec<PREC>::real>& acc, 
 }
 
 // the stencil at one output site cb: hop, spin projection and the fused epilogue
-template <int PREC, bool DAG, int EPI>
+template <int PREC, bool DAG, int EPI, bool CG = false>
 __device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site(const HopParams<PREC>& a, int cb) {
   using T = typename Prec<PREC>::real;
   int x[4];
@@ -74,10 +74,10 @@ __device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site(const HopP
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc.s[s][c] = mk<T>(0, 0);
   constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF g_mu
-  hop_dir<PREC, 0, SF>(acc, a, x, cb);
-  hop_dir<PREC, 1, SF>(acc, a, x, cb);
-  hop_dir<PREC, 2, SF>(acc, a, x, cb);
-  hop_dir<PREC, 3, SF>(acc, a, x, cb);
+  hop_dir<PREC, 0, SF, CG>(acc, a, x, cb);
+  hop_dir<PREC, 1, SF, CG>(acc, a, x, cb);
+  hop_dir<PREC, 2, SF, CG>(acc, a, x, cb);
+  hop_dir<PREC, 3, SF, CG>(acc, a, x, cb);
   Spinor<T> out;
   const T cf = (T)a.coef;
   if (EPI == EPI_PLAIN) {
@@ -97,7 +97,7 @@ __device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site(const HopP
     HermBlock<T> B[2];
     load_clover(B, a.clov, cb, a.g.Vh);
     Spinor<T> xl;
-    load_spinor(xl, a.x, cb, a.g.Vh);
+    load_spinor<CG>(xl, a.x, cb, a.g.Vh);
     out = clover_apply(B, xl);
 #pragma unroll
     for (int s = 0; s < 4; ++s)
@@ -321,7 +321,7 @@ __device__ __forceinline__ int nbr_cb_rt(const Geom& g, const int x[4], int mu, 
   return cb_index(g, y);
 }
 
-template <int PREC, bool DAG, int EPI>
+template <int PREC, bool DAG, int EPI, bool CG = false>
 __device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site_rolled(const HopParams<PREC>& a, int cb) {
   using T = typename Prec<PREC>::real;
   const Geom& g = a.g;
@@ -341,7 +341,7 @@ __device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site_rolled(con
     const bool sp = fwd ? SF_POS : !SF_POS;  // sign of this term's projector
     const int n = nbr_cb_rt(g, x, mu, fwd ? +1 : -1);
     Spinor<T> psi;
-    load_spinor(psi, a.in, n, Vh);
+    load_spinor<CG>(psi, a.in, n, Vh);
     const bool low = mu < 2, isI = (mu & 1) == 0;
     const bool n0 = (mu == 1) == sp, n1 = (mu == 2) == sp, n2 = isI == sp, n3 = low == sp;
     Half<T> h;
@@ -379,7 +379,7 @@ __device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site_rolled(con
   // clover: out = cf C acc (EPI_CLOV) or C x + cf acc (EPI_XPAY), one 6x6 block at a time
   Spinor<T> src;
   if (EPI == EPI_XPAY)
-    load_spinor(src, a.x, cb, Vh);
+    load_spinor<CG>(src, a.x, cb, Vh);
   else
     src = acc;
   Spinor<T> out;

@@ -160,12 +160,12 @@ struct pfmp_action {
   double2* U0 = nullptr;  // saved master gauge field
   std::vector<double2*> ev;  // even FP64 temporaries
   std::vector<double2*> xs;  // multi-shift solutions
-  double2* od[2] = {nullptr, nullptr};  // odd FP64 temporaries
-  // FP32 force path (force_prec = PFMP_F32): even and odd temporaries, solutions and
-  // filter chains
+  // FP32 force path (force_prec = PFMP_F32): even temporaries, solutions and filter
+  // chains
   std::vector<float4*> ev32;
   std::vector<float4*> xs32;
-  float4* od32[2] = {nullptr, nullptr};
+  // half-lattice scratch of the batched force contractions, FP64 [0] and FP32 [1]
+  std::vector<void*> fbuf[2];
   int force_evals = 0;
 };
 
@@ -228,19 +228,63 @@ void multishift(pfmp_action* A, pfmp_op* op, const std::vector<cd>& sig, const v
   PFMP_REQUIRE(st == PFMP_OK, st, "multi-shift CG inside the action did not converge");
 }
 
-// Re eta^dag dK chi (coef) -> F, Hc for the operator op (K or J); eta, chi even fields of
-// precision prec
-void deriv_K(pfmp_action* A, pfmp_op* op, const void* eta, const void* chi, double coef, int prec = PFMP_F64) {
-  const bool f64 = prec == PFMP_F64;
-  void* Mchi = f64 ? E(A, 6) : (void*)E32(A, 6);
-  void* Meta = f64 ? E(A, 7) : (void*)E32(A, 7);
-  void* y = f64 ? (void*)A->od[0] : (void*)A->od32[0];
-  void* w = f64 ? (void*)A->od[1] : (void*)A->od32[1];
-  mhat(op, prec, Mchi, chi, false, nullptr, nullptr);
-  mhat(op, prec, Meta, eta, false, nullptr, nullptr);
-  deriv_mhat(op, prec, A->F, A->Hc, Mchi, eta, coef, y, w);
-  deriv_mhat(op, prec, A->F, A->Hc, Meta, chi, coef, y, w);
+// half-lattice scratch field i of the force batches in precision prec
+void* fscratch(pfmp_action* A, int prec, int i) {
+  auto& v = A->fbuf[prec == PFMP_F64 ? 0 : 1];
+  while ((int)v.size() <= i) v.push_back(dev_alloc(spinor_bytes(A->ctx->g, prec)));
+  return v[i];
 }
+
+// The fermion-force contractions of one precision, collected and summed into F and Hc
+// by one launch of each force kernel per kMaxDerivSets of them (App. C: every force is
+// a sum of Re a^dag dM-hat b over the terms' fields).  The fields handed to add_mhat and
+// add_K are read when the batch is flushed: they must stay unchanged until then, which a
+// ring of kRing fields per caller guarantees (add_K flushes before it would overflow, so
+// at most kMaxDerivSets / 2 K contractions are pending).
+struct ForceBatch {
+  static constexpr int kRing = kMaxDerivSets / 2 + 1;
+  pfmp_action* A;
+  int prec;
+  DerivBatch b;
+  ForceBatch(pfmp_action* a, int p) : A(a), prec(p) {}
+  // callers flush before they read F or Hc; a batch dropped by an exception is lost
+  // with the force it belonged to
+  void flush() {
+    deriv_mhat_batch(A->ctx, prec, A->F, A->Hc, b);
+    b.n = 0;
+  }
+  // ring field j of this batch's precision (callers' chains of pending fields)
+  void* ring(int j) { return fscratch(A, prec, 3 * kMaxDerivSets + j % kRing); }
+  // Re a^dag dM-hat b (coef) for the operator op; a, b even fields
+  void add_mhat(pfmp_op* op, const void* a, const void* bf, double coef) {
+    if (b.n == kMaxDerivSets) flush();
+    const int k = b.n;
+    void* y = fscratch(A, prec, kMaxDerivSets + 2 * k);
+    void* w = fscratch(A, prec, kMaxDerivSets + 2 * k + 1);
+    hop_clov_odd(op, prec, y, bf, false);
+    hop_clov_odd(op, prec, w, a, true);
+    const double k2 = op->kappa * op->kappa, kc = op->kappa * op->csw;
+    b.s[k] = DerivSet{a, bf, y, w, -k2 * coef, -kc * coef, k2 * (-kc) * coef};
+    b.n++;
+  }
+  // Re eta^dag dK chi (coef) for K = M-hat^dag M-hat of op:
+  //   Re (M-hat chi)^dag dM-hat eta + Re (M-hat eta)^dag dM-hat chi
+  // (one contraction with twice the coefficient when eta and chi are the same field)
+  void add_K(pfmp_op* op, const void* eta, const void* chi, double coef) {
+    const int need = eta == chi ? 1 : 2;
+    if (b.n + need > kMaxDerivSets) flush();
+    void* Mchi = fscratch(A, prec, b.n);
+    mhat(op, prec, Mchi, chi, false, nullptr, nullptr);
+    if (eta == chi) {
+      add_mhat(op, Mchi, eta, 2.0 * coef);
+      return;
+    }
+    void* Meta = fscratch(A, prec, b.n + 1);
+    mhat(op, prec, Meta, eta, false, nullptr, nullptr);
+    add_mhat(op, Mchi, eta, coef);
+    add_mhat(op, Meta, chi, coef);
+  }
+};
 
 // clover terms of every operator after the gauge field changed; FP32 field strength
 // (fprec = PFMP_F32) for the link updates inside an MD with FP32 forces
@@ -330,10 +374,10 @@ void action_destroy(pfmp_action* A) {
   dev_free(A->U0);
   for (auto p : A->ev) dev_free(p);
   for (auto p : A->xs) dev_free(p);
-  for (auto p : A->od) dev_free(p);
   for (auto p : A->ev32) dev_free(p);
   for (auto p : A->xs32) dev_free(p);
-  for (auto p : A->od32) dev_free(p);
+  for (auto& v : A->fbuf)
+    for (auto p : v) dev_free(p);
   for (auto op : A->ops) op_delete(op);
   delete A;
 }
@@ -421,9 +465,6 @@ pfmp_action* action_create_def(pfmp_ctx* c, const pfmp_action_def* d) {
     A->mom = (double*)dev_alloc((size_t)g.Vh * 64 * sizeof(double));
     A->U0 = (double2*)dev_alloc((size_t)g.Vh * 72 * sizeof(double2));
     for (int i = 0; i < 8; ++i) A->ev.push_back((double2*)dev_alloc(spb(A)));
-    for (auto& p : A->od) p = (double2*)dev_alloc(spb(A));
-    if (d->force_prec == PFMP_F32)
-      for (auto& p : A->od32) p = (float4*)dev_alloc(spinor_bytes(g, PFMP_F32));
   } catch (...) {
     action_destroy(A);
     throw;
@@ -538,37 +579,45 @@ static void force_f32(pfmp_action* A, Term& T, pfmp_op* W, const void* phi) {
       kop(W, PFMP_F32, A->xs32[k], A->xs32[k + 1], nullptr, nullptr);
       caxpby(c, PFMP_F32, -T.q[k + 1], A->xs32[k + 1], 1.0, A->xs32[k]);
     }
-    // eta_0 = phi, eta_k = (J - q_{k-1}^*) eta_{k-1}
-    float4* eta = E32(A, 2);
-    float4* tmp = E32(A, 3);
-    PFMP_CUDA(cudaMemcpyAsync(eta, phi32, b32, cudaMemcpyDeviceToDevice, c->stream));
+    // eta_0 = phi, eta_k = (J - q_{k-1}^*) eta_{k-1}, each in its own ring field
+    ForceBatch fb(A, PFMP_F32);
+    const void* eta = phi32;
     for (int k = 0; k < m; ++k) {
       if (k > 0) {
-        kop(W, PFMP_F32, tmp, eta, nullptr, nullptr);
-        caxpby(c, PFMP_F32, 1.0, tmp, -std::conj(T.q[k - 1]), eta);
+        void* next = fb.ring(k);
+        kop(W, PFMP_F32, next, eta, nullptr, nullptr);
+        caxpby(c, PFMP_F32, -std::conj(T.q[k - 1]), eta, 1.0, next);
+        eta = next;
       }
-      deriv_K(A, W, eta, A->xs32[k], 1.0, PFMP_F32);
+      fb.add_K(W, eta, A->xs32[k], 1.0);
     }
+    fb.flush();
   } else if (T.d.kind == PFMP_KIND_FILTERCORR) {
     multishift(A, W, T.sig, phi32, PFMP_F32);
-    float4* chib = E32(A, 2);
+    ForceBatch fb(A, PFMP_F32);
     for (size_t k = 0; k < T.sig.size(); ++k) {
+      void* chib = fb.ring((int)k);
       caxpby(c, PFMP_F32, T.r[k], A->xs32[k], 0.0, chib);
-      deriv_K(A, W, A->xs32[T.conj_of[k]], chib, -1.0, PFMP_F32);
+      fb.add_K(W, A->xs32[T.conj_of[k]], chib, -1.0);
     }
+    fb.flush();
   } else if (T.d.kind == PFMP_KIND_RATIO) {
     pfmp_op* Mb = A->ops[T.d.b];
     mhat(W, PFMP_F64, E(A, 0), phi, true, nullptr, nullptr);
     cg_tol(A, Mb, E(A, 1), E(A, 0), md_tol(A));
     float4* chi32 = E32(A, 1);
     blas_copy(c, chi32, PFMP_F32, E(A, 1), PFMP_F64);
-    deriv_mhat(W, PFMP_F32, A->F, A->Hc, phi32, chi32, 2.0, A->od32[0], A->od32[1]);
-    deriv_K(A, Mb, chi32, chi32, -1.0, PFMP_F32);
+    ForceBatch fb(A, PFMP_F32);
+    fb.add_mhat(W, phi32, chi32, 2.0);
+    fb.add_K(Mb, chi32, chi32, -1.0);
+    fb.flush();
   } else {  // INV
     cg_tol(A, W, E(A, 1), phi, md_tol(A));
     float4* chi32 = E32(A, 1);
     blas_copy(c, chi32, PFMP_F32, E(A, 1), PFMP_F64);
-    deriv_K(A, W, chi32, chi32, -1.0, PFMP_F32);
+    ForceBatch fb(A, PFMP_F32);
+    fb.add_K(W, chi32, chi32, -1.0);
+    fb.flush();
   }
 }
 
@@ -601,36 +650,44 @@ void action_force(pfmp_action* A, int i) {
       kop(W, PFMP_F64, A->xs[k], A->xs[k + 1], nullptr, nullptr);
       caxpby(c, -T.q[k + 1], A->xs[k + 1], 1.0, A->xs[k]);
     }
-    // eta_0 = phi, eta_i = (J - q_{i-1}^*) eta_{i-1}
-    void* eta = E(A, 2);
-    void* tmp = E(A, 3);
-    PFMP_CUDA(cudaMemcpyAsync(eta, phi, spb(A), cudaMemcpyDeviceToDevice, c->stream));
+    // eta_0 = phi, eta_i = (J - q_{i-1}^*) eta_{i-1}, each in its own ring field
+    ForceBatch fb(A, PFMP_F64);
+    const void* eta = phi;
     for (int k = 0; k < m; ++k) {
       if (k > 0) {
-        kop(W, PFMP_F64, tmp, eta, nullptr, nullptr);
-        caxpby(c, 1.0, tmp, -std::conj(T.q[k - 1]), eta);
+        void* next = fb.ring(k);
+        kop(W, PFMP_F64, next, eta, nullptr, nullptr);
+        caxpby(c, -std::conj(T.q[k - 1]), eta, 1.0, next);
+        eta = next;
       }
-      deriv_K(A, W, eta, A->xs[k], 1.0);
+      fb.add_K(W, eta, A->xs[k], 1.0);
     }
+    fb.flush();
   } else if (T.d.kind == PFMP_KIND_FILTERCORR) {
     multishift(A, W, T.sig, phi);
-    void* chib = E(A, 2);
+    ForceBatch fb(A, PFMP_F64);
     for (size_t k = 0; k < T.sig.size(); ++k) {
+      void* chib = fb.ring((int)k);
       caxpby(c, T.r[k], A->xs[k], 0.0, chib);
-      deriv_K(A, W, A->xs[T.conj_of[k]], chib, -1.0);
+      fb.add_K(W, A->xs[T.conj_of[k]], chib, -1.0);
     }
+    fb.flush();
   } else if (T.d.kind == PFMP_KIND_RATIO) {
     pfmp_op* Mb = A->ops[T.d.b];
     mhat(W, PFMP_F64, E(A, 0), phi, true, nullptr, nullptr);
     void* chi = E(A, 1);
     cg64(A, Mb, chi, E(A, 0));
     // 2 Re chi^dag dW^dag phi = 2 Re phi^dag dW chi
-    deriv_mhat(W, PFMP_F64, A->F, A->Hc, phi, chi, 2.0, A->od[0], A->od[1]);
-    deriv_K(A, Mb, chi, chi, -1.0);
+    ForceBatch fb(A, PFMP_F64);
+    fb.add_mhat(W, phi, chi, 2.0);
+    fb.add_K(Mb, chi, chi, -1.0);
+    fb.flush();
   } else {  // INV
     void* chi = E(A, 1);
     cg64(A, W, chi, phi);
-    deriv_K(A, W, chi, chi, -1.0);
+    ForceBatch fb(A, PFMP_F64);
+    fb.add_K(W, chi, chi, -1.0);
+    fb.flush();
   }
   if (clover) clover_force(c, fprec, A->F, A->Hc);
 }

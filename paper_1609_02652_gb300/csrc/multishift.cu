@@ -172,11 +172,14 @@ __global__ void k_ms_xp(V* const* x, V* const* p, V* __restrict__ pseed, const V
   }
 }
 
-// y = a x + b y (complex a, b) on FP64 or FP32 even fields
+// y = a x + b y (complex a, b) on FP64 or FP32 even fields; with b = 0, y = a x without
+// reading y (its previous contents may be anything, NaN included)
 template <typename V>
 __global__ void k_caxpby(double2 a, const V* __restrict__ x, double2 b, V* __restrict__ y, long n) {
+  const bool read_y = b.x != 0.0 || b.y != 0.0;
+  const double2 zero = make_double2(0.0, 0.0);
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    y[i] = axpby_c(a, x[i], b, y[i]);
+    y[i] = read_y ? axpby_c(a, x[i], b, y[i]) : axpby_c(a, x[i], zero, x[i]);
 }
 
 static int ms_grid(long n) {

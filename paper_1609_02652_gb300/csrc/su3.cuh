@@ -1,6 +1,6 @@
 // SU(3) helpers in FP64 shared by field initialisation and the link update:
 // anti-Hermitian algebra elements, the matrix exponential (scaling and squaring of the
-// Taylor series) and reunitarisation.
+// Taylor series, reduced to three scalar series by Cayley-Hamilton) and reunitarisation.
 #pragma once
 #include "pfmp_internal.cuh"
 
@@ -22,30 +22,55 @@ __device__ inline void reunitarise(Mat3<double>& U) {
   reconstruct_row2(U);
 }
 
-// exp(X) for a small-ish 3x3 anti-Hermitian X: scaling by 2^-s until ||X||_F <= 1/4,
-// Taylor series to order 14, then s squarings.
+// exp(X) for a 3x3 complex X.  By Cayley-Hamilton X^3 = e1 X^2 - e2 X + e3 I
+// (e1 = tr X, e2 = (e1^2 - tr X^2) / 2, e3 = det X), so every term X^n / n! of the Taylor
+// series is a_n I + b_n X + c_n X^2 with scalar coefficients, and
+//   X^{n+1} / (n+1)! = (c_n e3, a_n - c_n e2, b_n + c_n e1) / (n + 1)   in that basis.
+// The series runs in those three scalars until the last term's bound ||X||^n / n! is
+// below 2^-56 (for ||X|| <= 1 it bounds the remainder too) and costs one
+// matrix product (X^2) instead of one per order.  X is first scaled by 2^-s until
+// ||X||_F <= 1 and the result squared s times; inside the MD ||eps P|| is well below 1.
 __device__ inline Mat3<double> expm3(Mat3<double> X) {
   double nf = 0;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) nf += norm2(X.m[i][j]);
   nf = sqrt(nf);
   int s = 0;
-  while (nf > 0.25 && s < 60) {
+  while (nf > 1.0 && s < 60) {
     nf *= 0.5;
     ++s;
   }
   const double sc = ldexp(1.0, -s);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) X.m[i][j] = sc * X.m[i][j];
-  // Horner: E = I + X (I + X/2 (I + X/3 ( ... )))
-  Mat3<double> E = mat_zero<double>();
-  for (int i = 0; i < 3; ++i) E.m[i][i] = mk(1.0, 0.0);
-  for (int k = 14; k >= 1; --k) {
-    Mat3<double> T = matmul(X, E);
-    const double f = 1.0 / k;
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) E.m[i][j] = (i == j ? mk(1.0, 0.0) : mk(0.0, 0.0)) + f * T.m[i][j];
+  const Mat3<double> X2 = matmul(X, X);
+  const cplx<double> e1 = X.m[0][0] + X.m[1][1] + X.m[2][2];
+  const cplx<double> trX2 = X2.m[0][0] + X2.m[1][1] + X2.m[2][2];
+  const cplx<double> e2 = 0.5 * (e1 * e1 - trX2);
+  const cplx<double> e3 = X.m[0][0] * (X.m[1][1] * X.m[2][2] - X.m[1][2] * X.m[2][1]) -
+                          X.m[0][1] * (X.m[1][0] * X.m[2][2] - X.m[1][2] * X.m[2][0]) +
+                          X.m[0][2] * (X.m[1][0] * X.m[2][1] - X.m[1][1] * X.m[2][0]);
+  // running term (a, b, c) = X^n / n! and the partial sums (f0, f1, f2)
+  cplx<double> a = mk(0.0, 0.0), b = mk(1.0, 0.0), c = mk(0.0, 0.0);
+  cplx<double> f0 = mk(1.0, 0.0), f1 = b, f2 = c;
+  double term = nf;  // ||X||^n / n!
+  for (int n = 1; n < 24 && term >= 1.3877787807814457e-17; ++n) {
+    const double r = 1.0 / (n + 1);
+    const cplx<double> a1 = r * (c * e3), b1 = r * (a - c * e2), c1 = r * (b + c * e1);
+    a = a1;
+    b = b1;
+    c = c1;
+    f0 = f0 + a;
+    f1 = f1 + b;
+    f2 = f2 + c;
+    term *= nf * r;
   }
+  Mat3<double> E;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      E.m[i][j] = f1 * X.m[i][j] + f2 * X2.m[i][j];
+      if (i == j) E.m[i][j] = E.m[i][j] + f0;
+    }
   for (int k = 0; k < s; ++k) E = matmul(E, E);
   return E;
 }

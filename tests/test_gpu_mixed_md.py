@@ -122,6 +122,33 @@ def test_fp32_forces(world, kind, a, b, p1, p2, tol):
         capi.pfmp_action_destroy(A)
 
 
+def test_filter_force_after_larger_filter(world):
+    """An order-12 filter force after order-64 ones on the same context, FP32 and FP64: the
+    new action's buffers may be recycled device memory holding anything (NaN patterns
+    included), and every field the force reads must be written first (a zero coefficient
+    never multiplies stale contents)."""
+    from oracle.action import Action, Term
+
+    lat, U, g, capi = world
+    phi = lat.even * torch.tensor(pin.spinor(DIMS, 61)).reshape(*lat.shape, 4, 3)
+    ref = None
+    for p1, p2, fp in ((0, 64, capi.PFMP_F32), (0, 64, 0), (0, 12, capi.PFMP_F32), (0, 12, 0)):
+        t = Term("filter", a=1, b=0, p1=p1, p2=p2)
+        A = capi.pfmp_action_create_def(g.ctx, _def(capi, [t], solver=1, force_prec=fp, md_tol=1e-6))
+        try:
+            capi.pfmp_action_set_phi(A, 0, canon(phi))
+            F = np.zeros(lat.V * 32)
+            capi.pfmp_action_force(A, 0, F)
+        finally:
+            capi.pfmp_action_destroy(A)
+        assert np.isfinite(F).all(), (p2, fp)
+        if p2 == 12:
+            if ref is None:
+                ref = Action(lat, BETA, CSW, KAPPAS, [t], mu=MU, nu=NU, tol=TOL).F(U, 0, phi)
+            err = rel_l2(torch.tensor(F).reshape(*lat.shape, 4, 8), ref)
+            assert err < (1e-4 if fp else 1e-9), (fp, err)
+
+
 @pytest.fixture(scope="module")
 def config1_reference():
     from oracle.action import PFMP, PFMPParams
