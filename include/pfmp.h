@@ -511,6 +511,9 @@ int pfmp_solve_fgcr(pfmp_op* op, pfmp_nn* nn, const pfmp_solver_params* params, 
 #define PFMP_KERNEL_HOP_F64 1
 #define PFMP_KERNEL_HOP_DF 2   /* double-float (FP32-pair) stencil of the true residual   */
 #define PFMP_KERNEL_HOP_H16 3  /* FP16-storage stencil (PFMP_SOLVER_CG_HALF)              */
+#define PFMP_KERNEL_CG_F32 4   /* the FP32 CG iteration's four stencil kernels with the CG
+                                  vector updates fused in (PFMP_SOLVER_CG_MIXED); bytes count
+                                  the CG vectors each reads or writes as well            */
 int pfmp_profile_begin(pfmp_ctx* ctx);
 int pfmp_profile_end(pfmp_ctx* ctx, int kernel_class, int64_t* launches, double* total_ms, double* total_bytes);
 /* Measured FMA throughput of the current GPU on the FP64 (prec = PFMP_F64) or FP32

@@ -32,6 +32,7 @@ PFMP_KERNEL_HOP_F32 = 0
 PFMP_KERNEL_HOP_F64 = 1
 PFMP_KERNEL_HOP_DF = 2
 PFMP_KERNEL_HOP_H16 = 3
+PFMP_KERNEL_CG_F32 = 4
 PFMP_SOLVER_CG64 = 0
 PFMP_SOLVER_CG_MIXED = 1
 PFMP_SOLVER_CG_HALF = 2

@@ -890,7 +890,7 @@ int pfmp_profile_end(pfmp_ctx* ctx, int cls, int64_t* launches, double* total_ms
   API_BEGIN
   PFMP_REQUIRE(ctx && launches && total_ms && total_bytes, PFMP_E_INVALID, "null argument");
   PFMP_REQUIRE(cls == PFMP_KERNEL_HOP_F32 || cls == PFMP_KERNEL_HOP_F64 || cls == PFMP_KERNEL_HOP_DF ||
-                   cls == PFMP_KERNEL_HOP_H16,
+                   cls == PFMP_KERNEL_HOP_H16 || cls == PFMP_KERNEL_CG_F32,
                PFMP_E_INVALID,
                "bad kernel class");
   long n = 0;

@@ -148,6 +148,10 @@ double true_residual_f64(pfmp_op* op, const void* x64, const void* b64, void* r6
 // double-float, confirmed in FP64 once below target_rr; the FP64 value decides
 double true_residual_mixed(pfmp_op* op, const void* x64, const void* b64, void* r64, double target_rr, long* kapply);
 
+// cg_fused.cu: one FP32 CG iteration as four stencil kernels with the vector updates
+// fused in (p = r + beta p formed by the next iteration; scalars in op->scal)
+void cg_fused_iteration(pfmp_op* op, float4* x, float4* r, float4* p);
+
 // force.cu
 // One contraction Re a^dag dM-hat b: the even fields a and b, the odd fields
 // y = A_oo^{-1} H_oe b and w = A_oo^{-1} H^dag_oe a (all of one precision), and the

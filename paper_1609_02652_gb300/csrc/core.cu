@@ -108,7 +108,7 @@ __global__ void k_gauge_from_algebra(Geom g, const double* __restrict__ h, doubl
   for (int mu = 0; mu < 4; ++mu) {
     double c[8];
     for (int a = 0; a < 8; ++a) c[a] = h[(s * 4 + mu) * 8 + a];
-    Mat3<double> E = expm3(i_algebra(c, eps));
+    Mat3<double> E = expm_algebra(c, eps);
     reunitarise(E);
     store_link18(U + (size_t)((p * 4 + mu) * 9) * g.Vh, E, cb, g.Vh);
   }

@@ -91,6 +91,7 @@ HopParams<PREC> params(pfmp_op* op, int p, void* out, const void* in) {
                                : (const vec*)(const void*)op->ctx->U32;
   a.clov = nullptr;
   a.x = nullptr;
+  a.in2 = nullptr;
   a.coef = 1.0;
   a.rb = op->ctx->rb;
   a.norm_out = nullptr;

@@ -25,23 +25,41 @@ struct HopParams {
   const vec* gauge;  // per (parity, mu) link planes, located by link_plane
   const vec* clov;   // clover blocks of parity p (EPI_CLOV, EPI_XPAY)
   const vec* x;      // local input of parity p (EPI_XPAY)
+  const vec* in2;    // second input (XPY stencils: the input is in + beta in2)
   double coef;
   ReduceBuf rb;
   double* norm_out;  // ||out||^2 (device) when reducing
   CGScalars* scal;   // optional: alpha = rr / ||out||^2; skip all work once done
 };
 
+// the stencil's input at site n: a.in, or with XPY a.in + beta a.in2 (a CG direction
+// p = r + beta p_old formed where the stencil reads it)
+template <int PREC, bool CG, bool XPY>
+__device__ __forceinline__ void load_in(Spinor<typename Prec<PREC>::real>& psi, const HopParams<PREC>& a, int n, int Vh,
+                                        typename Prec<PREC>::real beta) {
+  load_spinor<CG>(psi, a.in, n, Vh);
+  if constexpr (XPY) {
+    Spinor<typename Prec<PREC>::real> q;
+    load_spinor<CG>(q, a.in2, n, Vh);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) psi.s[s][c] = psi.s[s][c] + beta * q.s[s][c];
+  }
+}
+
 // forward (x+mu, projector 1 + SF g) and backward (x-mu, projector 1 - SF g) terms
-template <int PREC, int MU, int SF, bool CG = false>
+template <int PREC, int MU, int SF, bool CG = false, bool XPY = false>
 __device__ __forceinline__ void hop_dir(Spinor<typename Prec<PREC>::real>& acc, const HopParams<PREC>& a,
-                                        const int x[4], int cb) {
+                                        const int x[4], int cb,
+                                        typename Prec<PREC>::real beta = typename Prec<PREC>::real(0)) {
   using T = typename Prec<PREC>::real;
   const Geom& g = a.g;
   const int Vh = g.Vh;
   {
     const int n = nbr_cb(g, x, MU, +1);
     Spinor<T> psi;
-    load_spinor<CG>(psi, a.in, n, Vh);
+    load_in<PREC, CG, XPY>(psi, a, n, Vh, beta);
     Half<T> h = project<MU, SF>(psi);
     Mat3<T> U;
     load_link(U, link_plane<PREC>(a.gauge, a.p * 4 + MU, Vh), cb, Vh);
@@ -52,7 +70,7 @@ __device__ __forceinline__ void hop_dir(Spinor<typename Prec<PREC>::real>& acc, 
   {
     const int n = nbr_cb(g, x, MU, -1);
     Spinor<T> psi;
-    load_spinor<CG>(psi, a.in, n, Vh);
+    load_in<PREC, CG, XPY>(psi, a, n, Vh, beta);
     Half<T> h = project<MU, -SF>(psi);
     Mat3<T> U;
     load_link(U, link_plane<PREC>(a.gauge, (1 - a.p) * 4 + MU, Vh), n, Vh);
@@ -62,9 +80,13 @@ __device__ __forceinline__ void hop_dir(Spinor<typename Prec<PREC>::real>& acc, 
   }
 }
 
-// the stencil at one output site cb: hop, spin projection and the fused epilogue
-template <int PREC, bool DAG, int EPI, bool CG = false>
-__device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site(const HopParams<PREC>& a, int cb) {
+// the stencil at one output site cb: hop, spin projection and the fused epilogue.  XPY:
+// the input is a.in + beta a.in2; xl: the local input of EPI_XPAY given by the caller
+// instead of loaded from a.x
+template <int PREC, bool DAG, int EPI, bool CG = false, bool XPY = false>
+__device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site(
+    const HopParams<PREC>& a, int cb, typename Prec<PREC>::real beta = typename Prec<PREC>::real(0),
+    const Spinor<typename Prec<PREC>::real>* xl_given = nullptr) {
   using T = typename Prec<PREC>::real;
   int x[4];
   cb_coords(a.g, cb, a.p, x);
@@ -74,10 +96,10 @@ __device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site(const HopP
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc.s[s][c] = mk<T>(0, 0);
   constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF g_mu
-  hop_dir<PREC, 0, SF, CG>(acc, a, x, cb);
-  hop_dir<PREC, 1, SF, CG>(acc, a, x, cb);
-  hop_dir<PREC, 2, SF, CG>(acc, a, x, cb);
-  hop_dir<PREC, 3, SF, CG>(acc, a, x, cb);
+  hop_dir<PREC, 0, SF, CG, XPY>(acc, a, x, cb, beta);
+  hop_dir<PREC, 1, SF, CG, XPY>(acc, a, x, cb, beta);
+  hop_dir<PREC, 2, SF, CG, XPY>(acc, a, x, cb, beta);
+  hop_dir<PREC, 3, SF, CG, XPY>(acc, a, x, cb, beta);
   Spinor<T> out;
   const T cf = (T)a.coef;
   if (EPI == EPI_PLAIN) {
@@ -97,7 +119,10 @@ __device__ __forceinline__ Spinor<typename Prec<PREC>::real> hop_site(const HopP
     HermBlock<T> B[2];
     load_clover(B, a.clov, cb, a.g.Vh);
     Spinor<T> xl;
-    load_spinor<CG>(xl, a.x, cb, a.g.Vh);
+    if (xl_given)
+      xl = *xl_given;
+    else
+      load_spinor<CG>(xl, a.x, cb, a.g.Vh);
     out = clover_apply(B, xl);
 #pragma unroll
     for (int s = 0; s < 4; ++s)

@@ -63,7 +63,7 @@ __global__ void k_link_update(double2* U, const double* __restrict__ mom, Geom g
   if (cb >= g.Vh) return;
   double c[8];
   for (int a = 0; a < 8; ++a) c[a] = mom[(size_t)(pm * 8 + a) * g.Vh + cb];
-  Mat3<double> E = expm3(i_algebra(c, eps));
+  Mat3<double> E = expm_algebra(c, eps);
   Mat3<double> L;
   double2* base = U + (size_t)(pm * 9) * g.Vh;
   load_link18(L, base, cb, g.Vh);

@@ -18,13 +18,15 @@
 
 namespace pfmp {
 
-static void put_scalars(pfmp_op* op, double rr, double stop_rr) {
+// beta: the pending step of the fused FP32 iteration (p = r + beta p_old is formed by the
+// next iteration); 0 starts from p = r
+static void put_scalars(pfmp_op* op, double rr, double stop_rr, double beta = 0.0) {
   CGScalars* h = op->h_scal;
   h->rr = rr;
   h->rr_new = rr;
   h->pAp = 0;
   h->alpha = 0;
-  h->beta = 0;
+  h->beta = beta;
   h->stop_rr = stop_rr;
   h->done = 0;
   h->done_next = 0;
@@ -55,6 +57,10 @@ static double true_residual(pfmp_op* op, const void* x, const void* b, void* r, 
 
 static void launch_chunk(pfmp_op* op, int prec, void* x, void* r, void* p, void* Ap, int chunk) {
   pfmp_ctx* c = op->ctx;
+  if (prec == PFMP_F32) {  // four kernels per iteration, the vector updates fused in
+    for (int k = 0; k < chunk; ++k) cg_fused_iteration(op, (float4*)x, (float4*)r, (float4*)p);
+    return;
+  }
   for (int k = 0; k < chunk; ++k) {
     kop(op, prec, Ap, p, &op->scal->pAp, op->scal);
     cg_step_xr(c, prec, x, r, p, Ap, op->scal);
@@ -63,8 +69,9 @@ static void launch_chunk(pfmp_op* op, int prec, void* x, void* r, void* p, void*
 }
 
 // One chunk of CG iterations.  Without kernel profiling the chunk is captured once into
-// a CUDA graph (6 kernels per iteration, all parameters fixed: the scalars live on the
-// device) and replayed on the context's stream, which removes the per-launch host cost.
+// a CUDA graph (6 kernels per iteration, 4 for FP32; all parameters fixed: the scalars
+// live on the device) and replayed on the context's stream, which removes the per-launch
+// host cost.
 // K applications are counted by run_cg from the iterations the device actually ran (the
 // queued kernels of a converged chunk return at once), so the count kop keeps while the
 // chunk is launched or captured is put back afterwards.
@@ -182,16 +189,18 @@ int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int c
     blas_copy(c, p32, sp, r32, PFMP_F32);
     blas_zero(c, PFMP_F32, xs32);
     double rr_s = host_norm2(op, PFMP_F32, r32);
+    double beta = 0.0;  // the fused FP32 iteration's pending step, kept across updates
     while (total < max_iter) {
       // sloppy target: a factor delta below the last true residual, not below tol
       double stop = delta * delta * rr_true;
       const double floor_rr = 0.25 * tol * tol * bb;
       if (stop < floor_rr) stop = floor_rr;
-      put_scalars(op, rr_s, stop);
+      put_scalars(op, rr_s, stop, sp == PFMP_F32 ? beta : 0.0);
       const int it = run_cg(op, sp, xs32, r32, p32, Ap32, max_iter - total, check_every);
       total += it;
       *kapply += it;
       PFMP_REQUIRE(std::isfinite(op->h_scal->rr), PFMP_E_NAN, "sloppy CG residual became NaN/Inf");
+      beta = op->h_scal->beta;
       // reliable update: the true residual in double-float (FP32 pipe), confirmed in FP64
       // once it is below the target
       blas_add_lo(c, x, xs32);
@@ -203,6 +212,7 @@ int solve(pfmp_op* op, int method, double tol, int max_iter, double delta, int c
       rr_s = host_norm2(op, PFMP_F32, r32);
       if (it == 0) {  // stalled: restart the direction as well
         blas_copy(c, p32, sp, r32, PFMP_F32);
+        beta = 0.0;
       }
     }
   } else {
