@@ -156,9 +156,9 @@ __device__ void hop_force_dir(double* F, const void* gauge, const Geom& g, int p
   using V = typename Prec<PREC>::vec;
   const int n = nbr_cb(g, z, MU, +1);
   Mat3<T> Xf = mat_zero<T>(), Xb = mat_zero<T>();
-#pragma unroll
-  for (int k = 0; k < kMaxDerivSets; ++k) {
-    if (k < B.n) {
+#pragma unroll 1
+  for (int k = 0; k < B.n; ++k) {
+    {
       const DerivSet& d = B.s[k];
       const V* Lf = (const V*)(pz == 0 ? d.a : d.w);
       const V* Rf = (const V*)(pz == 0 ? d.y : d.b);
@@ -247,9 +247,9 @@ __device__ __forceinline__ void clover_insert_pair(double* Hc, const Geom& g, in
   using T = typename Prec<PREC>::real;
   using V = typename Prec<PREC>::vec;
   Mat3<T> P[2] = {mat_zero<T>(), mat_zero<T>()};
-#pragma unroll
-  for (int s = 0; s < kMaxDerivSets; ++s) {
-    if (s < B.n) {
+#pragma unroll 1
+  for (int s = 0; s < B.n; ++s) {
+    {
       const DerivSet& d = B.s[s];
       const T coef = (T)(2.0 * (p == 0 ? d.c_even : d.c_odd));
       Spinor<T> a, b;
