@@ -86,9 +86,13 @@ __device__ __forceinline__ Mat3<float> glink<float>(const void* gauge, const Geo
   load_link(M, link_plane<PFMP_F32>((const float4*)gauge, p * 4 + mu, g.Vh), cb_index(g, x), g.Vh);
   return M;
 }
+// y = x + d mu-hat (d = +-1), periodic
 __device__ __forceinline__ void shift(const Geom& g, const int x[4], int mu, int d, int y[4]) {
   for (int k = 0; k < 4; ++k) y[k] = x[k];
-  y[mu] = (y[mu] + d + g.L[mu]) % g.L[mu];
+  int v = y[mu] + d;
+  if (v >= g.L[mu]) v -= g.L[mu];
+  if (v < 0) v += g.L[mu];
+  y[mu] = v;
 }
 
 __device__ __forceinline__ double* fptr(double* F, const Geom& g, int p, int mu, int a) {
@@ -386,7 +390,12 @@ __device__ __forceinline__ int plane_index(int mu, int nu) {
 // A block takes 32 sites of parity blockIdx.y and warp mu the links U_mu of those sites,
 // so the four warps share the insertions and links they read through L1.
 template <typename T>
-__global__ void __launch_bounds__(128) k_clover_force(double* F, const void* U64, const T* Hc, Geom g) {
+constexpr int clover_force_min_blocks() {
+  return sizeof(T) == 4 ? 3 : 1;  // FP32: 3 resident blocks (168 registers, a few spilled)
+}
+template <typename T>
+__global__ void __launch_bounds__(128, clover_force_min_blocks<T>()) k_clover_force(double* F, const void* U64,
+                                                                                  const T* Hc, Geom g) {
   const int cb = blockIdx.x * 32 + (threadIdx.x & 31);
   const int mu = threadIdx.x >> 5;
   const int p = blockIdx.y;
