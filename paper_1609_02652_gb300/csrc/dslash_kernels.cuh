@@ -22,7 +22,7 @@
 #define HOP_MINB_F32 7
 #endif
 #ifndef HOP_MINB_H16
-#define HOP_MINB_H16 7
+#define HOP_MINB_H16 6
 #endif
 #ifndef HOP_MINB_F64
 #define HOP_MINB_F64 1
@@ -32,7 +32,9 @@ namespace pfmp {
 
 // Resident 128-thread blocks per SM that the register allocation must allow.  The
 // stencil is bound by memory latency, so more warps in flight pay even at the cost of a
-// few spilled registers (FP32, 32^3x64: 0.85 -> 0.89 of the copy bandwidth at 7 blocks);
+// few spilled registers (FP32, 32^3x64: 0.85 -> 0.89 of the copy bandwidth at 7 blocks).
+// The FP16-storage stencil does more arithmetic per byte and runs best with a few more
+// registers (K at 32^3x64: 97.4 us per launch at 7 blocks, 93.1 at 6 or 5, 103 at 8);
 // FP64 and double-float keep the compiler's choice (a bound of 3 blocks made the rolled
 // double-float stencil 7-18% slower).
 template <int PREC>

@@ -55,9 +55,23 @@ static double true_residual(pfmp_op* op, const void* x, const void* b, void* r, 
   return c->h_sums[0];
 }
 
+// The fused FP32 iteration reads fewer CG-vector bytes but more per stencil site (two
+// fields at every neighbour in its first phase) and runs at a lower occupancy; it wins
+// where the solve's working set (links, clover, five FP32 fields: ~1440 B per
+// half-lattice site) stays in L2 (16^3x32: 7.25 vs 8.43 ms per solve) and loses a few per
+// cent where K streams from HBM (32^3x64: 102 vs 99 ms), so it is used up to the L2 size.
+static bool fused_iteration(pfmp_op* op) {
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, op->ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return 1440.0 * op->ctx->g.Vh <= (double)l2;
+}
+
 static void launch_chunk(pfmp_op* op, int prec, void* x, void* r, void* p, void* Ap, int chunk) {
   pfmp_ctx* c = op->ctx;
-  if (prec == PFMP_F32) {  // four kernels per iteration, the vector updates fused in
+  if (prec == PFMP_F32 && fused_iteration(op)) {  // four kernels per iteration, updates fused in
     for (int k = 0; k < chunk; ++k) cg_fused_iteration(op, (float4*)x, (float4*)r, (float4*)p);
     return;
   }
