@@ -458,7 +458,7 @@ def run_ours(args, rank, world):
 def batched_96(capi, stream, l2_flush, args):
     """96 systems -- 32 each on 8^4, 12^3x24 and 16^3x32, eps = 0.4, kappa ~ U[0.120, 0.134]
     (seed 7), c_sw = 1.0, 1..8 Gaussian right-hand sides each (seed 8) -- solved to 1e-10 by
-    the batched grouped-kernel solver, against the same solves one after another with the
+    the batched solver (one persistent launch), against the same solves one after another with the
     single-system mixed solver."""
     import torch
 
